@@ -1,0 +1,161 @@
+"""Seeded synthetic inputs (sparse patterns, values, vectors) for tests and the benchmark.
+
+Inputs only: nothing here computes a format conversion or a product.  The C
+source (``synth.c``) is compiled by :func:`build`; every draw is counter-based
+SplitMix64, so results are independent of the thread count.
+
+Workload recipes (stand-ins for the paper's test set, Section 5.2, which is not
+available): R-MAT with the Graph500 parameters a/b/c/d = 0.57/0.19/0.19/0.05,
+Erdos-Renyi with a fixed number of columns per row, and Zipf power-law rows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "libsynth.so")
+_lock = threading.Lock()
+_lib = None
+
+RMAT_ABCD = (0.57, 0.19, 0.19, 0.05)
+
+
+def build(force: bool = False) -> str:
+    """Compile synth.c into _build/libsynth.so with gcc (portable flags only)."""
+    src = os.path.join(_HERE, "synth.c")
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
+        return _SO
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    tmp = _SO + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", src, "-o", tmp, "-lm"])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_SO)
+            i64, u64, i32, dbl, p = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+            lib.synth_draw.restype = u64
+            lib.synth_draw.argtypes = [u64, u64]
+            lib.synth_stream_key.restype = u64
+            lib.synth_stream_key.argtypes = [u64, u64]
+            lib.synth_rmat.restype = i64
+            lib.synth_rmat.argtypes = [i32, i64, dbl, dbl, dbl, u64, p, p]
+            lib.synth_values.restype = None
+            lib.synth_values.argtypes = [i64, p, p, u64, i32, p]
+            lib.synth_vector.restype = None
+            lib.synth_vector.argtypes = [i64, u64, i32, p]
+            lib.synth_er.restype = i64
+            lib.synth_er.argtypes = [i64, i32, u64, p, p]
+            lib.synth_zipf_lengths.restype = i64
+            lib.synth_zipf_lengths.argtypes = [i64, dbl, i64, dbl, u64, p]
+            lib.synth_zipf_fill.restype = None
+            lib.synth_zipf_fill.argtypes = [i64, u64, p, p, p, p]
+            lib.synth_set_threads.restype = None
+            lib.synth_set_threads.argtypes = [i32]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def splitmix_draw(key: int, ctr: int) -> int:
+    return int(_load().synth_draw(key, ctr))
+
+
+def rmat(scale: int, edge_factor: int = 16, seed: int = 0, abcd=RMAT_ABCD, edges: int | None = None):
+    """R-MAT pattern on 2^scale vertices, duplicates removed (first occurrence kept).
+
+    Returns (rows, cols) int32 arrays in edge order (unsorted)."""
+    lib = _load()
+    e = int(edges if edges is not None else edge_factor * (1 << scale))
+    rows = np.empty(e, dtype=np.int32)
+    cols = np.empty(e, dtype=np.int32)
+    a, b, c, _ = abcd
+    nnz = lib.synth_rmat(scale, e, a, b, c, seed, _ptr(rows), _ptr(cols))
+    if nnz < 0:
+        raise MemoryError("synth_rmat: out of host memory")
+    return rows[:nnz].copy(), cols[:nnz].copy()
+
+
+def values(rows: np.ndarray, cols: np.ndarray, seed: int = 0, integer: bool = False) -> np.ndarray:
+    """Matrix values v(seed, r, c): U[-1,1) doubles, or integers in [-8,8] stored as doubles."""
+    lib = _load()
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    out = np.empty(rows.shape[0], dtype=np.float64)
+    lib.synth_values(rows.shape[0], _ptr(rows), _ptr(cols), seed, 1 if integer else 0, _ptr(out))
+    return out
+
+
+def vector(n: int, seed: int = 1, integer: bool = False) -> np.ndarray:
+    """Dense vector x_j(seed, j) with the same value kinds as :func:`values`."""
+    lib = _load()
+    out = np.empty(n, dtype=np.float64)
+    lib.synth_vector(n, seed, 1 if integer else 0, _ptr(out))
+    return out
+
+
+def erdos_renyi(n: int, per_row: int = 8, seed: int = 0):
+    """n x n pattern with exactly ``per_row`` distinct uniform columns in each row."""
+    lib = _load()
+    rows = np.empty(n * per_row, dtype=np.int32)
+    cols = np.empty(n * per_row, dtype=np.int32)
+    if lib.synth_er(n, per_row, seed, _ptr(rows), _ptr(cols)) < 0:
+        raise ValueError("per_row > n")
+    return rows, cols
+
+
+def zipf_rows(n: int, alpha: float = 1.8, cap: int = 1 << 20, empty_frac: float = 0.05, seed: int = 0):
+    """n x n pattern with Zipf(alpha) row lengths (capped), a fraction of empty rows,
+    and distinct uniform columns.  Rows are emitted in row order."""
+    lib = _load()
+    lens = np.empty(n, dtype=np.int64)
+    total = lib.synth_zipf_lengths(n, alpha, min(cap, n), empty_frac, seed, _ptr(lens))
+    if total < 0:
+        raise MemoryError("synth_zipf_lengths")
+    off = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=off[1:])
+    rows = np.empty(total, dtype=np.int32)
+    cols = np.empty(total, dtype=np.int32)
+    lib.synth_zipf_fill(n, seed, _ptr(off), _ptr(lens), _ptr(rows), _ptr(cols))
+    return rows, cols
+
+
+def shuffle_order(nnz: int, seed: int = 7) -> np.ndarray:
+    """A seeded permutation of range(nnz) (to present COO triplets in random order)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.permutation(nnz)
+
+
+def random_coo(m: int, n: int, nnz: int, seed: int = 0, dup_frac: float = 0.0):
+    """Small uniform random COO pattern for unit tests (numpy PCG64; may contain
+    duplicates when dup_frac > 0)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if m == 0 or n == 0:
+        return np.zeros(0, np.int32), np.zeros(0, np.int32)
+    r = rng.integers(0, m, size=nnz, dtype=np.int64)
+    c = rng.integers(0, n, size=nnz, dtype=np.int64)
+    key = r * n + c
+    _, first = np.unique(key, return_index=True)
+    first.sort()
+    r, c = r[first], c[first]
+    if dup_frac > 0 and r.size > 0:
+        k = max(1, int(dup_frac * r.size))
+        pick = rng.integers(0, r.size, size=k)
+        r = np.concatenate([r, r[pick]])
+        c = np.concatenate([c, c[pick]])
+        perm = rng.permutation(r.size)
+        r, c = r[perm], c[perm]
+    return r.astype(np.int32), c.astype(np.int32)
