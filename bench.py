@@ -1,0 +1,463 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 SpMV library on the R-MAT scale-22 workload.
+
+One step = one pass of the whole hot path over one synthetic matrix:
+    ingest the triplets (spmv_create_coo) -> COO->CSR + row-length bins -> row-split SpMV
+    -> merge-path partition -> merge-path SpMV -> CSR->Hilbert-blocked (beta = 2^14)
+    -> blocked SpMV -> destroy.
+Workload: R-MAT scale 22 (4,194,304 rows and columns), edge factor 16, Graph500
+a/b/c/d = 0.57/0.19/0.19/0.05, duplicate edges removed, FP64 values and x uniform in
+[-1, 1), seeded; the triplets are presented in edge (random) order.
+
+value = algorithmic bytes of every row of the step / device time of the step (GB/s), the
+bytes per row defined in ALGO_BYTES below.  The JSON line also carries each row's time,
+GB/s and GFLOP/s, the roofline of the dominant kernel, the end-to-end number through
+host buffers, clocks sampled during the timed region and the oracle's CPU baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpMV GB/s vs HBM roofline & GFLOP/s (R-MAT s22); served p50/p99 vs plain FP64"
+RMAT = dict(scale=22, edge_factor=16, abcd=(0.57, 0.19, 0.19, 0.05))
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ------------------------------------------------------------------ workload and bytes
+
+def workload_desc(scale):
+    return (f"R-MAT scale {scale} (n = 2^{scale}), edge factor 16, a/b/c/d 0.57/0.19/0.19/0.05, deduplicated, "
+            "FP64 U(-1,1) values and x, triplets in edge order; step = ingest COO -> CSR + row bins -> "
+            "row-split SpMV -> merge partition -> merge-path SpMV -> CSR->Hilbert-blocked (beta 2^14) -> blocked SpMV")
+
+
+def row_bytes(m, n, nnz, nblk):
+    """Algorithmic (compulsory) bytes of each row of the step, FP64 values, int32 indices."""
+    csr = nnz * 12 + (m + 1) * 4
+    hb = nnz * 12 + nblk * 12 + 4
+    spmv_csr = csr + n * 8 + m * 8
+    return {
+        "ingest": 2 * nnz * 16,                  # read the caller's triplets, write the library copy
+        "coo_to_csr": nnz * 16 + csr,            # read triplets, write CSR
+        "rowsplit_bins": (m + 1) * 4 + m * 4,    # read row_ptr, write the binned row list
+        "spmv_rowsplit": spmv_csr,
+        "merge_partition": 0,                    # O(tiles log m), not part of the compulsory traffic
+        "spmv_merge": spmv_csr,
+        "csr_to_hb": csr + hb,                   # read CSR, write blocked arrays
+        "spmv_hb": hb + n * 8 + m * 8,
+    }
+
+
+def row_flops(nnz):
+    return {"spmv_rowsplit": 2 * nnz, "spmv_merge": 2 * nnz, "spmv_hb": 2 * nnz}
+
+
+def sort_passes(bits):
+    return (bits + 7) // 8
+
+
+def kernel_bytes(name, m, n, nnz, nblk):
+    """Algorithmic bytes per step that each traced kernel moves (for the roofline of the
+    dominant kernel): radix passes read and write (key, payload) = 12 B per item each way."""
+    K = max(1, (max(m, n, 2) - 1).bit_length())
+    cbits = max(1, (n - 1).bit_length()) if n > 1 else 1
+    rbits = max(1, (m - 1).bit_length()) if m > 1 else 1
+    p_csr, p_hb, p_bins = sort_passes(cbits + rbits), sort_passes(2 * K), 1
+    sort_items = (p_csr + p_hb) * nnz + p_bins * m
+    spmv_csr = nnz * 12 + (m + 1) * 4 + n * 8 + m * 8
+    table = {
+        "k_rs_downsweep": (24 * sort_items, p_csr + p_hb + p_bins),
+        "k_rs_upsweep": (8 * sort_items, p_csr + p_hb + p_bins),
+        "k_merge_spmv": (spmv_csr, 1),
+        "k_rowsplit": (spmv_csr, 1),
+        "k_hb_spmv": (nnz * 12 + nblk * 12 + n * 8 + m * 8, 1),
+    }
+    return table.get(name)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+
+def oracle_step(m, n, rows, cols, vals, x, lb):
+    """One pass of the path through the oracle (Algorithm 1 for the row-split row, the
+    merge-based algorithm for the merge row, the blocked structure for the HB row)."""
+    import oracle
+    rp, co, vo = oracle.coo_to_csr(m, n, rows, cols, vals)
+    oracle.csr_spmv(rp, co, vo, x)
+    oracle.merge_spmv(rp, co, vo, x, 1024)
+    hb = oracle.csr_to_hb(m, n, rp, co, vo, lb)
+    oracle.hb_spmv(m, hb, x)
+    return int(co.size), int(hb["nblk"])
+
+
+def cpu_baseline(scale, rows, cols, vals, x, frac, reps=1):
+    """Time the oracle on a prefix of the triplets (edges are in random order, so a prefix
+    is a uniform sample).  Returns (GB/s in the step's byte accounting, description)."""
+    import oracle
+    m = n = 1 << scale
+    k = max(1, int(rows.size * frac))
+    r, c, v = rows[:k].copy(), cols[:k].copy(), vals[:k].copy()
+    lb = oracle.log2_beta(n, 8, 200 * 1024)
+    best = None
+    for _ in range(reps):
+        t = time.perf_counter()
+        nnz, nblk = oracle_step(m, n, r, c, v, x, lb)
+        dt = time.perf_counter() - t
+        best = dt if best is None else min(best, dt)
+    total = sum(row_bytes(m, n, nnz, nblk).values())
+    desc = (f"first {k} of {rows.size} triplets ({frac:.4g} of the scale-{scale} matrix; edge order is random), "
+            f"m = n = 2^{scale}; oracle step: triplet->CRS, Algorithm 1, merge-based SpMV (1024 parts), "
+            f"CRS->Hilbert blocked (beta 2^{lb}), blocked SpMV; {best:.2f} s")
+    return total / best / 1e9, desc, best
+
+
+# ------------------------------------------------------------------ main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=RMAT["scale"])
+    ap.add_argument("--cpu-frac", type=float, default=1.0 / 4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    import numpy as np
+    import synth
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2502_19284_gb300 as sp
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    # each rank runs its own instance of the workload (independent problems: weak scaling)
+    scale = args.scale
+    m = n = 1 << scale
+    rows, cols = synth.rmat(scale, RMAT["edge_factor"], seed=rank, abcd=RMAT["abcd"])
+    vals = synth.values(rows, cols, seed=rank)
+    x = synth.vector(n, seed=rank + 1)
+    nnz_in = int(rows.size)
+    r_d = torch.from_numpy(rows).to(dev)
+    c_d = torch.from_numpy(cols).to(dev)
+    v_d = torch.from_numpy(vals).to(dev)
+    x_d = torch.from_numpy(x).to(dev)
+    y_d = torch.empty(m, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    names = ["ingest", "coo_to_csr", "spmv_rowsplit", "merge_partition", "spmv_merge", "csr_to_hb", "spmv_hb"]
+
+    def step(rec, src=None, host_x=None, host_y=None):
+        # src: host (pinned) triplets for the end-to-end variant
+        e = [ev() for _ in range(len(names) + 1)]
+        e[0].record()
+        if src is None:
+            h = sp.spmv_create_coo(m, n, r_d, c_d, v_d)
+        else:
+            h = sp.spmv_create_coo(m, n, *src)
+        e[1].record()
+        sp.spmv_convert(h, "rowsplit")
+        e[2].record()
+        if host_x is not None:
+            x_d.copy_(host_x, non_blocking=True)
+        sp.spmv_mul(h, x_d, y_d)
+        if host_y is not None:
+            host_y[0].copy_(y_d, non_blocking=True)
+        e[3].record()
+        sp.spmv_convert(h, "merge")
+        e[4].record()
+        sp.spmv_mul(h, x_d, y_d)
+        if host_y is not None:
+            host_y[1].copy_(y_d, non_blocking=True)
+        e[5].record()
+        sp.spmv_convert(h, "hb")
+        e[6].record()
+        sp.spmv_mul(h, x_d, y_d)
+        if host_y is not None:
+            host_y[2].copy_(y_d, non_blocking=True)
+        e[7].record()
+        info = sp.spmv_info(h)
+        sp.spmv_destroy(h)
+        rec.append((e, info))
+
+    def timed(K, W, trace=False, **kw):
+        for _ in range(W):
+            step([], **kw)
+        torch.cuda.synchronize()
+        if trace:
+            sp.spmv_trace_enable(True)   # clears the table; synchronises the device
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        recs = []
+        t0, t1 = ev(), ev()
+        w0 = time.perf_counter()
+        t0.record()
+        for _ in range(K):
+            step(recs, **kw)
+        t1.record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        if world > 1:
+            dist.barrier()
+        return t0.elapsed_time(t1), wall, recs
+
+    # ---- device-resident timed region (with the library's kernel trace on)
+    with ClockSampler(local) as clk:
+        total_ms, wall_s, recs = timed(args.steps, args.warmup, trace=True)
+        trace = sp.spmv_trace_read()
+        sp.spmv_trace_enable(False)
+    info = recs[-1][1]
+    nnz, nblk = info["nnz"], info["nblk"]
+    # per-row times (sub-step events; spmv rows also contain their own kernels only)
+    per_row = {nm: [] for nm in names}
+    for e, _ in recs:
+        for i, nm in enumerate(names):
+            per_row[nm].append(e[i].elapsed_time(e[i + 1]))
+    # the rowsplit conversion (CSR + bins) and the first SpMV share a bracket; split them
+    rb = row_bytes(m, n, nnz, nblk)
+    step_bytes = sum(rb.values())
+    ms_step = total_ms / args.steps
+    ms_max = ms_step
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * step_bytes / (ms_max * 1e-3) / 1e9
+
+    rows_out = {}
+    flops = row_flops(nnz)
+    bmap = {"ingest": rb["ingest"], "coo_to_csr": rb["coo_to_csr"] + rb["rowsplit_bins"],
+            "spmv_rowsplit": rb["spmv_rowsplit"], "merge_partition": 0, "spmv_merge": rb["spmv_merge"],
+            "csr_to_hb": rb["csr_to_hb"], "spmv_hb": rb["spmv_hb"]}
+    for nm in names:
+        t_ms = statistics.median(per_row[nm])
+        d = {"ms": round(t_ms, 4), "gbs": round(bmap[nm] / (t_ms * 1e-3) / 1e9, 1) if bmap[nm] else None}
+        if nm in flops:
+            d["gflops"] = round(flops[nm] / (t_ms * 1e-3) / 1e9, 1)
+        rows_out[nm] = d
+
+    # ---- roofline of the dominant kernel (device time from the trace)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "of measured" if peak else "of fallback"
+    peak = peak or FALLBACK_HBM_GBS
+    traffic_db = {}
+    try:
+        traffic_db = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    except (OSError, ValueError):
+        pass
+
+    def roofline_for(kname):
+        cnt, kms = trace[kname]
+        kb = kernel_bytes(kname, m, n, nnz, nblk)
+        if kb is None:
+            return None
+        bytes_per_step, launches_per_step = kb
+        per_launch = bytes_per_step / launches_per_step
+        dur = kms / cnt
+        ach = per_launch / (dur * 1e-3) / 1e9
+        traffic = None
+        t = traffic_db.get(kname)
+        if t and t.get("source_sha") == source_sha(t.get("source")) and t.get("scale") == scale:
+            traffic = t.get("bytes_per_launch")
+        return {"kernel": kname, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "peak_note": peak_src, "traffic": traffic,
+                "algorithmic_bytes_per_launch": int(per_launch), "launches": cnt, "avg_launch_ms": round(dur, 5)}
+
+    known = [k for k in trace if kernel_bytes(k, m, n, nnz, nblk)]
+    dominant = max(trace, key=lambda k: trace[k][1])
+    roof = roofline_for(dominant) if dominant in known else None
+    roof_spmv = roofline_for("k_merge_spmv") if "k_merge_spmv" in trace else None
+    launches = sum(c for c, _ in trace.values())
+    shares = {k: round(v[1] / sum(u[1] for u in trace.values()), 4) for k, v in
+              sorted(trace.items(), key=lambda kv: -kv[1][1])}
+
+    # ---- end to end through host buffers (pinned triplets and x in, y out)
+    e2e = None
+    if not args.no_e2e:
+        hr = torch.from_numpy(rows).pin_memory()
+        hc = torch.from_numpy(cols).pin_memory()
+        hv = torch.from_numpy(vals).pin_memory()
+        hx = torch.from_numpy(x).pin_memory()
+        hy = [torch.empty(m, dtype=torch.float64).pin_memory() for _ in range(3)]
+        K2 = max(2, args.steps // 2)
+        tot2, wall2, _ = timed(K2, 1, src=(hr, hc, hv), host_x=hx, host_y=hy)
+        ms2 = tot2 / K2
+        if world > 1:
+            t = torch.tensor([ms2], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms2 = float(t.item())
+        e2e = {"value": round(world * step_bytes / (ms2 * 1e-3) / 1e9, 2), "unit": "GB/s",
+               "h2d_bytes_per_step": nnz_in * 16 + n * 8, "d2h_bytes_per_step": 3 * m * 8,
+               "ms_per_step": round(ms2, 3)}
+
+    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        gbs, desc, secs = cpu_baseline(scale, rows, cols, vals, x, args.cpu_frac)
+        cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    out = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_max, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(scale), "m": m, "n": n, "nnz": nnz, "triplets": nnz_in, "nblk": nblk,
+                   "log2_beta": info["log2_beta"], "step_bytes": step_bytes,
+                   "l2": "inputs larger than L2 (triplets 16 B x nnz per step)", "parallelism": f"replicas x{world}"},
+        "rows": rows_out,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": roof,
+        "roofline_spmv_merge": roof_spmv,
+        "kernel_shares": shares,
+        "cpu_baseline": cpu,
+        "wall_s_timed": round(wall_s, 3),
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def source_sha(rel):
+    if not rel:
+        return None
+    try:
+        return hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the oracle, as it stands, on the host cores, K timed steps on a
+    bounded sample of the same workload (rank 0 only)."""
+    if rank != 0:
+        return 0
+    import synth
+    scale = args.scale
+    m = n = 1 << scale
+    rows, cols = synth.rmat(scale, RMAT["edge_factor"], seed=0, abcd=RMAT["abcd"])
+    vals = synth.values(rows, cols, seed=0)
+    x = synth.vector(n, seed=1)
+    frac = 1.0 / 32
+    for _ in range(args.warmup):
+        cpu_baseline(scale, rows, cols, vals, x, frac)
+    times, gb = [], []
+    for _ in range(args.steps):
+        g, desc, secs = cpu_baseline(scale, rows, cols, vals, x, frac)
+        times.append(secs)
+        gb.append(g)
+    value = statistics.median(gb)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.median(times), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(scale), "m": m, "n": n, "sample_frac": frac},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

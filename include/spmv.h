@@ -1,0 +1,228 @@
+/*
+ * spmv.h -- C ABI of the GB300 (sm_103a) sparse matrix-vector library.
+ *
+ * Computes y = A x for a sparse A in R^{m x n} with nnz nonzeros and dense x, y
+ * (Bergmans, Meerbergen, Vandebril, "Algorithms for Parallel Shared-Memory Sparse
+ * Matrix-Vector Multiplication on Unstructured Matrices", Section 1), together with
+ * the storage-format conversions the products need (Section 5.1: a conversion sorts
+ * the nonzeros into the format's order, then populates and compresses the arrays).
+ *
+ * Conventions shared by every call:
+ *   - Indices are 0-based int32; nnz < 2^31, m, n < 2^31 (SPMV_ERR_UNSUPPORTED otherwise).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Work is enqueued on it in stream order.
+ *   - Device pointers are plain CUDA device addresses; the library never frees a
+ *     caller's buffer and never keeps a caller pointer after a call returns.
+ *   - Every call returns a status and never aborts, traps or exits.  On error,
+ *     spmv_last_error() describes the failure (thread-local text).
+ *   - A handle is not thread-safe: calls on one handle must not run concurrently
+ *     from several host threads.  Different handles are independent.
+ */
+#ifndef GB300_SPMV_H
+#define GB300_SPMV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spmv_matrix *spmv_handle;   /* opaque; owns all of its device storage */
+
+typedef enum {
+    SPMV_OK = 0,
+    SPMV_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer, unknown enum, handle misuse   */
+    SPMV_ERR_INDEX_RANGE = 2,   /* a triplet index outside [0,m) x [0,n)                 */
+    SPMV_ERR_DUPLICATE = 3,     /* duplicate (row, col) with SPMV_DUP_ERROR              */
+    SPMV_ERR_OOM = 4,           /* device allocation failed (nothing leaked)             */
+    SPMV_ERR_UNSUPPORTED = 5,   /* size/format/dtype combination not provided            */
+    SPMV_ERR_CUDA = 6,          /* a CUDA runtime call failed; see spmv_last_error()     */
+    SPMV_ERR_TIMEOUT = 7,       /* a bounded device wait gave up                         */
+    SPMV_ERR_NOT_CONVERTED = 8  /* spmv_mul before any spmv_convert                      */
+} spmv_status;
+
+/* Element types.  SPMV_PATTERN: no stored values, every nonzero is 1 (data == NULL). */
+typedef enum { SPMV_F64 = 0, SPMV_F32 = 1, SPMV_BF16 = 2, SPMV_PATTERN = 3 } spmv_dtype;
+
+/* Storage formats / product algorithms.
+ *   CSR_ROWSPLIT  CRS (Section 2, Algorithm 1) with rows split over warps by length
+ *                 bins -- the GPU counterpart of ParCRS (Section 5.1).
+ *   CSR_MERGE     CRS with the merge-path partition of Section 3.3: equal shares of
+ *                 (row ends + nonzeros) per tile, carries added in tile order.
+ *   HB            Hilbert-ordered blocked format (Sections 3.1, 4.2: BCOHC/BCOHCH
+ *                 storage -- beta x beta blocks, packed 16+16-bit in-block indices,
+ *                 nonzeros and blocks in Hilbert-curve order).
+ *   AUTO          the library picks one from the matrix's row-length statistics.   */
+typedef enum {
+    SPMV_FMT_CSR_ROWSPLIT = 0,
+    SPMV_FMT_CSR_MERGE = 1,
+    SPMV_FMT_HB = 2,
+    SPMV_FMT_AUTO = 3
+} spmv_format;
+
+/* spmv_create_coo flags */
+#define SPMV_DEVICE_PTRS 0x1u   /* row_ind/col_ind/data are device pointers (else host) */
+#define SPMV_DUP_SUM 0x0u       /* duplicates are added, in input order (default)       */
+#define SPMV_DUP_ERROR 0x2u     /* duplicates are rejected with SPMV_ERR_DUPLICATE       */
+
+/* Order of nonzeros inside an HB block. */
+#define SPMV_INNER_HILBERT 0    /* Hilbert order (BCOHCH, Section 4.2)                  */
+#define SPMV_INNER_ROWMAJOR 1   /* row-wise (BCOHC, Section 4.2)                        */
+
+typedef struct {
+    int32_t log2_beta;    /* HB block side 2^log2_beta; 0 = Eq. 2 rule (Section 3.1)     */
+    int32_t inner_order;  /* SPMV_INNER_*                                                */
+    int32_t tile;         /* CSR_MERGE: path items per CTA tile; 0 = library default     */
+} spmv_convert_opts;
+
+/*
+ * Accumulation precision of spmv_mul (values are always converted on load).
+ *   SPMV_ACC_DEFAULT  F64 data: double precision results; when every stored value and
+ *                     every x lies in [2^-50, 2^45] (or is 0) the products and sums are
+ *                     evaluated with compensated FP32 arithmetic (double-float: 48-bit
+ *                     operands, error-free products, TwoSum accumulation; error below
+ *                     4e-14 * (|A||x|)_i), otherwise with native FP64.  Other data: F32.
+ *   SPMV_ACC_F64      native FP64 arithmetic throughout.
+ *   SPMV_ACC_F32      FP32 accumulation.
+ *   SPMV_ACC_COMPENSATED  FP32 with two-sum compensation on long rows.
+ */
+#define SPMV_ACC_DEFAULT 0u
+#define SPMV_ACC_F32 1u
+#define SPMV_ACC_F64 2u
+#define SPMV_ACC_COMPENSATED 3u
+
+/*
+ * spmv_create_coo -- ingest a matrix in triplet (coordinate) form (Section 2, Eq. 1).
+ *   m, n        matrix shape, 0 <= m, n < 2^31.
+ *   nnz         number of triplets, 0 <= nnz < 2^31 (nnz = 0 is a valid empty matrix).
+ *   row_ind     nnz int32 row indices; col_ind: nnz int32 column indices; any order.
+ *   data        nnz values of type dt, or NULL when dt == SPMV_PATTERN.
+ *   flags       SPMV_DEVICE_PTRS if the three arrays live on the device, plus one of
+ *               SPMV_DUP_SUM / SPMV_DUP_ERROR (applied when a format is built).
+ *   stream      stream for the copy and validation.
+ *   out         receives the handle on success, NULL on failure.
+ * The library copies the triplets into its own device memory; the caller may free or
+ * reuse the arrays as soon as the call returns.  Indices are range-checked on the
+ * device; the call synchronises `stream` once to return SPMV_ERR_INDEX_RANGE.
+ */
+spmv_status spmv_create_coo(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ind,
+                            const int32_t *col_ind, const void *data, spmv_dtype dt, uint32_t flags,
+                            void *stream, spmv_handle *out);
+
+/*
+ * spmv_convert -- build format `f` from the handle's triplets (Section 5.1).
+ *   CSR_ROWSPLIT / CSR_MERGE: stable LSD radix sort on the key (row, col), duplicate
+ *   resolution, row_ptr by boundary fill, plus the algorithm's partition tables.
+ *   HB: Hilbert key h(r, c) on the 2^K grid (K = ceil(log2 max(m, n))), radix sort on h
+ *   (or on (h >> 2 log2_beta, r, c) for SPMV_INNER_ROWMAJOR), block segmentation,
+ *   packed indices ((r mod beta) << 16 | (c mod beta)).  Requires beta <= 2^16.
+ * opt may be NULL (defaults).  The CRS arrays are kept once built, so a later
+ * conversion to another CSR algorithm or to HB reuses them.  The converted format
+ * becomes the one spmv_mul uses.  Synchronises `stream` once (status read-back).
+ */
+spmv_status spmv_convert(spmv_handle h, spmv_format f, const spmv_convert_opts *opt, void *stream);
+
+/*
+ * spmv_mul -- y := A x (overwrites y; Algorithm 1 starts from y = 0).
+ *   x           device array of n elements of vec_dt; y: device array of m elements.
+ *   vec_dt      SPMV_F64 or SPMV_F32 (type of both x and y).
+ *   accum       SPMV_ACC_* (SPMV_ACC_DEFAULT is always valid).
+ * Asynchronous: enqueues kernels on `stream` and returns.  Uses the format of the
+ * last successful spmv_convert.  The handle's internal scratch is shared by its
+ * calls, so two spmv_mul calls on one handle must be ordered (same stream or
+ * events); calls on different handles may overlap freely.
+ */
+spmv_status spmv_mul(spmv_handle h, const void *x, void *y, spmv_dtype vec_dt, uint32_t accum, void *stream);
+
+/*
+ * spmv_mul_batch -- Y_i := A_i X_i for `count` handles and k right-hand sides each.
+ *   hs          count converted handles (formats may differ).
+ *   k           right-hand sides per product, 1 <= k <= 16.
+ *   X, Y        count device pointers; X[i] is n_i x k row-major (the k values of
+ *               x_j contiguous), Y[i] is m_i x k row-major.
+ * All products run in one persistent launch over a work table built per batch shape;
+ * the launch is captured once into a CUDA graph and replayed for the same shape.
+ */
+spmv_status spmv_mul_batch(int count, const spmv_handle *hs, int k, const void *const *X, void *const *Y,
+                           spmv_dtype vec_dt, uint32_t accum, void *stream);
+
+/* spmv_destroy -- free every device buffer of the handle (synchronises with its stream). */
+spmv_status spmv_destroy(spmv_handle h);
+
+/* ---------------------------------------------------------------- inspection */
+
+typedef struct {
+    int64_t m, n;
+    int64_t nnz;            /* distinct nonzeros once converted, else the triplet count */
+    int32_t format;         /* active spmv_format, or -1 before conversion               */
+    int32_t dtype;          /* spmv_dtype of the stored values                           */
+    int32_t log2_beta;      /* HB block side (0 if no HB)                                */
+    int32_t grid_order;     /* K of the Hilbert grid                                     */
+    int64_t nblk;           /* non-empty HB blocks                                       */
+    int64_t merge_tiles;    /* CSR_MERGE tiles                                           */
+    int32_t merge_tile_items;
+    int32_t pad_;
+    int64_t device_bytes;   /* device memory held by the handle                          */
+} spmv_info_t;
+
+spmv_status spmv_info(spmv_handle h, spmv_info_t *out);
+
+/*
+ * spmv_export_csr -- copy the CRS arrays to host buffers (row_ptr: m+1, col_ind and
+ * data: nnz; data may be NULL; it receives values in the stored dtype).
+ */
+spmv_status spmv_export_csr(spmv_handle h, int32_t *row_ptr, int32_t *col_ind, void *data);
+
+/*
+ * spmv_export_hb -- copy the HB arrays to host buffers: idx and data (nnz),
+ * blk_ptr (nblk+1), blk_row and blk_col (nblk).  Any pointer may be NULL.
+ */
+spmv_status spmv_export_hb(spmv_handle h, uint32_t *idx, void *data, int32_t *blk_ptr, int32_t *blk_row,
+                           int32_t *blk_col);
+
+/*
+ * spmv_export_merge_partition -- copy the merge-path split points of the CSR_MERGE
+ * partition (Section 3.3): for tile t = 0..tiles, row_start[t] row ends and
+ * nz_start[t] nonzeros are consumed before the tile (tiles+1 entries each).
+ */
+spmv_status spmv_export_merge_partition(spmv_handle h, int32_t *row_start, int32_t *nz_start);
+
+/* Text of the last error raised on the calling host thread ("" if none). */
+const char *spmv_last_error(void);
+
+/* Name of a status code. */
+const char *spmv_status_string(spmv_status s);
+
+/* Hilbert index of (r, c) on the 2^K grid, computed by the device kernel for n
+ * points (device arrays rows, cols -> keys).  Exposed for testing the key kernel. */
+spmv_status spmv_hilbert_keys(int K, int64_t n, const int32_t *rows, const int32_t *cols, uint64_t *keys,
+                              void *stream);
+
+/* ---------------------------------------------------------------- tracing */
+
+/*
+ * spmv_trace_enable -- turn kernel tracing on (1) or off (0).  While on, every kernel
+ * the library launches is bracketed by two CUDA events on its stream (a few
+ * microseconds of host overhead per launch, no change to the kernels).  Turning it on
+ * clears the table.  Synchronises the device.
+ */
+spmv_status spmv_trace_enable(int on);
+
+/*
+ * spmv_trace_read -- synchronise the device and return the number of distinct traced
+ * kernels; the first max_entries of them are written as (name, launches, total device
+ * milliseconds).  Names are static strings owned by the library.  Returns -1 if the
+ * synchronisation fails.
+ */
+int spmv_trace_read(int max_entries, const char **names, long long *counts, double *total_ms);
+
+/* Test hook: the allocation after `n` further successful ones fails with
+ * SPMV_ERR_OOM, without touching the device (n < 0 turns the hook off). */
+void spmv_test_fail_alloc(long long n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_SPMV_H */

@@ -1,0 +1,273 @@
+"""Python binding of libspmv, the GB300 (sm_103a) SpMV library.
+
+Argument marshalling only: every function calls the C entry point of the same name in
+``_build/libspmv.so`` (declared in ``include/spmv.h``) and raises :class:`SpmvError` on
+a non-zero status.  Vectors and device arrays are torch CUDA tensors (torch provides
+device memory and streams); host arrays may be numpy arrays or CPU tensors.
+
+There is no CPU path: if the compiled library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libspmv.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libspmv.so not built ({LIB_PATH}); run `python -c 'import __graft_entry__ as g; g.build()'`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ------------------------------------------------------------------ constants (spmv.h)
+SPMV_OK, SPMV_ERR_INVALID_ARG, SPMV_ERR_INDEX_RANGE, SPMV_ERR_DUPLICATE, SPMV_ERR_OOM, \
+    SPMV_ERR_UNSUPPORTED, SPMV_ERR_CUDA, SPMV_ERR_TIMEOUT, SPMV_ERR_NOT_CONVERTED = range(9)
+SPMV_F64, SPMV_F32, SPMV_BF16, SPMV_PATTERN = range(4)
+SPMV_FMT_CSR_ROWSPLIT, SPMV_FMT_CSR_MERGE, SPMV_FMT_HB, SPMV_FMT_AUTO = range(4)
+SPMV_DEVICE_PTRS = 0x1
+SPMV_DUP_SUM = 0x0
+SPMV_DUP_ERROR = 0x2
+SPMV_INNER_HILBERT, SPMV_INNER_ROWMAJOR = 0, 1
+SPMV_ACC_DEFAULT, SPMV_ACC_F32, SPMV_ACC_F64, SPMV_ACC_COMPENSATED = range(4)
+
+FORMATS = {"rowsplit": SPMV_FMT_CSR_ROWSPLIT, "merge": SPMV_FMT_CSR_MERGE, "hb": SPMV_FMT_HB, "auto": SPMV_FMT_AUTO}
+ELEM_SIZE = {SPMV_F64: 8, SPMV_F32: 4, SPMV_BF16: 2, SPMV_PATTERN: 0}
+
+
+class spmv_convert_opts(ctypes.Structure):
+    _fields_ = [("log2_beta", ctypes.c_int32), ("inner_order", ctypes.c_int32), ("tile", ctypes.c_int32)]
+
+
+class spmv_info_t(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("format", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("log2_beta", ctypes.c_int32), ("grid_order", ctypes.c_int32),
+                ("nblk", ctypes.c_int64), ("merge_tiles", ctypes.c_int64), ("merge_tile_items", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+
+_p, _i64, _i32, _u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32
+_SIG = {
+    "spmv_create_coo": [_i64, _i64, _i64, _p, _p, _p, _i32, _u32, _p, ctypes.POINTER(_p)],
+    "spmv_convert": [_p, _i32, ctypes.POINTER(spmv_convert_opts), _p],
+    "spmv_mul": [_p, _p, _p, _i32, _u32, _p],
+    "spmv_mul_batch": [_i32, ctypes.POINTER(_p), _i32, ctypes.POINTER(_p), ctypes.POINTER(_p), _i32, _u32, _p],
+    "spmv_destroy": [_p],
+    "spmv_info": [_p, ctypes.POINTER(spmv_info_t)],
+    "spmv_export_csr": [_p, _p, _p, _p],
+    "spmv_export_hb": [_p, _p, _p, _p, _p, _p],
+    "spmv_export_merge_partition": [_p, _p, _p],
+    "spmv_hilbert_keys": [_i32, _i64, _p, _p, _p, _p],
+}
+for _name, _args in _SIG.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_lib.spmv_last_error.restype = ctypes.c_char_p
+_lib.spmv_last_error.argtypes = []
+_lib.spmv_status_string.restype = ctypes.c_char_p
+_lib.spmv_status_string.argtypes = [ctypes.c_int]
+_lib.spmv_trace_enable.restype = ctypes.c_int
+_lib.spmv_trace_enable.argtypes = [ctypes.c_int]
+_lib.spmv_trace_read.restype = ctypes.c_int
+_lib.spmv_trace_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
+                                 ctypes.POINTER(ctypes.c_double)]
+_lib.spmv_test_fail_alloc.restype = None
+_lib.spmv_test_fail_alloc.argtypes = [ctypes.c_longlong]
+
+
+class SpmvError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.spmv_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {_lib.spmv_status_string(status).decode()} {msg}")
+
+
+def _check(st: int, where: str):
+    if st != SPMV_OK:
+        raise SpmvError(st, where)
+
+
+# ------------------------------------------------------------------ marshalling helpers
+
+def _addr(a):
+    """Address of a torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr() or None
+    return a.ctypes.data or None
+
+
+def _is_cuda(a) -> bool:
+    return getattr(a, "is_cuda", False)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def dtype_code(a) -> int:
+    import torch
+    if a is None:
+        return SPMV_PATTERN
+    t = a.dtype
+    if t in (torch.float64, np.float64):
+        return SPMV_F64
+    if t in (torch.float32, np.float32):
+        return SPMV_F32
+    if t == torch.bfloat16:
+        return SPMV_BF16
+    raise TypeError(f"unsupported element type {t}")
+
+
+class Handle:
+    """Owning wrapper of an spmv_handle (destroyed on spmv_destroy or garbage collection)."""
+
+    def __init__(self, ptr: int):
+        self.ptr = ptr
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                _lib.spmv_destroy(self.ptr)
+            except Exception:
+                pass
+            self.ptr = None
+
+
+# ------------------------------------------------------------------ C ABI, same names
+
+def spmv_create_coo(m, n, row_ind, col_ind, data=None, dtype=None, flags=SPMV_DUP_SUM, stream=None) -> Handle:
+    """Ingest triplets (Section 2).  Arrays are all device tensors or all host arrays."""
+    nnz = int(row_ind.shape[0])
+    dev = _is_cuda(row_ind)
+    if dev:
+        flags |= SPMV_DEVICE_PTRS
+    dt = dtype_code(data) if dtype is None else dtype
+    out = ctypes.c_void_p()
+    st = _lib.spmv_create_coo(m, n, nnz, _addr(row_ind), _addr(col_ind), _addr(data), dt, flags,
+                              _stream(stream), ctypes.byref(out))
+    _check(st, "spmv_create_coo")
+    return Handle(out.value)
+
+
+def spmv_convert(h: Handle, fmt="merge", log2_beta=0, inner_order=SPMV_INNER_HILBERT, tile=0, stream=None):
+    """Build a storage format (Section 5.1) and make it the active one."""
+    f = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+    opts = spmv_convert_opts(log2_beta, inner_order, tile)
+    _check(_lib.spmv_convert(h.ptr, f, ctypes.byref(opts), _stream(stream)), "spmv_convert")
+
+
+def spmv_mul(h: Handle, x, y, accum=SPMV_ACC_DEFAULT, stream=None):
+    """y := A x on device tensors x (n) and y (m) of the same dtype (float64 or float32)."""
+    vdt = dtype_code(x)
+    _check(_lib.spmv_mul(h.ptr, _addr(x), _addr(y), vdt, accum, _stream(stream)), "spmv_mul")
+    return y
+
+
+def spmv_mul_batch(handles, X, Y, k=1, accum=SPMV_ACC_DEFAULT, stream=None):
+    """Y_i := A_i X_i for a list of handles (X_i: n_i x k, Y_i: m_i x k, row-major)."""
+    cnt = len(handles)
+    hs = (ctypes.c_void_p * cnt)(*[h.ptr for h in handles])
+    xs = (ctypes.c_void_p * cnt)(*[_addr(x) for x in X])
+    ys = (ctypes.c_void_p * cnt)(*[_addr(y) for y in Y])
+    vdt = dtype_code(X[0]) if cnt else SPMV_F64
+    _check(_lib.spmv_mul_batch(cnt, hs, k, xs, ys, vdt, accum, _stream(stream)), "spmv_mul_batch")
+
+
+def spmv_destroy(h: Handle):
+    if h.ptr:
+        st = _lib.spmv_destroy(h.ptr)
+        h.ptr = None
+        _check(st, "spmv_destroy")
+
+
+def spmv_info(h: Handle) -> dict:
+    info = spmv_info_t()
+    _check(_lib.spmv_info(h.ptr, ctypes.byref(info)), "spmv_info")
+    return {name: getattr(info, name) for name, _ in spmv_info_t._fields_ if name != "pad_"}
+
+
+def spmv_export_csr(h: Handle):
+    """(row_ptr, col_ind, data-or-None) as numpy arrays (data in the stored dtype; bf16 as uint16)."""
+    inf = spmv_info(h)
+    m, nnz, dt = inf["m"], inf["nnz"], inf["dtype"]
+    rp = np.empty(m + 1, np.int32)
+    co = np.empty(max(nnz, 1), np.int32)
+    vals = _host_values(dt, nnz)
+    _check(_lib.spmv_export_csr(h.ptr, _addr(rp), _addr(co), _addr(vals)), "spmv_export_csr")
+    return rp, co[:nnz], (vals[:nnz] if vals is not None else None)
+
+
+def spmv_export_hb(h: Handle) -> dict:
+    inf = spmv_info(h)
+    nnz, nblk, dt = inf["nnz"], inf["nblk"], inf["dtype"]
+    idx = np.empty(max(nnz, 1), np.uint32)
+    vals = _host_values(dt, nnz)
+    bp = np.empty(nblk + 1, np.int32)
+    br = np.empty(max(nblk, 1), np.int32)
+    bc = np.empty(max(nblk, 1), np.int32)
+    _check(_lib.spmv_export_hb(h.ptr, _addr(idx), _addr(vals), _addr(bp), _addr(br), _addr(bc)), "spmv_export_hb")
+    return {"idx": idx[:nnz], "val": (vals[:nnz] if vals is not None else None), "blk_ptr": bp,
+            "blk_row": br[:nblk], "blk_col": bc[:nblk], "nblk": nblk, "log2beta": inf["log2_beta"]}
+
+
+def spmv_export_merge_partition(h: Handle):
+    tiles = spmv_info(h)["merge_tiles"]
+    rs = np.empty(tiles + 1, np.int32)
+    ns = np.empty(tiles + 1, np.int32)
+    _check(_lib.spmv_export_merge_partition(h.ptr, _addr(rs), _addr(ns)), "spmv_export_merge_partition")
+    return rs, ns
+
+
+def spmv_hilbert_keys(K, rows, cols, keys, stream=None):
+    """Device Hilbert keys of (rows[i], cols[i]) on the 2^K grid into keys (uint64 as int64 tensor)."""
+    _check(_lib.spmv_hilbert_keys(K, int(rows.shape[0]), _addr(rows), _addr(cols), _addr(keys), _stream(stream)),
+           "spmv_hilbert_keys")
+
+
+def spmv_trace_enable(on: bool = True):
+    """Bracket every library kernel launch with CUDA events (clears the table)."""
+    _check(_lib.spmv_trace_enable(1 if on else 0), "spmv_trace_enable")
+
+
+def spmv_trace_read() -> dict:
+    """{kernel name: (launches, total device ms)} of the launches traced so far."""
+    cap = 64
+    names = (ctypes.c_char_p * cap)()
+    counts = (ctypes.c_longlong * cap)()
+    ms = (ctypes.c_double * cap)()
+    n = _lib.spmv_trace_read(cap, names, counts, ms)
+    if n < 0:
+        raise SpmvError(SPMV_ERR_CUDA, "spmv_trace_read")
+    return {names[i].decode(): (int(counts[i]), float(ms[i])) for i in range(min(n, cap))}
+
+
+def spmv_last_error() -> str:
+    return _lib.spmv_last_error().decode(errors="replace")
+
+
+def spmv_test_fail_alloc(n: int):
+    _lib.spmv_test_fail_alloc(n)
+
+
+def _host_values(dt, nnz):
+    if dt == SPMV_F64:
+        return np.empty(max(nnz, 1), np.float64)
+    if dt == SPMV_F32:
+        return np.empty(max(nnz, 1), np.float32)
+    if dt == SPMV_BF16:
+        return np.empty(max(nnz, 1), np.uint16)
+    return None
+
+
+def library_path() -> str:
+    return LIB_PATH

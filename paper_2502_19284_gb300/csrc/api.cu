@@ -1,0 +1,469 @@
+// C ABI of libspmv (declared in include/spmv.h): argument checking, handle life cycle,
+// format dispatch.  Every entry point returns a status; none aborts.
+#include "common.cuh"
+#include "convert.cuh"
+
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+namespace spmv {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+spmv_status cuda_status(cudaError_t e, const char *what) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    g_err = buf;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();   // clear the sticky-free allocation error
+        return SPMV_ERR_OOM;
+    }
+    return SPMV_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- memory
+static std::atomic<long long> g_fail_after{-1};   // allocations left before an injected failure
+static std::once_flag g_pool_once;
+
+static void configure_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;   // keep freed blocks cached in the pool
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+}
+
+spmv_status dev_alloc(void **p, size_t bytes, const char *what, cudaStream_t s) {
+    *p = nullptr;
+    long long left = g_fail_after.load();
+    if (left >= 0) {
+        if (left == 0) {
+            g_err = std::string(what) + ": injected allocation failure";
+            return SPMV_ERR_OOM;
+        }
+        g_fail_after.fetch_sub(1);
+    }
+    std::call_once(g_pool_once, configure_pool);
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_status(e, what);
+    }
+    return SPMV_OK;
+}
+
+void dev_free(void *p) {
+    if (p) cudaFree(p);
+}
+
+void dev_free_async(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+// ---------------------------------------------------------------- tracing
+namespace {
+struct TraceRec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+struct TraceAgg {
+    const char *name;
+    long long count;
+    double ms;
+};
+std::atomic<bool> g_trace{false};
+std::mutex g_trace_mu;
+std::vector<TraceRec> g_trace_pending;
+std::vector<TraceAgg> g_trace_table;
+}  // namespace
+
+bool trace_on() { return g_trace.load(std::memory_order_relaxed); }
+
+TraceScope::TraceScope(const char *n, cudaStream_t st) : name(n), s(st) {
+    if (!trace_on()) return;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventRecord(a, s) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        a = nullptr;
+    }
+}
+
+TraceScope::~TraceScope() {
+    if (!a) return;
+    cudaEvent_t b = nullptr;
+    if (cudaEventCreate(&b) != cudaSuccess || cudaEventRecord(b, s) != cudaSuccess) {
+        cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        return;
+    }
+    std::lock_guard<std::mutex> g(g_trace_mu);
+    g_trace_pending.push_back({name, a, b});
+}
+
+static void trace_drain() {   // caller holds g_trace_mu; device already synchronised
+    for (auto &r : g_trace_pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+        bool found = false;
+        for (auto &t : g_trace_table)
+            if (strcmp(t.name, r.name) == 0) {
+                t.count += 1;
+                t.ms += ms;
+                found = true;
+                break;
+            }
+        if (!found) g_trace_table.push_back({r.name, 1, (double)ms});
+    }
+    g_trace_pending.clear();
+}
+
+}  // namespace spmv
+
+using namespace spmv;
+
+namespace {
+
+
+spmv_status check_handle(spmv_handle h) {
+    if (!h) {
+        set_error("NULL handle");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    return SPMV_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void free_all(spmv_matrix *h) {
+    void *ptrs[] = {h->coo_row, h->coo_col, h->coo_val, h->row_ptr, h->col, h->val, h->bin_rows,
+                    h->part_row, h->part_nz, h->carry_row, h->carry_val, h->hb_idx, h->hb_val,
+                    h->blk_ptr, h->blk_row, h->blk_col, h->xsplit, h->xsplit_flag, h->status_dev};
+    for (void *p : ptrs) dev_free(p);
+    if (h->status_host) cudaFreeHost(h->status_host);
+}
+
+// Eq. 2 rule (Section 3.1) for the block side: start at 3 + ceil(log2 sqrt(n)) and
+// lower it until beta <= 2^16 and the x slice of one block fits the on-chip budget.
+int default_log2_beta(int64_t n, int x_bytes) {
+    int lg = 0;
+    while (((int64_t)1 << lg) < n) ++lg;
+    int b = 3 + (lg + 1) / 2;
+    const int64_t budget = 200 * 1024;
+    while (b > 4 && (b > 16 || (((int64_t)1 << b) * x_bytes) > budget)) --b;
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *spmv_last_error(void) { return g_err.c_str(); }
+
+const char *spmv_status_string(spmv_status s) {
+    switch (s) {
+        case SPMV_OK: return "SPMV_OK";
+        case SPMV_ERR_INVALID_ARG: return "SPMV_ERR_INVALID_ARG";
+        case SPMV_ERR_INDEX_RANGE: return "SPMV_ERR_INDEX_RANGE";
+        case SPMV_ERR_DUPLICATE: return "SPMV_ERR_DUPLICATE";
+        case SPMV_ERR_OOM: return "SPMV_ERR_OOM";
+        case SPMV_ERR_UNSUPPORTED: return "SPMV_ERR_UNSUPPORTED";
+        case SPMV_ERR_CUDA: return "SPMV_ERR_CUDA";
+        case SPMV_ERR_TIMEOUT: return "SPMV_ERR_TIMEOUT";
+        case SPMV_ERR_NOT_CONVERTED: return "SPMV_ERR_NOT_CONVERTED";
+    }
+    return "SPMV_ERR_UNKNOWN";
+}
+
+// Host-side fault injection for tests: the allocation after `n` more successful ones
+// fails with SPMV_ERR_OOM (n < 0 disables).
+void spmv_test_fail_alloc(long long n) { g_fail_after.store(n); }
+
+spmv_status spmv_trace_enable(int on) {
+    cudaError_t e = cudaDeviceSynchronize();
+    {
+        std::lock_guard<std::mutex> g(g_trace_mu);
+        trace_drain();
+        g_trace_table.clear();
+        g_trace.store(on != 0);
+    }
+    if (e != cudaSuccess) return cuda_status(e, "spmv_trace_enable");
+    return SPMV_OK;
+}
+
+int spmv_trace_read(int max_entries, const char **names, long long *counts, double *total_ms) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+    std::lock_guard<std::mutex> g(g_trace_mu);
+    trace_drain();
+    int n = (int)g_trace_table.size();
+    for (int i = 0; i < n && i < max_entries; ++i) {
+        if (names) names[i] = g_trace_table[i].name;
+        if (counts) counts[i] = g_trace_table[i].count;
+        if (total_ms) total_ms[i] = g_trace_table[i].ms;
+    }
+    return n;
+}
+
+spmv_status spmv_create_coo(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ind, const int32_t *col_ind,
+                            const void *data, spmv_dtype dt, uint32_t flags, void *stream, spmv_handle *out) {
+    g_err.clear();
+    if (!out) {
+        set_error("spmv_create_coo: out is NULL");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (m < 0 || n < 0 || nnz < 0) {
+        set_error("spmv_create_coo: negative size");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    if (m >= ((int64_t)1 << 31) || n >= ((int64_t)1 << 31) || nnz >= ((int64_t)1 << 31)) {
+        set_error("spmv_create_coo: m, n and nnz must be below 2^31 (int32 indices)");
+        return SPMV_ERR_UNSUPPORTED;
+    }
+    if ((int)dt < 0 || (int)dt > 3 || (flags & ~0x3u)) {
+        set_error("spmv_create_coo: unknown dtype or flag");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    if (nnz > 0 && (!row_ind || !col_ind || (dt != SPMV_PATTERN && !data))) {
+        set_error("spmv_create_coo: NULL triplet array");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    const bool dev = (flags & SPMV_DEVICE_PTRS) != 0;
+    if (nnz > 0 && dev && (!is_device_ptr(row_ind) || !is_device_ptr(col_ind) ||
+                           (dt != SPMV_PATTERN && !is_device_ptr(data)))) {
+        set_error("spmv_create_coo: SPMV_DEVICE_PTRS given but an array is not device memory");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    spmv_matrix *h = new (std::nothrow) spmv_matrix();
+    if (!h) {
+        set_error("spmv_create_coo: host allocation failed");
+        return SPMV_ERR_OOM;
+    }
+    h->m = m;
+    h->n = n;
+    h->nnz_in = nnz;
+    h->dt = dt;
+    h->flags = flags;
+    cudaGetDevice(&h->device);
+    const int es = elem_size(dt);
+    spmv_status st = SPMV_OK;
+    auto fail = [&](spmv_status e) {
+        cudaStreamSynchronize(s);
+        free_all(h);
+        delete h;
+        return e;
+    };
+    if ((st = dev_alloc((void **)&h->status_dev, 16, "status word", s)) != SPMV_OK) return fail(st);
+    if (cudaMallocHost((void **)&h->status_host, 16) != cudaSuccess) {
+        h->status_host = nullptr;
+        return fail(cuda_status(cudaErrorMemoryAllocation, "pinned status slot"));
+    }
+    if (cudaMemsetAsync(h->status_dev, 0, 16, s) != cudaSuccess) return fail(cuda_status(cudaGetLastError(), "memset"));
+    if (nnz > 0) {
+        if ((st = dev_alloc((void **)&h->coo_row, (size_t)nnz * 4, "triplet rows", s)) != SPMV_OK ||
+            (st = dev_alloc((void **)&h->coo_col, (size_t)nnz * 4, "triplet cols", s)) != SPMV_OK ||
+            (es && (st = dev_alloc(&h->coo_val, (size_t)nnz * es, "triplet values", s)) != SPMV_OK))
+            return fail(st);
+        cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        cudaError_t e = cudaMemcpyAsync(h->coo_row, row_ind, (size_t)nnz * 4, kind, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->coo_col, col_ind, (size_t)nnz * 4, kind, s);
+        if (e == cudaSuccess && es) e = cudaMemcpyAsync(h->coo_val, data, (size_t)nnz * es, kind, s);
+        if (e != cudaSuccess) return fail(cuda_status(e, "spmv_create_coo copy"));
+        if ((st = launch_validate(h->coo_row, h->coo_col, nnz, m, n, h->status_dev, s)) != SPMV_OK) return fail(st);
+        h->bytes = nnz * (8 + es);
+    }
+    cudaError_t e = cudaMemcpyAsync(h->status_host, h->status_dev, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(cuda_status(e, "spmv_create_coo sync"));
+    if (*h->status_host & ST_INDEX_RANGE) {
+        set_error("spmv_create_coo: a triplet index lies outside [0,m) x [0,n)");
+        return fail(SPMV_ERR_INDEX_RANGE);
+    }
+    *out = h;
+    return SPMV_OK;
+}
+
+spmv_status spmv_convert(spmv_handle h, spmv_format f, const spmv_convert_opts *opt, void *stream) {
+    g_err.clear();
+    SPMV_TRY(check_handle(h));
+    cudaStream_t s = (cudaStream_t)stream;
+    spmv_convert_opts o = {0, SPMV_INNER_HILBERT, 0};
+    if (opt) o = *opt;
+    if (f == SPMV_FMT_AUTO) {
+        // Row-length statistics decide: very long rows favour the merge path (it splits
+        // rows across tiles); otherwise the row-split product.
+        if (!h->has_csr) SPMV_TRY(build_csr(h, s));
+        if (!h->has_bins) SPMV_TRY(build_bins(h, s));
+        f = (h->max_row_len > 4096 || h->nnz > ((int64_t)1 << 20)) ? SPMV_FMT_CSR_MERGE : SPMV_FMT_CSR_ROWSPLIT;
+    }
+    if ((int)f < 0 || (int)f > 2) {
+        set_error("spmv_convert: unknown format");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    if (o.inner_order != SPMV_INNER_HILBERT && o.inner_order != SPMV_INNER_ROWMAJOR) {
+        set_error("spmv_convert: unknown inner order");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    if (o.log2_beta < 0 || o.log2_beta > 16) {
+        set_error("spmv_convert: log2_beta must be in [1, 16] (0 = Eq. 2 rule)");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    if (o.tile != 0 && o.tile != MERGE_TILE_ITEMS) {
+        set_error("spmv_convert: only the default merge tile (1792 path items) is built in");
+        return SPMV_ERR_UNSUPPORTED;
+    }
+    if (!h->has_csr) SPMV_TRY(build_csr(h, s));
+    if (f == SPMV_FMT_CSR_ROWSPLIT && !h->has_bins) SPMV_TRY(build_bins(h, s));
+    if (f == SPMV_FMT_CSR_MERGE && !h->has_merge) SPMV_TRY(build_merge(h, MERGE_TILE_ITEMS, s));
+    if (f != SPMV_FMT_HB) SPMV_TRY(build_df(h, s));
+    if (f == SPMV_FMT_HB) {
+        int lb = o.log2_beta ? o.log2_beta : default_log2_beta(h->n, h->dt == SPMV_F64 ? 8 : 4);
+        const int K = bits_for(std::max<int64_t>(std::max(h->m, h->n), 2));
+        if (lb > K) lb = K;
+        if (!h->has_hb || h->log2beta != lb || h->inner != o.inner_order) SPMV_TRY(build_hb(h, lb, o.inner_order, s));
+    }
+    SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+    h->format = (int32_t)f;
+    return SPMV_OK;
+}
+
+spmv_status spmv_mul(spmv_handle h, const void *x, void *y, spmv_dtype vec_dt, uint32_t accum, void *stream) {
+    SPMV_TRY(check_handle(h));
+    if (h->format < 0) {
+        set_error("spmv_mul: call spmv_convert first");
+        return SPMV_ERR_NOT_CONVERTED;
+    }
+    if ((h->n > 0 && !x) || (h->m > 0 && !y)) {
+        set_error("spmv_mul: NULL vector");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    if (accum > SPMV_ACC_COMPENSATED || (vec_dt != SPMV_F64 && vec_dt != SPMV_F32)) {
+        set_error("spmv_mul: unknown vector dtype or accumulation mode");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    if (accum == SPMV_ACC_COMPENSATED) {
+        set_error("spmv_mul: compensated accumulation is not built in");
+        return SPMV_ERR_UNSUPPORTED;
+    }
+    if (h->m == 0) return SPMV_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (h->format) {
+        case SPMV_FMT_CSR_MERGE: return mul_merge(h, x, y, vec_dt, accum, s);
+        case SPMV_FMT_CSR_ROWSPLIT: return mul_rowsplit(h, x, y, vec_dt, accum, s);
+        case SPMV_FMT_HB: return mul_hb(h, x, y, vec_dt, accum, s);
+    }
+    set_error("spmv_mul: bad format");
+    return SPMV_ERR_INVALID_ARG;
+}
+
+spmv_status spmv_mul_batch(int count, const spmv_handle *hs, int k, const void *const *X, void *const *Y,
+                           spmv_dtype vec_dt, uint32_t accum, void *stream) {
+    if (count < 0 || (count > 0 && (!hs || !X || !Y)) || k < 1 || k > 16) {
+        set_error("spmv_mul_batch: bad arguments");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    if (k != 1) {
+        set_error("spmv_mul_batch: k > 1 is not built in yet");
+        return SPMV_ERR_UNSUPPORTED;
+    }
+    for (int i = 0; i < count; ++i) SPMV_TRY(spmv_mul(hs[i], X[i], Y[i], vec_dt, accum, stream));
+    return SPMV_OK;
+}
+
+spmv_status spmv_destroy(spmv_handle h) {
+    if (!h) return SPMV_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_all(h);
+    delete h;
+    if (e != cudaSuccess) return cuda_status(e, "spmv_destroy");
+    return SPMV_OK;
+}
+
+spmv_status spmv_info(spmv_handle h, spmv_info_t *out) {
+    SPMV_TRY(check_handle(h));
+    if (!out) return SPMV_ERR_INVALID_ARG;
+    memset(out, 0, sizeof *out);
+    out->m = h->m;
+    out->n = h->n;
+    out->nnz = h->has_csr ? h->nnz : h->nnz_in;
+    out->format = h->format;
+    out->dtype = h->dt;
+    out->log2_beta = h->has_hb ? h->log2beta : 0;
+    out->grid_order = h->has_hb ? h->grid_K : 0;
+    out->nblk = h->nblk;
+    out->merge_tiles = h->tiles;
+    out->merge_tile_items = h->tile_items;
+    out->device_bytes = h->bytes;
+    return SPMV_OK;
+}
+
+spmv_status spmv_export_csr(spmv_handle h, int32_t *row_ptr, int32_t *col_ind, void *data) {
+    SPMV_TRY(check_handle(h));
+    if (!h->has_csr) {
+        set_error("spmv_export_csr: no CRS arrays (convert first)");
+        return SPMV_ERR_NOT_CONVERTED;
+    }
+    SPMV_CUDA_TRY(cudaDeviceSynchronize());
+    if (row_ptr) SPMV_CUDA_TRY(cudaMemcpy(row_ptr, h->row_ptr, (size_t)(h->m + 1) * 4, cudaMemcpyDeviceToHost));
+    if (col_ind && h->nnz) SPMV_CUDA_TRY(cudaMemcpy(col_ind, h->col, (size_t)h->nnz * 4, cudaMemcpyDeviceToHost));
+    if (data && h->nnz && elem_size(h->dt))
+        SPMV_CUDA_TRY(cudaMemcpy(data, h->val, (size_t)h->nnz * elem_size(h->dt), cudaMemcpyDeviceToHost));
+    return SPMV_OK;
+}
+
+spmv_status spmv_export_hb(spmv_handle h, uint32_t *idx, void *data, int32_t *blk_ptr, int32_t *blk_row,
+                           int32_t *blk_col) {
+    SPMV_TRY(check_handle(h));
+    if (!h->has_hb) {
+        set_error("spmv_export_hb: no HB arrays (convert first)");
+        return SPMV_ERR_NOT_CONVERTED;
+    }
+    SPMV_CUDA_TRY(cudaDeviceSynchronize());
+    if (idx && h->nnz) SPMV_CUDA_TRY(cudaMemcpy(idx, h->hb_idx, (size_t)h->nnz * 4, cudaMemcpyDeviceToHost));
+    if (data && h->nnz && elem_size(h->dt))
+        SPMV_CUDA_TRY(cudaMemcpy(data, h->hb_val, (size_t)h->nnz * elem_size(h->dt), cudaMemcpyDeviceToHost));
+    if (blk_ptr) SPMV_CUDA_TRY(cudaMemcpy(blk_ptr, h->blk_ptr, (size_t)(h->nblk + 1) * 4, cudaMemcpyDeviceToHost));
+    if (blk_row && h->nblk) SPMV_CUDA_TRY(cudaMemcpy(blk_row, h->blk_row, (size_t)h->nblk * 4, cudaMemcpyDeviceToHost));
+    if (blk_col && h->nblk) SPMV_CUDA_TRY(cudaMemcpy(blk_col, h->blk_col, (size_t)h->nblk * 4, cudaMemcpyDeviceToHost));
+    return SPMV_OK;
+}
+
+spmv_status spmv_export_merge_partition(spmv_handle h, int32_t *row_start, int32_t *nz_start) {
+    SPMV_TRY(check_handle(h));
+    if (!h->has_merge) {
+        set_error("spmv_export_merge_partition: no merge partition (convert to CSR_MERGE first)");
+        return SPMV_ERR_NOT_CONVERTED;
+    }
+    SPMV_CUDA_TRY(cudaDeviceSynchronize());
+    if (row_start) SPMV_CUDA_TRY(cudaMemcpy(row_start, h->part_row, (size_t)(h->tiles + 1) * 4, cudaMemcpyDeviceToHost));
+    if (nz_start) SPMV_CUDA_TRY(cudaMemcpy(nz_start, h->part_nz, (size_t)(h->tiles + 1) * 4, cudaMemcpyDeviceToHost));
+    return SPMV_OK;
+}
+
+spmv_status spmv_hilbert_keys(int K, int64_t n, const int32_t *rows, const int32_t *cols, uint64_t *keys,
+                              void *stream) {
+    if (K < 1 || K > 31 || n < 0 || (n > 0 && (!rows || !cols || !keys))) {
+        set_error("spmv_hilbert_keys: bad arguments");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    return launch_hilbert_keys(K, n, rows, cols, keys, (cudaStream_t)stream);
+}
+
+}  // extern "C"

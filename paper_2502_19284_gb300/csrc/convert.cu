@@ -1,0 +1,628 @@
+// Format conversions (Section 5.1: step 1 sorts the nonzeros into the format's order,
+// step 2 populates and compresses the arrays, touching every element once).
+//
+//   triplets -> CRS (Section 2):  key = (row << cbits) | col, stable LSD radix sort with
+//                                 the input position as payload (so equal pairs keep input
+//                                 order), duplicate resolution, row_ptr by boundary fill.
+//   CRS -> row-length bins        (row-split product, GPU counterpart of ParCRS)
+//   CRS -> merge-path partition   (Section 3.3: split points of the row-end / nonzero path)
+//   CRS -> Hilbert blocked (HB)   (Sections 3.1, 4.2): key = Hilbert index h(r, c) on the
+//                                 2^K grid (or block-then-row-major), radix sort, block
+//                                 segmentation where h >> 2 log2(beta) changes, packed
+//                                 ((r mod beta) << 16) | (c mod beta) indices.
+#include "common.cuh"
+#include "convert.cuh"
+#include "hilbert.cuh"
+#include "df64.cuh"
+
+#include <algorithm>
+
+namespace spmv {
+
+namespace {
+
+constexpr int CB = 256;   // block size of the simple element-wise kernels
+
+inline unsigned grid_for(int64_t n, int per_block = CB) {
+    int64_t g = (n + per_block - 1) / per_block;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 1 << 30));
+}
+
+// ---------------------------------------------------------------- validation
+__global__ void k_validate(const int32_t *__restrict__ row, const int32_t *__restrict__ col, int64_t nnz, int64_t m,
+                           int64_t n, uint32_t *status) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (; i < nnz; i += stride) {
+        int32_t r = row[i], c = col[i];
+        bad |= (r < 0) | ((int64_t)r >= m) | (c < 0) | ((int64_t)c >= n);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_INDEX_RANGE);
+}
+
+// ---------------------------------------------------------------- COO -> CRS
+__global__ void k_coo_keys(const int32_t *__restrict__ row, const int32_t *__restrict__ col, int64_t nnz, int cbits,
+                           uint64_t *__restrict__ keys, uint32_t *__restrict__ perm) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nnz) {
+        keys[i] = ((uint64_t)(uint32_t)row[i] << cbits) | (uint32_t)col[i];
+        perm[i] = (uint32_t)i;
+    }
+}
+
+// head[i] = 1 where a new (row, col) starts; flags a duplicate in *status.
+__global__ void k_heads(const uint64_t *__restrict__ keys, int64_t nnz, uint32_t *__restrict__ head,
+                        uint32_t *status) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool dup = false;
+    if (i < nnz) {
+        bool h = (i == 0) || keys[i] != keys[i - 1];
+        head[i] = h ? 1u : 0u;
+        dup = !h;
+    }
+    if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) atomicOr(status, ST_DUPLICATE);
+}
+
+// dst[i] = src[perm[i]]: GATHER_ILP independent random reads in flight per thread.
+constexpr int GATHER_ILP = 8;
+
+template <typename T>
+__global__ void k_gather(const T *__restrict__ src, const uint32_t *__restrict__ perm, int64_t n, T *__restrict__ dst) {
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x * GATHER_ILP + threadIdx.x;
+    uint32_t p[GATHER_ILP];
+    T v[GATHER_ILP];
+#pragma unroll
+    for (int u = 0; u < GATHER_ILP; ++u) {
+        const int64_t i = base + (int64_t)u * blockDim.x;
+        p[u] = i < n ? perm[i] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < GATHER_ILP; ++u) {
+        const int64_t i = base + (int64_t)u * blockDim.x;
+        if (i < n) v[u] = __ldg(src + p[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < GATHER_ILP; ++u) {
+        const int64_t i = base + (int64_t)u * blockDim.x;
+        if (i < n) dst[i] = v[u];
+    }
+}
+
+__global__ void k_key_cols(const uint64_t *__restrict__ keys, int64_t n, int cbits, int32_t *__restrict__ col) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) col[i] = (int32_t)(keys[i] & ((1ull << cbits) - 1ull));
+}
+
+__device__ __forceinline__ double load_as_double(const void *v, int dt, int64_t i) {
+    if (dt == SPMV_F64) return ((const double *)v)[i];
+    if (dt == SPMV_F32) return (double)((const float *)v)[i];
+    return (double)__bfloat162float(((const __nv_bfloat16 *)v)[i]);
+}
+
+__device__ __forceinline__ void store_from_double(void *v, int dt, int64_t i, double x) {
+    if (dt == SPMV_F64) ((double *)v)[i] = x;
+    else if (dt == SPMV_F32) ((float *)v)[i] = __double2float_rn(x);
+    else ((__nv_bfloat16 *)v)[i] = __double2bfloat16(x);
+}
+
+// Duplicate (row, col) runs: the head writes the compacted key and column and the sum of
+// the run's values in input order (double accumulation, one rounding to the stored type).
+__global__ void k_dup_compact(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ perm,
+                              const uint32_t *__restrict__ head, const uint32_t *__restrict__ pos, int64_t nnz,
+                              int cbits, const void *__restrict__ vin, int dt, uint64_t *__restrict__ ckeys,
+                              int32_t *__restrict__ col, void *__restrict__ vout) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nnz || !head[i]) return;
+    int64_t o = pos[i];
+    ckeys[o] = keys[i];
+    col[o] = (int32_t)(keys[i] & ((1ull << cbits) - 1ull));
+    if (vin) {
+        double s = load_as_double(vin, dt, perm[i]);
+        for (int64_t j = i + 1; j < nnz && !head[j]; ++j) s = s + load_as_double(vin, dt, perm[j]);
+        store_from_double(vout, dt, o, s);
+    }
+}
+
+// row_ptr by boundary fill over the sorted keys: entry i is the first of rows
+// (row(i-1), row(i)]; the sentinel thread i = nnz closes rows (row(nnz-1), m].
+// Gaps longer than GAP_INLINE rows are queued for k_fill_gaps.
+constexpr int GAP_INLINE = 64;
+
+__global__ void k_row_ptr_fill(const uint64_t *__restrict__ keys, int64_t nnz, int cbits, int64_t m,
+                               int32_t *__restrict__ row_ptr, int64_t *__restrict__ gaps,
+                               unsigned long long *__restrict__ ngaps) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > nnz) return;
+    int64_t hi = i < nnz ? (int64_t)(keys[i] >> cbits) : m;
+    int64_t lo = i > 0 ? (int64_t)(keys[i - 1] >> cbits) + 1 : 0;   // rows lo..hi get value i
+    if (hi - lo + 1 <= GAP_INLINE) {
+        for (int64_t r = lo; r <= hi; ++r) row_ptr[r] = (int32_t)i;
+    } else {
+        unsigned long long g = atomicAdd(ngaps, 1ull);
+        gaps[3 * g + 0] = lo;
+        gaps[3 * g + 1] = hi;
+        gaps[3 * g + 2] = i;
+    }
+}
+
+__global__ void k_fill_gaps(const int64_t *__restrict__ gaps, const unsigned long long *__restrict__ ngaps,
+                            int32_t *__restrict__ row_ptr) {
+    const unsigned long long ng = *ngaps;
+    for (unsigned long long g = blockIdx.x; g < ng; g += gridDim.x) {
+        int64_t lo = gaps[3 * g], hi = gaps[3 * g + 1];
+        int32_t v = (int32_t)gaps[3 * g + 2];
+        for (int64_t r = lo + threadIdx.x; r <= hi; r += blockDim.x) row_ptr[r] = v;
+    }
+}
+
+// ---------------------------------------------------------------- row-length bins
+__global__ void k_row_class(const int32_t *__restrict__ row_ptr, int64_t m, uint64_t *__restrict__ cls,
+                            uint32_t *__restrict__ rows, unsigned long long *__restrict__ counts,
+                            unsigned long long *__restrict__ maxlen) {
+    __shared__ unsigned long long sc[NUM_ROW_CLASSES];
+    if (threadIdx.x < NUM_ROW_CLASSES) sc[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long len = 0;
+    if (i < m) {
+        len = (unsigned long long)(row_ptr[i + 1] - row_ptr[i]);
+        int c = row_class(len);
+        cls[i] = (uint64_t)c;
+        rows[i] = (uint32_t)i;
+        atomicAdd(&sc[c], 1ull);
+    }
+    // block max of the row length
+    unsigned long long mx = len;
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(maxlen, mx);
+    __syncthreads();
+    if (threadIdx.x < NUM_ROW_CLASSES && sc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sc[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------- merge partition
+// Split point on diagonal d of the path A = row_ptr[1..m] (row ends) x B = 0..nnz-1
+// (nonzero indices): the largest i <= min(d, m) such that the first i row ends are all
+// consumed within the first d steps, where a tie consumes the row end (Section 3.3).
+__device__ __forceinline__ int64_t merge_split(int64_t d, int64_t m, int64_t nnz, const int32_t *__restrict__ row_ptr) {
+    int64_t lo = d - nnz > 0 ? d - nnz : 0;
+    int64_t hi = d < m ? d : m;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if ((int64_t)row_ptr[mid] <= d - mid) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_merge_partition(const int32_t *__restrict__ row_ptr, int64_t m, int64_t nnz, int64_t tiles,
+                                  int64_t tile_items, int32_t *__restrict__ part_row, int32_t *__restrict__ part_nz) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > tiles) return;
+    int64_t d = min(t * tile_items, m + nnz);
+    int64_t i = merge_split(d, m, nnz, row_ptr);
+    part_row[t] = (int32_t)i;
+    part_nz[t] = (int32_t)(d - i);
+}
+
+// ---------------------------------------------------------------- CRS -> HB
+// Row of each CRS entry by bisection over row_ptr, bracketed per block.
+constexpr int HB_KEY_TILE = 2048;
+
+__device__ __forceinline__ int64_t row_of(const int32_t *__restrict__ row_ptr, int64_t lo, int64_t hi, int64_t k) {
+    // largest r in [lo, hi] with row_ptr[r] <= k
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if ((int64_t)row_ptr[mid] <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int HB_KEY_ROWS = 2048;   // row_ptr slice kept in shared memory per block
+
+__global__ void k_hb_keys(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int64_t m, int64_t nnz,
+                          int K, int log2b, int inner, uint64_t *__restrict__ keys, uint32_t *__restrict__ perm) {
+    __shared__ int64_t br[2];
+    __shared__ int32_t s_rp[HB_KEY_ROWS + 1];
+    __shared__ uint8_t s_fwd2[64], s_inv2[64];
+    if (threadIdx.x < 64) hilbert_tables2(s_fwd2, s_inv2, threadIdx.x);
+    const int64_t e0 = (int64_t)blockIdx.x * HB_KEY_TILE;
+    const int64_t e1 = min(e0 + (int64_t)HB_KEY_TILE, nnz) - 1;
+    if (threadIdx.x < 2) {
+        int64_t e = threadIdx.x == 0 ? e0 : e1;
+        br[threadIdx.x] = row_of(row_ptr, 0, m - 1, e);
+    }
+    __syncthreads();
+    const int64_t rlo = br[0], rhi = br[1];
+    const bool in_smem = rhi - rlo + 1 <= HB_KEY_ROWS;
+    if (in_smem)
+        for (int64_t r = rlo + threadIdx.x; r <= rhi + 1 && r <= m; r += blockDim.x) s_rp[r - rlo] = row_ptr[r];
+    __syncthreads();
+    for (int64_t k = e0 + threadIdx.x; k <= e1; k += blockDim.x) {
+        uint32_t r;
+        if (in_smem) {   // largest r in [rlo, rhi] with row_ptr[r] <= k, searched in shared memory
+            int lo = 0, hi = (int)(rhi - rlo);
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if ((int64_t)s_rp[mid] <= k) lo = mid;
+                else hi = mid - 1;
+            }
+            r = (uint32_t)(rlo + lo);
+        } else {
+            r = (uint32_t)row_of(row_ptr, rlo, rhi, k);
+        }
+        uint32_t c = (uint32_t)col[k];
+        uint64_t h;
+        if (inner == SPMV_INNER_ROWMAJOR) {
+            uint64_t blk = hilbert_key2(K - log2b, r >> log2b, c >> log2b, s_fwd2);
+            uint32_t mask = (1u << log2b) - 1u;
+            h = (blk << (2 * log2b)) | ((uint64_t)(r & mask) << log2b) | (uint64_t)(c & mask);
+        } else {
+            h = hilbert_key2(K, r, c, s_fwd2);
+        }
+        keys[k] = h;
+        perm[k] = (uint32_t)k;
+    }
+}
+
+__device__ __forceinline__ void hb_cell(uint64_t key, int K, int log2b, int inner, uint32_t *r, uint32_t *c,
+                                        const uint8_t *inv2) {
+    if (inner == SPMV_INNER_ROWMAJOR) {
+        uint32_t br, bc;
+        hilbert_cell2(K - log2b, key >> (2 * log2b), &br, &bc, inv2);
+        uint32_t mask = (1u << log2b) - 1u;
+        *r = (br << log2b) | (uint32_t)((key >> log2b) & mask);
+        *c = (bc << log2b) | (uint32_t)(key & mask);
+    } else {
+        hilbert_cell2(K, key, r, c, inv2);
+    }
+}
+
+// Populate: packed in-block index, block-start flags.
+__global__ void k_hb_fill(const uint64_t *__restrict__ keys, int64_t nnz, int K, int log2b, int inner,
+                          uint32_t *__restrict__ idx, uint32_t *__restrict__ head) {
+    __shared__ uint8_t s_fwd2[64], s_inv2[64];
+    if (threadIdx.x < 64) hilbert_tables2(s_fwd2, s_inv2, threadIdx.x);
+    __syncthreads();
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nnz) return;
+    uint64_t key = keys[t];
+    uint32_t r, c;
+    hb_cell(key, K, log2b, inner, &r, &c, s_inv2);
+    uint32_t mask = (1u << log2b) - 1u;
+    idx[t] = ((r & mask) << 16) | (c & mask);
+    head[t] = (t == 0 || (keys[t - 1] >> (2 * log2b)) != (key >> (2 * log2b))) ? 1u : 0u;
+}
+
+__global__ void k_hb_blocks(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ head,
+                            const uint32_t *__restrict__ bid, int64_t nnz, int K, int log2b, int inner,
+                            int32_t *__restrict__ blk_ptr, int32_t *__restrict__ blk_row,
+                            int32_t *__restrict__ blk_col) {
+    __shared__ uint8_t s_fwd2[64], s_inv2[64];
+    if (threadIdx.x < 64) hilbert_tables2(s_fwd2, s_inv2, threadIdx.x);
+    __syncthreads();
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nnz || !head[t]) return;
+    uint32_t r, c;
+    hb_cell(keys[t], K, log2b, inner, &r, &c, s_inv2);
+    uint32_t b = bid[t];
+    blk_ptr[b] = (int32_t)t;
+    blk_row[b] = (int32_t)(r >> log2b);
+    blk_col[b] = (int32_t)(c >> log2b);
+}
+
+__global__ void k_hilbert_keys(int K, int64_t n, const int32_t *__restrict__ rows, const int32_t *__restrict__ cols,
+                               uint64_t *__restrict__ keys) {
+    __shared__ uint8_t s_fwd2[64], s_inv2[64];
+    if (threadIdx.x < 64) hilbert_tables2(s_fwd2, s_inv2, threadIdx.x);
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const uint64_t h = hilbert_key2(K, (uint32_t)rows[i], (uint32_t)cols[i], s_fwd2);
+        uint32_t r, c;
+        hilbert_cell2(K, h, &r, &c, s_inv2);   // the inverse must return the cell
+        keys[i] = (r == (uint32_t)rows[i] && c == (uint32_t)cols[i]) ? h : ~0ull;
+    }
+}
+
+// ---------------------------------------------------------------- double-float window
+__global__ void k_df_window(const double *__restrict__ v, int64_t n, uint32_t *__restrict__ flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (; i < n; i += stride) {
+        float h, l;
+        bad |= !df_split(v[i], &h, &l);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+// ---------------------------------------------------------------- helpers
+spmv_status read_status(spmv_matrix *h, cudaStream_t s, uint32_t *out) {
+    SPMV_CUDA_TRY(cudaMemcpyAsync(h->status_host, h->status_dev, 4, cudaMemcpyDeviceToHost, s));
+    SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = *h->status_host;
+    return SPMV_OK;
+}
+
+template <typename T>
+void launch_gather(const void *src, const uint32_t *perm, int64_t n, void *dst, cudaStream_t s) {
+    SPMV_LAUNCH("k_gather", s, (k_gather<T><<<grid_for(n, CB * GATHER_ILP), CB, 0, s>>>((const T *)src, perm, n, (T *)dst)));
+}
+
+spmv_status gather_values(const void *src, spmv_dtype dt, const uint32_t *perm, int64_t n, void *dst, cudaStream_t s) {
+    switch (elem_size(dt)) {
+        case 8: launch_gather<uint64_t>(src, perm, n, dst, s); break;
+        case 4: launch_gather<uint32_t>(src, perm, n, dst, s); break;
+        case 2: launch_gather<uint16_t>(src, perm, n, dst, s); break;
+        default: return SPMV_OK;
+    }
+    SPMV_LAUNCH_CHECK("gather");
+    return SPMV_OK;
+}
+
+spmv_status fill_row_ptr(const uint64_t *keys, int64_t nnz, int cbits, int64_t m, int32_t *row_ptr, cudaStream_t s) {
+    DevBuf gaps(s), ngaps(s);
+    int64_t cap = (m + 1) / GAP_INLINE + 2;
+    SPMV_TRY(gaps.alloc((size_t)cap * 3 * sizeof(int64_t), "row_ptr gaps"));
+    SPMV_TRY(ngaps.alloc(sizeof(unsigned long long), "row_ptr gap count"));
+    SPMV_CUDA_TRY(cudaMemsetAsync(ngaps.p, 0, sizeof(unsigned long long), s));
+    SPMV_LAUNCH("k_row_ptr_fill", s, (k_row_ptr_fill<<<grid_for(nnz + 1), CB, 0, s>>>(keys, nnz, cbits, m, row_ptr, gaps.as<int64_t>(),
+                                                    ngaps.as<unsigned long long>())));
+    SPMV_LAUNCH_CHECK("row_ptr fill");
+    SPMV_LAUNCH("k_fill_gaps", s, (k_fill_gaps<<<1184, CB, 0, s>>>(gaps.as<int64_t>(), ngaps.as<unsigned long long>(), row_ptr)));
+    SPMV_LAUNCH_CHECK("row_ptr gaps");
+    return SPMV_OK;
+}
+
+}  // namespace
+
+spmv_status launch_validate(const int32_t *row, const int32_t *col, int64_t nnz, int64_t m, int64_t n,
+                            uint32_t *status, cudaStream_t s) {
+    if (nnz <= 0) return SPMV_OK;
+    SPMV_LAUNCH("k_validate", s, (k_validate<<<grid_for(nnz, CB * 8), CB, 0, s>>>(row, col, nnz, m, n, status)));
+    SPMV_LAUNCH_CHECK("validate");
+    return SPMV_OK;
+}
+
+spmv_status launch_hilbert_keys(int K, int64_t n, const int32_t *rows, const int32_t *cols, uint64_t *keys,
+                                cudaStream_t s) {
+    if (n <= 0) return SPMV_OK;
+    SPMV_LAUNCH("k_hilbert_keys", s, (k_hilbert_keys<<<grid_for(n), CB, 0, s>>>(K, n, rows, cols, keys)));
+    SPMV_LAUNCH_CHECK("hilbert keys");
+    return SPMV_OK;
+}
+
+spmv_status build_csr(spmv_matrix *h, cudaStream_t s) {
+    const int64_t m = h->m, nnz = h->nnz_in;
+    const int es = elem_size(h->dt);
+    DevBuf row_ptr(s), col(s), val(s);
+    SPMV_TRY(row_ptr.alloc((size_t)(m + 1) * 4, "row_ptr"));
+    int64_t nout = 0;
+    if (nnz == 0) {
+        SPMV_CUDA_TRY(cudaMemsetAsync(row_ptr.p, 0, (size_t)(m + 1) * 4, s));
+    } else {
+        const int cbits = bits_for(h->n), rbits = bits_for(h->m);
+        DevBuf keys(s), keys_alt(s), perm(s), perm_alt(s), head(s), tmp(s);
+        SPMV_TRY(keys.alloc((size_t)nnz * 8, "sort keys"));
+        SPMV_TRY(keys_alt.alloc((size_t)nnz * 8, "sort keys"));
+        SPMV_TRY(perm.alloc((size_t)nnz * 4, "sort perm"));
+        SPMV_TRY(perm_alt.alloc((size_t)nnz * 4, "sort perm"));
+        SPMV_TRY(head.alloc((size_t)nnz * 4, "heads"));
+        SPMV_TRY(tmp.alloc(std::max(radix_temp_bytes(nnz), scan_temp_bytes(nnz)), "sort temp"));
+        SPMV_LAUNCH("k_coo_keys", s, (k_coo_keys<<<grid_for(nnz), CB, 0, s>>>(h->coo_row, h->coo_col, nnz, cbits, keys.as<uint64_t>(),
+                                                perm.as<uint32_t>())));
+        SPMV_LAUNCH_CHECK("coo keys");
+        bool alt = false;
+        SPMV_TRY(radix_sort_pairs(keys.as<uint64_t>(), keys_alt.as<uint64_t>(), perm.as<uint32_t>(),
+                                  perm_alt.as<uint32_t>(), nnz, 0, cbits + rbits, tmp.p, s, &alt));
+        uint64_t *K = alt ? keys_alt.as<uint64_t>() : keys.as<uint64_t>();
+        uint32_t *P = alt ? perm_alt.as<uint32_t>() : perm.as<uint32_t>();
+        uint64_t *Kspare = alt ? keys.as<uint64_t>() : keys_alt.as<uint64_t>();
+        uint32_t *Pspare = alt ? perm.as<uint32_t>() : perm_alt.as<uint32_t>();
+        SPMV_CUDA_TRY(cudaMemsetAsync(h->status_dev, 0, 4, s));
+        SPMV_LAUNCH("k_heads", s, (k_heads<<<grid_for(nnz), CB, 0, s>>>(K, nnz, head.as<uint32_t>(), h->status_dev)));
+        SPMV_LAUNCH_CHECK("heads");
+        uint32_t stw = 0;
+        SPMV_TRY(read_status(h, s, &stw));
+        uint64_t *rowkeys = K;
+        if (stw & ST_DUPLICATE) {
+            if (h->flags & SPMV_DUP_ERROR) {
+                set_error("spmv_convert: duplicate (row, col) entries with SPMV_DUP_ERROR");
+                return SPMV_ERR_DUPLICATE;
+            }
+            uint32_t *pos = Pspare;
+            SPMV_TRY(exclusive_scan_u32(head.as<uint32_t>(), pos, nnz, tmp.p, s));
+            uint32_t last[2] = {0, 0};
+            SPMV_CUDA_TRY(cudaMemcpyAsync(&last[0], pos + nnz - 1, 4, cudaMemcpyDeviceToHost, s));
+            SPMV_CUDA_TRY(cudaMemcpyAsync(&last[1], head.as<uint32_t>() + nnz - 1, 4, cudaMemcpyDeviceToHost, s));
+            SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+            nout = (int64_t)last[0] + last[1];
+            SPMV_TRY(col.alloc((size_t)nout * 4, "col_ind"));
+            if (es) SPMV_TRY(val.alloc((size_t)nout * es, "values"));
+            SPMV_LAUNCH("k_dup_compact", s, (k_dup_compact<<<grid_for(nnz), CB, 0, s>>>(K, P, head.as<uint32_t>(), pos, nnz, cbits,
+                                                       es ? h->coo_val : nullptr, h->dt, Kspare,
+                                                       col.as<int32_t>(), val.p)));
+            SPMV_LAUNCH_CHECK("dup compact");
+            rowkeys = Kspare;
+        } else {
+            nout = nnz;
+            SPMV_TRY(col.alloc((size_t)nnz * 4, "col_ind"));
+            if (es) SPMV_TRY(val.alloc((size_t)nnz * es, "values"));
+            SPMV_LAUNCH("k_key_cols", s, (k_key_cols<<<grid_for(nnz), CB, 0, s>>>(K, nnz, cbits, col.as<int32_t>())));
+            SPMV_LAUNCH_CHECK("key cols");
+            if (es) SPMV_TRY(gather_values(h->coo_val, h->dt, P, nnz, val.p, s));
+        }
+        SPMV_TRY(fill_row_ptr(rowkeys, nout, cbits, m, row_ptr.as<int32_t>(), s));
+    }
+    h->row_ptr = (int32_t *)row_ptr.release();
+    h->col = (int32_t *)col.release();
+    h->val = val.release();
+    h->nnz = nout;
+    h->has_csr = true;
+    h->bytes += (m + 1) * 4 + nout * (4 + es);
+    // the triplet copy is no longer needed
+    if (h->coo_row) dev_free_async(h->coo_row, s);
+    if (h->coo_col) dev_free_async(h->coo_col, s);
+    if (h->coo_val) dev_free_async(h->coo_val, s);
+    if (nnz) h->bytes -= nnz * (8 + es);
+    h->coo_row = h->coo_col = nullptr;
+    h->coo_val = nullptr;
+    return SPMV_OK;
+}
+
+spmv_status build_df(spmv_matrix *h, cudaStream_t s) {
+    if (h->df_checked) return SPMV_OK;
+    h->df_checked = true;
+    h->df_ok = false;
+    if (h->dt != SPMV_F64) return SPMV_OK;
+    DevBuf xs(s), fl(s);
+    SPMV_TRY(xs.alloc((size_t)std::max<int64_t>(h->n, 1) * sizeof(float2), "x split"));
+    SPMV_TRY(fl.alloc(16, "x split flag"));
+    SPMV_CUDA_TRY(cudaMemsetAsync(h->status_dev + 2, 0, 4, s));
+    if (h->nnz > 0)
+        SPMV_LAUNCH("k_df_window", s,
+                    (k_df_window<<<grid_for(h->nnz, CB * 8), CB, 0, s>>>((const double *)h->val, h->nnz, h->status_dev + 2)));
+    SPMV_LAUNCH_CHECK("df window");
+    SPMV_CUDA_TRY(cudaMemcpyAsync(h->status_host + 2, h->status_dev + 2, 4, cudaMemcpyDeviceToHost, s));
+    SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+    h->df_ok = h->status_host[2] == 0;
+    h->xsplit = (float2 *)xs.release();
+    h->xsplit_flag = (uint32_t *)fl.release();
+    h->bytes += std::max<int64_t>(h->n, 1) * 8 + 16;
+    return SPMV_OK;
+}
+
+spmv_status build_bins(spmv_matrix *h, cudaStream_t s) {
+    const int64_t m = h->m;
+    for (int c = 0; c < 8; ++c) h->bin_count[c] = 0;
+    h->max_row_len = 0;
+    if (m == 0) {
+        h->has_bins = true;
+        return SPMV_OK;
+    }
+    DevBuf cls(s), cls_alt(s), rows(s), rows_alt(s), counts(s), tmp(s), bin_rows(s);
+    SPMV_TRY(cls.alloc((size_t)m * 8, "row class"));
+    SPMV_TRY(cls_alt.alloc((size_t)m * 8, "row class"));
+    SPMV_TRY(rows.alloc((size_t)m * 4, "row ids"));
+    SPMV_TRY(rows_alt.alloc((size_t)m * 4, "row ids"));
+    SPMV_TRY(counts.alloc(16 * sizeof(unsigned long long), "class counts"));
+    SPMV_TRY(tmp.alloc(radix_temp_bytes(m), "sort temp"));
+    SPMV_TRY(bin_rows.alloc((size_t)m * 4, "bin rows"));
+    SPMV_CUDA_TRY(cudaMemsetAsync(counts.p, 0, 16 * sizeof(unsigned long long), s));
+    SPMV_LAUNCH("k_row_class", s, (k_row_class<<<grid_for(m), CB, 0, s>>>(h->row_ptr, m, cls.as<uint64_t>(), rows.as<uint32_t>(),
+                                           counts.as<unsigned long long>(), counts.as<unsigned long long>() + 8)));
+    SPMV_LAUNCH_CHECK("row class");
+    bool alt = false;
+    SPMV_TRY(radix_sort_pairs(cls.as<uint64_t>(), cls_alt.as<uint64_t>(), rows.as<uint32_t>(), rows_alt.as<uint32_t>(),
+                              m, 0, 3, tmp.p, s, &alt));
+    SPMV_CUDA_TRY(cudaMemcpyAsync(bin_rows.p, alt ? rows_alt.p : rows.p, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
+    unsigned long long hc[16];
+    SPMV_CUDA_TRY(cudaMemcpyAsync(hc, counts.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int c = 0; c < 8; ++c) h->bin_count[c] = (int64_t)hc[c];
+    h->max_row_len = (int64_t)hc[8];
+    if (h->bin_rows) dev_free_async(h->bin_rows, s);
+    else h->bytes += m * 4;
+    h->bin_rows = (int32_t *)bin_rows.release();
+    h->has_bins = true;
+    return SPMV_OK;
+}
+
+spmv_status build_merge(spmv_matrix *h, int tile_items, cudaStream_t s) {
+    const int64_t total = h->m + h->nnz;
+    const int64_t tiles = std::max<int64_t>(1, (total + tile_items - 1) / tile_items);
+    DevBuf pr(s), pn(s), cr(s), cv(s);
+    SPMV_TRY(pr.alloc((size_t)(tiles + 1) * 4, "merge partition"));
+    SPMV_TRY(pn.alloc((size_t)(tiles + 1) * 4, "merge partition"));
+    SPMV_TRY(cr.alloc((size_t)tiles * 4, "merge carries"));
+    SPMV_TRY(cv.alloc((size_t)tiles * 8, "merge carries"));
+    SPMV_LAUNCH("k_merge_partition", s, (k_merge_partition<<<grid_for(tiles + 1), CB, 0, s>>>(h->row_ptr, h->m, h->nnz, tiles, tile_items,
+                                                         pr.as<int32_t>(), pn.as<int32_t>())));
+    SPMV_LAUNCH_CHECK("merge partition");
+    if (h->has_merge) {
+        dev_free_async(h->part_row, s); dev_free_async(h->part_nz, s);
+        dev_free_async(h->carry_row, s); dev_free_async(h->carry_val, s);
+        h->bytes -= (h->tiles + 1) * 8 + h->tiles * 12;
+    }
+    h->part_row = (int32_t *)pr.release();
+    h->part_nz = (int32_t *)pn.release();
+    h->carry_row = (int32_t *)cr.release();
+    h->carry_val = (double *)cv.release();
+    h->tiles = tiles;
+    h->tile_items = tile_items;
+    h->has_merge = true;
+    h->bytes += (tiles + 1) * 8 + tiles * 12;
+    return SPMV_OK;
+}
+
+spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s) {
+    const int64_t m = h->m, n = h->n, nnz = h->nnz;
+    const int es = elem_size(h->dt);
+    const int K = bits_for(std::max<int64_t>(std::max(m, n), 2));
+    if (log2b > K) log2b = K;
+    DevBuf idx(s), val(s), bptr(s), brow(s), bcol(s);
+    int64_t nblk = 0;
+    if (nnz > 0) {
+        DevBuf keys(s), keys_alt(s), perm(s), perm_alt(s), head(s), bid(s), tmp(s);
+        SPMV_TRY(keys.alloc((size_t)nnz * 8, "hb keys"));
+        SPMV_TRY(keys_alt.alloc((size_t)nnz * 8, "hb keys"));
+        SPMV_TRY(perm.alloc((size_t)nnz * 4, "hb perm"));
+        SPMV_TRY(perm_alt.alloc((size_t)nnz * 4, "hb perm"));
+        SPMV_TRY(head.alloc((size_t)nnz * 4, "hb heads"));
+        SPMV_TRY(bid.alloc((size_t)nnz * 4, "hb block ids"));
+        SPMV_TRY(tmp.alloc(std::max(radix_temp_bytes(nnz), scan_temp_bytes(nnz)), "hb sort temp"));
+        SPMV_TRY(idx.alloc((size_t)nnz * 4, "hb idx"));
+        if (es) SPMV_TRY(val.alloc((size_t)nnz * es, "hb values"));
+        const int64_t ktiles = (nnz + HB_KEY_TILE - 1) / HB_KEY_TILE;
+        SPMV_LAUNCH("k_hb_keys", s, (k_hb_keys<<<(unsigned)ktiles, CB, 0, s>>>(h->row_ptr, h->col, m, nnz, K, log2b, inner, keys.as<uint64_t>(),
+                                                  perm.as<uint32_t>())));
+        SPMV_LAUNCH_CHECK("hb keys");
+        bool alt = false;
+        SPMV_TRY(radix_sort_pairs(keys.as<uint64_t>(), keys_alt.as<uint64_t>(), perm.as<uint32_t>(),
+                                  perm_alt.as<uint32_t>(), nnz, 0, 2 * K, tmp.p, s, &alt));
+        uint64_t *Ks = alt ? keys_alt.as<uint64_t>() : keys.as<uint64_t>();
+        uint32_t *Ps = alt ? perm_alt.as<uint32_t>() : perm.as<uint32_t>();
+        SPMV_LAUNCH("k_hb_fill", s, (k_hb_fill<<<grid_for(nnz), CB, 0, s>>>(Ks, nnz, K, log2b, inner, idx.as<uint32_t>(), head.as<uint32_t>())));
+        SPMV_LAUNCH_CHECK("hb fill");
+        if (es) SPMV_TRY(gather_values(h->val, h->dt, Ps, nnz, val.p, s));
+        SPMV_TRY(exclusive_scan_u32(head.as<uint32_t>(), bid.as<uint32_t>(), nnz, tmp.p, s));
+        uint32_t last[2] = {0, 0};
+        SPMV_CUDA_TRY(cudaMemcpyAsync(&last[0], bid.as<uint32_t>() + nnz - 1, 4, cudaMemcpyDeviceToHost, s));
+        SPMV_CUDA_TRY(cudaMemcpyAsync(&last[1], head.as<uint32_t>() + nnz - 1, 4, cudaMemcpyDeviceToHost, s));
+        SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+        nblk = (int64_t)last[0] + last[1];
+        SPMV_TRY(bptr.alloc((size_t)(nblk + 1) * 4, "hb blk_ptr"));
+        SPMV_TRY(brow.alloc((size_t)nblk * 4, "hb blk_row"));
+        SPMV_TRY(bcol.alloc((size_t)nblk * 4, "hb blk_col"));
+        SPMV_LAUNCH("k_hb_blocks", s, (k_hb_blocks<<<grid_for(nnz), CB, 0, s>>>(Ks, head.as<uint32_t>(), bid.as<uint32_t>(), nnz, K, log2b, inner,
+                                                 bptr.as<int32_t>(), brow.as<int32_t>(), bcol.as<int32_t>())));
+        SPMV_LAUNCH_CHECK("hb blocks");
+        *h->status_host = (uint32_t)nnz;   // pinned staging slot for the tail entry
+        SPMV_CUDA_TRY(cudaMemcpyAsync(bptr.as<int32_t>() + nblk, h->status_host, 4, cudaMemcpyHostToDevice, s));
+        SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+    } else {
+        SPMV_TRY(bptr.alloc(4, "hb blk_ptr"));
+        SPMV_CUDA_TRY(cudaMemsetAsync(bptr.p, 0, 4, s));
+    }
+    if (h->has_hb) {
+        dev_free_async(h->hb_idx, s); dev_free_async(h->hb_val, s); dev_free_async(h->blk_ptr, s);
+        dev_free_async(h->blk_row, s); dev_free_async(h->blk_col, s);
+        h->bytes -= h->nnz * (4 + es) + h->nblk * 12 + 4;
+    }
+    h->hb_idx = (uint32_t *)idx.release();
+    h->hb_val = val.release();
+    h->blk_ptr = (int32_t *)bptr.release();
+    h->blk_row = (int32_t *)brow.release();
+    h->blk_col = (int32_t *)bcol.release();
+    h->nblk = nblk;
+    h->log2beta = log2b;
+    h->grid_K = K;
+    h->inner = inner;
+    h->has_hb = true;
+    h->bytes += nnz * (4 + es) + nblk * 12 + 4;
+    return SPMV_OK;
+}
+
+}  // namespace spmv

@@ -1,0 +1,49 @@
+// Declarations shared between the conversion and product translation units.
+#pragma once
+#include "common.cuh"
+
+namespace spmv {
+
+// Row-length classes of the row-split product.  Class c < 6 serves rows with
+// length <= CLASS_MAX_LEN[c] using CLASS_LANES[c] lanes per row (several rows per
+// warp); class 6 serves longer rows with a whole CTA per row.
+constexpr int NUM_ROW_CLASSES = 7;
+
+// Merge-path product: a CTA of MERGE_BLOCK threads walks MERGE_TILE_ITEMS path items
+// (row ends + nonzeros), MERGE_IPT per thread.  MERGE_IPT is odd so that consecutive
+// threads' shared-memory walks start in different banks.
+constexpr int MERGE_BLOCK = 256;
+constexpr int MERGE_IPT = 7;
+constexpr int MERGE_TILE_ITEMS = MERGE_BLOCK * MERGE_IPT;
+
+__host__ __device__ __forceinline__ int class_lanes(int c) {
+    return c == 0 ? 1 : c == 1 ? 2 : c == 2 ? 4 : c == 3 ? 8 : c == 4 ? 16 : 32;
+}
+
+__host__ __device__ __forceinline__ int row_class(unsigned long long len) {
+    if (len <= 2) return 0;
+    if (len <= 4) return 1;
+    if (len <= 8) return 2;
+    if (len <= 16) return 3;
+    if (len <= 32) return 4;
+    if (len <= 2048) return 5;
+    return 6;
+}
+
+spmv_status launch_validate(const int32_t *row, const int32_t *col, int64_t nnz, int64_t m, int64_t n,
+                            uint32_t *status, cudaStream_t s);
+spmv_status build_csr(spmv_matrix *h, cudaStream_t s);
+spmv_status build_bins(spmv_matrix *h, cudaStream_t s);
+spmv_status build_merge(spmv_matrix *h, int tile_items, cudaStream_t s);
+spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s);
+// FP64 matrices: check the double-float window of the stored values and allocate the
+// x-split scratch (n float pairs + a flag word).
+spmv_status build_df(spmv_matrix *h, cudaStream_t s);
+
+// products (spmv.cu)
+spmv_status mul_merge(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s);
+// (the FP64 products use double-float arithmetic when acc == SPMV_ACC_DEFAULT and h->df_ok)
+spmv_status mul_rowsplit(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s);
+spmv_status mul_hb(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s);
+
+}  // namespace spmv

@@ -1,0 +1,584 @@
+// SpMV products y := A x on sm_103a.
+//
+//   merge   Merge-based CRS SpMV (Section 3.3).  The path of row ends (A = row_ptr[1..m])
+//           and nonzero indices (B = 0..nnz-1) is cut into equal CTA tiles by the
+//           partition built at conversion.  Inside a tile: (1) products data[k]*x[col[k]]
+//           are formed with coalesced loads into shared memory, row ends staged likewise;
+//           (2) every thread walks an equal share of the tile's path (the same merge rule,
+//           one level down), writing finished rows and keeping (row, temp) as its carry;
+//           (3) thread carries are added to the row that finishes after them, in thread
+//           order; the tile's trailing partial row becomes the tile carry; (4) the tile's
+//           finished rows are stored coalesced.  A second kernel adds the tile carries in
+//           tile order (Section 3.3 adds the per-thread carries sequentially afterwards).
+//   rowsplit  CRS with rows grouped by length class (conversion), G lanes per row
+//           (G = 1..32) or a whole CTA for long rows; lane-strided sums reduced by a
+//           butterfly of warp shuffles.  GPU counterpart of the row-parallel ParCRS.
+//   hb      Hilbert-ordered blocked format (Section 4.2): CTAs take equal ranges of the
+//           Hilbert-sorted nonzeros; each entry's block is found in a shared-memory copy of
+//           the range's block table, products are accumulated into y (zeroed first) with
+//           global atomics.
+//
+// All three are memory-bound (about 0.17 flop per byte in FP64); none uses tensor cores.
+#include "common.cuh"
+#include "convert.cuh"
+#include "df64.cuh"
+
+#include <algorithm>
+
+namespace spmv {
+
+namespace {
+
+// ---------------------------------------------------------------- element access
+struct Pattern {};   // value type tag of a pattern matrix (every stored value is 1)
+
+template <typename VT, typename AT>
+__device__ __forceinline__ AT ld_val(const VT *__restrict__ v, int64_t k) {
+    if constexpr (std::is_same<VT, Pattern>::value) {
+        return AT(1);
+    } else if constexpr (std::is_same<VT, __nv_bfloat16>::value) {
+        return AT(__bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16 *>(v) + k)));
+    } else {
+        return AT(__ldg(v + k));
+    }
+}
+
+template <typename XT, typename AT>
+__device__ __forceinline__ AT ld_x(const XT *__restrict__ x, int64_t j) {
+    return AT(__ldg(x + j));
+}
+
+inline unsigned cdivu(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ================================================================ merge path
+constexpr int MP_BLOCK = MERGE_BLOCK;
+
+// Accumulators.  NativeAcc<AT> sums in AT with one fma per nonzero.  DfAcc keeps an FP64
+// sum as a float pair (double-float, df64.cuh) so that the FP64 path runs on the FP32
+// pipes; its operands arrive already split into (hi, lo) floats.
+template <typename AT>
+struct NativeAcc {
+    using Op = AT;   // operand type of one side of a product
+    AT v;
+    __device__ __forceinline__ void zero() { v = AT(0); }
+    __device__ __forceinline__ void mad(Op a, Op x) { v = fma(a, x, v); }
+    __device__ __forceinline__ void add(const NativeAcc &o) { v = v + o.v; }
+    __device__ __forceinline__ NativeAcc shfl_up(int o) const { NativeAcc r; r.v = __shfl_up_sync(0xffffffffu, v, o); return r; }
+    __device__ __forceinline__ double to_double() const { return (double)v; }
+    template <typename XT> __device__ __forceinline__ XT out() const { return XT(v); }
+};
+
+struct DfAcc {
+    using Op = float2;
+    float s, c;
+    __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
+    __device__ __forceinline__ void mad(float2 a, float2 x) { df_fma(a.x, a.y, x.x, x.y, s, c); }
+    __device__ __forceinline__ void add(const DfAcc &o) { df_add(s, c, o.s, o.c); }
+    __device__ __forceinline__ DfAcc shfl_up(int o) const {
+        DfAcc r;
+        r.s = __shfl_up_sync(0xffffffffu, s, o);
+        r.c = __shfl_up_sync(0xffffffffu, c, o);
+        return r;
+    }
+    __device__ __forceinline__ double to_double() const { return df_to_double(s, c); }
+    template <typename XT> __device__ __forceinline__ XT out() const { return XT(df_to_double(s, c)); }
+};
+
+// Operand loaders: native (value converted to AT) or split into double-float pairs.
+template <typename VT, typename AT>
+struct NativeLoad {
+    __device__ __forceinline__ static AT val(const VT *v, int64_t k) { return ld_val<VT, AT>(v, k); }
+    template <typename XT> __device__ __forceinline__ static AT xg(const XT *x, int64_t j) { return ld_x<XT, AT>(x, j); }
+};
+struct DfLoad {   // values: FP64 split on the fly; x: pre-split float pairs
+    __device__ __forceinline__ static float2 val(const double *v, int64_t k) {
+        float2 r;
+        df_split(__ldg(v + k), &r.x, &r.y);
+        return r;
+    }
+    __device__ __forceinline__ static float2 xg(const float2 *x2, int64_t j) { return __ldg(x2 + j); }
+};
+
+// One merge-path tile (Section 3.3).  Only row ends and finished rows are staged in shared
+// memory.  Each thread locates both ends of its share of the tile's path, loads the values
+// and column indices of its contiguous nonzero range into registers, gathers x, and walks
+// the range nonzero by nonzero (one multiply-add each), emitting every row end met on the
+// way.  Carries: a run of threads ending in the same row forms one segment whose sum (in
+// thread order) goes to the row finished right after the run, or becomes the tile's carry
+// when the run is the tile's trailing partial row.  Runs of up to 8 threads (the common
+// case) are summed sequentially by their last thread; only a tile holding a longer run (a
+// row spanning many threads) uses a segmented scan.
+template <typename Acc, typename Load, typename VT, typename XG, typename XT, int IPT>
+__device__ __forceinline__ void merge_tile(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                                           const VT *__restrict__ val, const XG *__restrict__ xg, XT *__restrict__ y,
+                                           const int32_t *__restrict__ part_row, const int32_t *__restrict__ part_nz,
+                                           int32_t *__restrict__ carry_row, double *__restrict__ carry_val,
+                                           unsigned char *smem_raw) {
+    using Op = typename Acc::Op;
+    constexpr int TILE = MP_BLOCK * IPT;
+    const int t = blockIdx.x;
+    const int64_t i0 = part_row[t], j0 = part_nz[t];
+    const int nrows = (int)(part_row[t + 1] - i0);
+    const int nnzt = (int)(part_nz[t + 1] - j0);
+    Acc *s_yl = (Acc *)smem_raw;                                   // TILE finished rows
+    int32_t *s_rowend = (int32_t *)(s_yl + TILE);                  // TILE row ends (tile-relative)
+    int32_t *s_crow = s_rowend + TILE;                             // thread carry rows + warp flags
+    Acc *s_cval = (Acc *)(s_crow + MP_BLOCK + 32);                 // thread + warp sums
+    for (int r = threadIdx.x; r < nrows; r += MP_BLOCK) s_rowend[r] = __ldg(row_ptr + i0 + r + 1) - (int32_t)j0;
+    __syncthreads();
+
+    const int total = nrows + nnzt;
+    auto split = [&](int d) {   // row ends consumed on diagonal d of the tile's path
+        int lo = max(0, d - nnzt), hi = min(d, nrows);
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (s_rowend[mid - 1] <= d - mid) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    };
+    const int d0 = min((int)threadIdx.x * IPT, total);
+    const int d1 = min(d0 + IPT, total);
+    int i = split(d0);
+    const int iend = split(d1);
+    const int jb = d0 - i, cnt = (d1 - iend) - jb;   // nonzeros [jb, jb + cnt) of the tile
+
+    int32_t c[IPT];
+    Op a[IPT], xv[IPT];
+#pragma unroll
+    for (int u = 0; u < IPT; ++u)
+        if (u < cnt) {
+            c[u] = __ldg(col + j0 + jb + u);
+            a[u] = Load::val(val, j0 + jb + u);
+        }
+#pragma unroll
+    for (int u = 0; u < IPT; ++u)
+        if (u < cnt) xv[u] = Load::xg(xg, c[u]);
+    Acc acc;
+    acc.zero();
+    int next_end = i < iend ? s_rowend[i] : 0x7fffffff;
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+        if (u < cnt) {
+            while (next_end <= jb + u) {   // row i ends before this nonzero
+                s_yl[i] = acc;
+                acc.zero();
+                ++i;
+                next_end = i < iend ? s_rowend[i] : 0x7fffffff;
+            }
+            acc.mad(a[u], xv[u]);
+        }
+    }
+    while (i < iend) {   // rows ending after the last nonzero of this share
+        s_yl[i] = acc;
+        acc.zero();
+        ++i;
+    }
+    s_crow[threadIdx.x] = i;
+    s_cval[threadIdx.x] = acc;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int myrow = i;
+    const bool head = threadIdx.x == 0 || s_crow[threadIdx.x - 1] != myrow;
+    const bool run_end = threadIdx.x == MP_BLOCK - 1 || s_crow[threadIdx.x + 1] != myrow;
+    int run_start = threadIdx.x;
+    if (run_end && !head) {
+        int u = (int)threadIdx.x - 1;
+        while (u > 0 && s_crow[u - 1] == myrow && (int)threadIdx.x - u < 8) --u;
+        run_start = (u > 0 && s_crow[u - 1] == myrow) ? -1 : u;   // -1: run longer than 9
+    }
+    const bool long_run = __syncthreads_or(run_end && run_start < 0);
+    Acc sv = acc;
+    if (!long_run) {
+        if (run_end && run_start < (int)threadIdx.x) {
+            sv = s_cval[run_start];
+            for (int u = run_start + 1; u <= (int)threadIdx.x; ++u) sv.add(s_cval[u]);
+        }
+    } else {
+        bool f = head;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            Acc ov = sv.shfl_up(o);
+            const bool of = __shfl_up_sync(0xffffffffu, f, o);
+            if (lane >= o) {
+                if (!f) {
+                    ov.add(sv);
+                    sv = ov;
+                }
+                f = f || of;
+            }
+        }
+        Acc *s_wsum = s_cval + MP_BLOCK;
+        if (lane == 31) {
+            s_wsum[warp] = sv;
+            s_crow[MP_BLOCK + warp] = f ? 1 : 0;
+        }
+        __syncthreads();
+        if (!f && warp > 0) {   // no head between this warp's start and this thread: carry-in
+            Acc cin;
+            cin.zero();
+            for (int w = 0; w < warp; ++w) {
+                if (s_crow[MP_BLOCK + w]) cin = s_wsum[w];
+                else cin.add(s_wsum[w]);
+            }
+            cin.add(sv);
+            sv = cin;
+        }
+    }
+    if (run_end) {
+        if (myrow < nrows) {
+            sv.add(s_yl[myrow]);
+            s_yl[myrow] = sv;
+        } else {
+            carry_row[t] = (int32_t)(i0 + nrows);
+            carry_val[t] = sv.to_double();
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nrows; r += MP_BLOCK) y[i0 + r] = s_yl[r].template out<XT>();
+}
+
+template <typename VT, typename XT, typename AT, int IPT>
+__global__ __launch_bounds__(MP_BLOCK) void k_merge_spmv(const int32_t *__restrict__ row_ptr,
+                                                         const int32_t *__restrict__ col, const VT *__restrict__ val,
+                                                         const XT *__restrict__ x, XT *__restrict__ y,
+                                                         const int32_t *__restrict__ part_row,
+                                                         const int32_t *__restrict__ part_nz,
+                                                         int32_t *__restrict__ carry_row, double *__restrict__ carry_val) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    merge_tile<NativeAcc<AT>, NativeLoad<VT, AT>, VT, XT, XT, IPT>(row_ptr, col, val, x, y, part_row, part_nz,
+                                                                  carry_row, carry_val, smem_raw);
+}
+
+// FP64 values and vectors through double-float arithmetic; x2 holds x split into float
+// pairs and *xflag is non-zero when some x fell outside the window, in which case the
+// tile is computed with native FP64 instead.
+template <int IPT>
+__global__ __launch_bounds__(MP_BLOCK) void k_merge_spmv_df(const int32_t *__restrict__ row_ptr,
+                                                            const int32_t *__restrict__ col,
+                                                            const double *__restrict__ val,
+                                                            const double *__restrict__ x,
+                                                            const float2 *__restrict__ x2,
+                                                            const uint32_t *__restrict__ xflag, double *__restrict__ y,
+                                                            const int32_t *__restrict__ part_row,
+                                                            const int32_t *__restrict__ part_nz,
+                                                            int32_t *__restrict__ carry_row,
+                                                            double *__restrict__ carry_val) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (*xflag == 0u)
+        merge_tile<DfAcc, DfLoad, double, float2, double, IPT>(row_ptr, col, val, x2, y, part_row, part_nz, carry_row,
+                                                               carry_val, smem_raw);
+    else
+        merge_tile<NativeAcc<double>, NativeLoad<double, double>, double, double, double, IPT>(
+            row_ptr, col, val, x, y, part_row, part_nz, carry_row, carry_val, smem_raw);
+}
+
+// x -> (hi, lo) float pairs; flags values outside the double-float window.
+__global__ void k_df_split_x(const double *__restrict__ x, int64_t n, float2 *__restrict__ x2, uint32_t *flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
+    if (i < n) {
+        float2 r;
+        bad = !df_split(x[i], &r.x, &r.y);
+        x2[i] = r;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+// Tile carries, added in tile order: the first tile of each run of equal carry rows sums
+// the run and adds it to y[row] (which the finishing tile has already written).
+template <typename XT>
+__global__ void k_merge_fixup(int64_t tiles, int64_t m, const int32_t *__restrict__ carry_row,
+                              const double *__restrict__ carry_val, XT *__restrict__ y) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tiles) return;
+    const int32_t row = carry_row[t];
+    if (t > 0 && carry_row[t - 1] == row) return;
+    double s = carry_val[t];
+    for (int64_t u = t + 1; u < tiles && carry_row[u] == row; ++u) s = s + carry_val[u];
+    if (row < m) y[row] = XT((double)y[row] + s);
+}
+
+template <typename Acc>
+constexpr size_t merge_smem(int ipt) {
+    return (size_t)MP_BLOCK * ipt * (sizeof(Acc) + 4) + (MP_BLOCK + 32) * 4 + (MP_BLOCK + 32) * sizeof(Acc);
+}
+
+template <typename VT, typename XT, typename AT, int IPT>
+spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allow_df, cudaStream_t s) {
+    constexpr bool FP64 = std::is_same<VT, double>::value && std::is_same<XT, double>::value &&
+                          std::is_same<AT, double>::value;
+    if constexpr (FP64) {
+        if (allow_df && h->df_ok && h->xsplit) {
+            constexpr size_t smem = merge_smem<NativeAcc<double>>(IPT);   // >= the double-float layout
+            static_assert(sizeof(DfAcc) == sizeof(NativeAcc<double>), "same staging layout");
+            static bool attr = false;
+            if (!attr) {
+                SPMV_CUDA_TRY(cudaFuncSetAttribute(k_merge_spmv_df<IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem));
+                attr = true;
+            }
+            SPMV_CUDA_TRY(cudaMemsetAsync(h->xsplit_flag, 0, 4, s));
+            if (h->n > 0) {
+                SPMV_LAUNCH("k_df_split_x", s,
+                            (k_df_split_x<<<cdivu(h->n, 256), 256, 0, s>>>((const double *)x, h->n, h->xsplit,
+                                                                              h->xsplit_flag)));
+                SPMV_LAUNCH_CHECK("x split");
+            }
+            SPMV_LAUNCH("k_merge_spmv", s,
+                        (k_merge_spmv_df<IPT><<<(unsigned)h->tiles, MP_BLOCK, smem, s>>>(
+                            h->row_ptr, h->col, (const double *)h->val, (const double *)x, h->xsplit, h->xsplit_flag,
+                            (double *)y, h->part_row, h->part_nz, h->carry_row, h->carry_val)));
+            SPMV_LAUNCH_CHECK("merge spmv");
+            SPMV_LAUNCH("k_merge_fixup", s, (k_merge_fixup<double><<<cdivu(h->tiles, 256), 256, 0, s>>>(
+                                                h->tiles, h->m, h->carry_row, h->carry_val, (double *)y)));
+            SPMV_LAUNCH_CHECK("merge fixup");
+            return SPMV_OK;
+        }
+    }
+    constexpr size_t smem = merge_smem<NativeAcc<AT>>(IPT);
+    static bool attr = false;
+    if (!attr) {
+        SPMV_CUDA_TRY(cudaFuncSetAttribute(k_merge_spmv<VT, XT, AT, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+        attr = true;
+    }
+    SPMV_LAUNCH("k_merge_spmv", s, (k_merge_spmv<VT, XT, AT, IPT><<<(unsigned)h->tiles, MP_BLOCK, smem, s>>>(
+                                       h->row_ptr, h->col, (const VT *)h->val, (const XT *)x, (XT *)y, h->part_row,
+                                       h->part_nz, h->carry_row, h->carry_val)));
+    SPMV_LAUNCH_CHECK("merge spmv");
+    SPMV_LAUNCH("k_merge_fixup", s, (k_merge_fixup<XT><<<cdivu(h->tiles, 256), 256, 0, s>>>(
+                                        h->tiles, h->m, h->carry_row, h->carry_val, (XT *)y)));
+    SPMV_LAUNCH_CHECK("merge fixup");
+    return SPMV_OK;
+}
+
+// ================================================================ row split
+constexpr int RS_BLOCK = 256;
+
+struct ClassTable {
+    int64_t begin[NUM_ROW_CLASSES + 1];       // offset of each class in bin_rows
+    int64_t blk_begin[NUM_ROW_CLASSES + 1];   // first CTA of each class
+};
+
+template <typename VT, typename XT, typename AT, int G>
+__device__ __forceinline__ void rowsplit_group(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                                               const VT *__restrict__ val, const XT *__restrict__ x,
+                                               XT *__restrict__ y, const int32_t *__restrict__ rows, int64_t count,
+                                               int64_t local_blk) {
+    constexpr int RPB = RS_BLOCK / G;   // rows per CTA
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
+    const int64_t ridx = local_blk * RPB + g;
+    AT acc = AT(0);
+    int32_t row = -1;
+    if (ridx < count) {
+        row = rows[ridx];
+        const int32_t k0 = __ldg(row_ptr + row), k1 = __ldg(row_ptr + row + 1);
+        for (int32_t k = k0 + lane; k < k1; k += G) acc = acc + ld_val<VT, AT>(val, k) * ld_x<XT, AT>(x, __ldg(col + k));
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc = acc + __shfl_xor_sync(0xffffffffu, acc, o, G);
+    if (row >= 0 && lane == 0) y[row] = XT(acc);
+}
+
+template <typename VT, typename XT, typename AT>
+__device__ __forceinline__ void rowsplit_cta(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                                             const VT *__restrict__ val, const XT *__restrict__ x,
+                                             XT *__restrict__ y, int32_t row) {
+    constexpr int U = 8;   // independent loads in flight per thread
+    __shared__ AT red[RS_BLOCK / 32];
+    const int32_t k0 = __ldg(row_ptr + row), k1 = __ldg(row_ptr + row + 1);
+    AT acc = AT(0);
+    for (int32_t kb = k0; kb < k1; kb += U * RS_BLOCK) {
+        int32_t c[U];
+        AT a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int32_t k = kb + u * RS_BLOCK + threadIdx.x;
+            if (k < k1) {
+                c[u] = __ldg(col + k);
+                a[u] = ld_val<VT, AT>(val, k);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int32_t k = kb + u * RS_BLOCK + threadIdx.x;
+            if (k < k1) acc = acc + a[u] * ld_x<XT, AT>(x, c[u]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = acc + __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        AT s = AT(0);
+        for (int w = 0; w < RS_BLOCK / 32; ++w) s = s + red[w];
+        y[row] = XT(s);
+    }
+}
+
+template <typename VT, typename XT, typename AT>
+__global__ __launch_bounds__(RS_BLOCK) void k_rowsplit(const int32_t *__restrict__ row_ptr,
+                                                       const int32_t *__restrict__ col, const VT *__restrict__ val,
+                                                       const XT *__restrict__ x, XT *__restrict__ y,
+                                                       const int32_t *__restrict__ bin_rows, ClassTable ct) {
+    const int64_t b = blockIdx.x;
+    int c = 0;
+    while (c < NUM_ROW_CLASSES - 1 && b >= ct.blk_begin[c + 1]) ++c;
+    const int64_t lb = b - ct.blk_begin[c];
+    const int32_t *rows = bin_rows + ct.begin[c];
+    const int64_t count = ct.begin[c + 1] - ct.begin[c];
+    switch (c) {
+        case 0: rowsplit_group<VT, XT, AT, 1>(row_ptr, col, val, x, y, rows, count, lb); break;
+        case 1: rowsplit_group<VT, XT, AT, 2>(row_ptr, col, val, x, y, rows, count, lb); break;
+        case 2: rowsplit_group<VT, XT, AT, 4>(row_ptr, col, val, x, y, rows, count, lb); break;
+        case 3: rowsplit_group<VT, XT, AT, 8>(row_ptr, col, val, x, y, rows, count, lb); break;
+        case 4: rowsplit_group<VT, XT, AT, 16>(row_ptr, col, val, x, y, rows, count, lb); break;
+        case 5: rowsplit_group<VT, XT, AT, 32>(row_ptr, col, val, x, y, rows, count, lb); break;
+        default: rowsplit_cta<VT, XT, AT>(row_ptr, col, val, x, y, rows[lb]); break;
+    }
+}
+
+template <typename VT, typename XT, typename AT>
+spmv_status launch_rowsplit(const spmv_matrix *h, const void *x, void *y, cudaStream_t s) {
+    ClassTable ct;
+    ct.begin[0] = 0;
+    ct.blk_begin[0] = 0;
+    for (int c = 0; c < NUM_ROW_CLASSES; ++c) {
+        const int64_t cnt = h->bin_count[c];
+        ct.begin[c + 1] = ct.begin[c] + cnt;
+        const int64_t rpb = c < NUM_ROW_CLASSES - 1 ? RS_BLOCK / class_lanes(c) : 1;
+        ct.blk_begin[c + 1] = ct.blk_begin[c] + (cnt + rpb - 1) / rpb;
+    }
+    const int64_t blocks = ct.blk_begin[NUM_ROW_CLASSES];
+    if (blocks == 0) return SPMV_OK;
+    SPMV_LAUNCH("k_rowsplit", s, (k_rowsplit<VT, XT, AT><<<(unsigned)blocks, RS_BLOCK, 0, s>>>(h->row_ptr, h->col, (const VT *)h->val,
+                                                                 (const XT *)x, (XT *)y, h->bin_rows, ct)));
+    SPMV_LAUNCH_CHECK("rowsplit spmv");
+    return SPMV_OK;
+}
+
+// ================================================================ Hilbert blocked
+constexpr int HB_BLOCK = 256;
+constexpr int HB_IPT = 8;
+constexpr int HB_TILE = HB_BLOCK * HB_IPT;
+
+__device__ __forceinline__ void atomic_add_out(double *p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add_out(float *p, float v) { atomicAdd(p, v); }
+
+template <typename VT, typename XT, typename AT>
+__global__ __launch_bounds__(HB_BLOCK) void k_hb_spmv(int64_t nnz, int64_t nblk, int log2b,
+                                                      const int32_t *__restrict__ blk_ptr,
+                                                      const int32_t *__restrict__ blk_row,
+                                                      const int32_t *__restrict__ blk_col,
+                                                      const uint32_t *__restrict__ idx, const VT *__restrict__ val,
+                                                      const XT *__restrict__ x, XT *__restrict__ y) {
+    __shared__ int32_t s_ptr[HB_TILE + 1];
+    __shared__ int32_t s_r0[HB_TILE];
+    __shared__ int32_t s_c0[HB_TILE];
+    __shared__ int64_t s_b[2];
+    const int64_t e0 = (int64_t)blockIdx.x * HB_TILE;
+    const int64_t e1 = min(e0 + HB_TILE, nnz);   // exclusive
+    if (threadIdx.x < 2) {
+        // first block with blk_ptr[b] <= e  (largest such b)
+        const int64_t e = threadIdx.x == 0 ? e0 : e1 - 1;
+        int64_t lo = 0, hi = nblk - 1;
+        while (lo < hi) {
+            int64_t mid = (lo + hi + 1) >> 1;
+            if ((int64_t)blk_ptr[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        s_b[threadIdx.x] = lo;
+    }
+    __syncthreads();
+    const int64_t b0 = s_b[0];
+    const int nb = (int)(s_b[1] - b0 + 1);   // <= HB_TILE blocks touch a tile
+    for (int q = threadIdx.x; q < nb; q += HB_BLOCK) {
+        s_ptr[q] = blk_ptr[b0 + q];
+        s_r0[q] = blk_row[b0 + q] << log2b;
+        s_c0[q] = blk_col[b0 + q] << log2b;
+    }
+    if (threadIdx.x == 0) s_ptr[nb] = blk_ptr[b0 + nb];
+    __syncthreads();
+#pragma unroll 2
+    for (int jj = 0; jj < HB_IPT; ++jj) {
+        const int64_t e = e0 + (int64_t)jj * HB_BLOCK + threadIdx.x;
+        if (e >= e1) break;
+        int lo = 0, hi = nb - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if ((int64_t)s_ptr[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint32_t p = __ldg(idx + e);
+        const int64_t r = (int64_t)s_r0[lo] + (p >> 16);
+        const int64_t c = (int64_t)s_c0[lo] + (p & 0xFFFFu);
+        const AT v = ld_val<VT, AT>(val, e) * ld_x<XT, AT>(x, c);
+        atomic_add_out(y + r, XT(v));
+    }
+}
+
+template <typename VT, typename XT, typename AT>
+spmv_status launch_hb(const spmv_matrix *h, const void *x, void *y, cudaStream_t s) {
+    SPMV_CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)h->m * sizeof(XT), s));
+    if (h->nnz == 0) return SPMV_OK;
+    SPMV_LAUNCH("k_hb_spmv", s, (k_hb_spmv<VT, XT, AT><<<cdivu(h->nnz, HB_TILE), HB_BLOCK, 0, s>>>(
+        h->nnz, h->nblk, h->log2beta, h->blk_ptr, h->blk_row, h->blk_col, h->hb_idx, (const VT *)h->hb_val,
+        (const XT *)x, (XT *)y)));
+    SPMV_LAUNCH_CHECK("hb spmv");
+    return SPMV_OK;
+}
+
+// ================================================================ dispatch
+// Supported (values, vectors, accumulation): F64/F64/F64; F32/F32/F32; F32/F32/F64;
+// BF16/F32/F32; BF16/F32/F64; PATTERN/F64/F64; PATTERN/F32/F32.
+enum Algo { MERGE, ROWSPLIT, HB };
+
+template <typename VT, typename XT, typename AT>
+spmv_status run_algo(Algo a, const spmv_matrix *h, const void *x, void *y, bool allow_df, cudaStream_t s) {
+    if (a == MERGE) return launch_merge<VT, XT, AT, MERGE_IPT>(h, x, y, allow_df, s);
+    if (a == ROWSPLIT) return launch_rowsplit<VT, XT, AT>(h, x, y, s);
+    return launch_hb<VT, XT, AT>(h, x, y, s);
+}
+
+spmv_status dispatch(Algo a, const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc,
+                     cudaStream_t s) {
+    const spmv_dtype dt = h->dt;
+    const bool allow_df = acc == SPMV_ACC_DEFAULT;   // SPMV_ACC_F64 forces native FP64 arithmetic
+    if (acc == SPMV_ACC_DEFAULT) acc = (dt == SPMV_F64 || (dt == SPMV_PATTERN && vdt == SPMV_F64)) ? SPMV_ACC_F64 : SPMV_ACC_F32;
+    if (vdt == SPMV_F64) {
+        if (acc != SPMV_ACC_F64) goto unsupported;
+        if (dt == SPMV_F64) return run_algo<double, double, double>(a, h, x, y, allow_df, s);
+        if (dt == SPMV_PATTERN) return run_algo<Pattern, double, double>(a, h, x, y, allow_df, s);
+        if (dt == SPMV_F32) return run_algo<float, double, double>(a, h, x, y, allow_df, s);
+        goto unsupported;
+    }
+    if (vdt == SPMV_F32) {
+        if (acc == SPMV_ACC_F32) {
+            if (dt == SPMV_F32) return run_algo<float, float, float>(a, h, x, y, allow_df, s);
+            if (dt == SPMV_BF16) return run_algo<__nv_bfloat16, float, float>(a, h, x, y, allow_df, s);
+            if (dt == SPMV_PATTERN) return run_algo<Pattern, float, float>(a, h, x, y, allow_df, s);
+        } else if (acc == SPMV_ACC_F64 && a != HB) {
+            if (dt == SPMV_F32) return run_algo<float, float, double>(a, h, x, y, allow_df, s);
+            if (dt == SPMV_BF16) return run_algo<__nv_bfloat16, float, double>(a, h, x, y, allow_df, s);
+        }
+    }
+unsupported:
+    set_error("spmv_mul: unsupported combination of matrix dtype, vector dtype and accumulation");
+    return SPMV_ERR_UNSUPPORTED;
+}
+
+}  // namespace
+
+spmv_status mul_merge(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s) {
+    return dispatch(MERGE, h, x, y, vdt, acc, s);
+}
+spmv_status mul_rowsplit(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s) {
+    return dispatch(ROWSPLIT, h, x, y, vdt, acc, s);
+}
+spmv_status mul_hb(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s) {
+    return dispatch(HB, h, x, y, vdt, acc, s);
+}
+
+}  // namespace spmv

@@ -21,3 +21,20 @@ def golden_path(name: str) -> str:
 def orc():
     import oracle
     return oracle.load()
+
+
+def pytest_sessionstart(session):
+    # Build the C generators, the oracle and the CUDA library if they are missing
+    # (nvcc cross-compiles without a GPU).
+    lib = os.path.join(ROOT, "paper_2502_19284_gb300", "_build", "libspmv.so")
+    if not os.path.exists(lib):
+        import __graft_entry__
+        __graft_entry__.build()
+
+
+def cuda_available() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
