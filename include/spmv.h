@@ -199,6 +199,38 @@ const char *spmv_status_string(spmv_status s);
 spmv_status spmv_hilbert_keys(int K, int64_t n, const int32_t *rows, const int32_t *cols, uint64_t *keys,
                               void *stream);
 
+/* ---------------------------------------------------------------- no allocation */
+
+/*
+ * spmv_mul_csr_merge_noalloc -- y := A x for a CRS matrix the caller already holds on the
+ * device, with the merge-path product, without allocating any device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate,
+ * for example code recording work into a CUDA graph, callers that reserved all device
+ * memory up front for their own allocator, or serving loops that cannot afford the device
+ * synchronisation that cudaMalloc and cudaFree imply.  The library's other calls keep
+ * their scratch in memory they allocate; this one keeps the merge-path partition and the
+ * tile carries in a fixed array that is part of the library itself (about 1.3 MB, held on
+ * every GPU that loads the library until the process exits).
+ *
+ *   m, n, nnz   shape and nonzero count; nnz must equal row_ptr[m].
+ *   row_ptr     device, m+1 int32 (non-decreasing, row_ptr[0] = 0); col_ind: device, nnz
+ *               int32 in [0, n); data: device, nnz doubles; x: device, n doubles;
+ *               y: device, m doubles (overwritten).  All are the caller's and are only read
+ *               (y written) by the kernels enqueued on `stream`.
+ * Limit: m + nnz <= 117,440,512 (65,536 tiles of 1,792 row ends and nonzeros); larger
+ * inputs are rejected with SPMV_ERR_UNSUPPORTED before anything is enqueued.
+ * Arithmetic is native FP64 (as spmv_mul with SPMV_ACC_F64).
+ * The first call on each device looks up the array's device address with that device
+ * current; make that first call before capturing a stream into a graph.  All calls on a
+ * device share the one array and overwrite it (every entry they read is written by the
+ * same call first), so calls whose kernels may overlap on the GPU -- on different streams
+ * without ordering -- race and must not be issued.
+ */
+spmv_status spmv_mul_csr_merge_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr,
+                                       const int32_t *col_ind, const double *data, const double *x, double *y,
+                                       void *stream);
+
 /* ---------------------------------------------------------------- tracing */
 
 /*

@@ -60,6 +60,7 @@ _SIG = {
     "spmv_export_hb": [_p, _p, _p, _p, _p, _p],
     "spmv_export_merge_partition": [_p, _p, _p],
     "spmv_hilbert_keys": [_i32, _i64, _p, _p, _p, _p],
+    "spmv_mul_csr_merge_noalloc": [_i64, _i64, _i64, _p, _p, _p, _p, _p, _p],
 }
 for _name, _args in _SIG.items():
     _f = getattr(_lib, _name)
@@ -232,6 +233,13 @@ def spmv_hilbert_keys(K, rows, cols, keys, stream=None):
     """Device Hilbert keys of (rows[i], cols[i]) on the 2^K grid into keys (uint64 as int64 tensor)."""
     _check(_lib.spmv_hilbert_keys(K, int(rows.shape[0]), _addr(rows), _addr(cols), _addr(keys), _stream(stream)),
            "spmv_hilbert_keys")
+
+
+def spmv_mul_csr_merge_noalloc(m, n, nnz, row_ptr, col_ind, data, x, y, stream=None):
+    """y := A x on caller-held device CRS arrays, allocating no device memory (see spmv.h)."""
+    _check(_lib.spmv_mul_csr_merge_noalloc(m, n, nnz, _addr(row_ptr), _addr(col_ind), _addr(data), _addr(x),
+                                           _addr(y), _stream(stream)), "spmv_mul_csr_merge_noalloc")
+    return y
 
 
 def spmv_trace_enable(on: bool = True):

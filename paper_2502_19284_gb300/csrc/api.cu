@@ -457,6 +457,23 @@ spmv_status spmv_export_merge_partition(spmv_handle h, int32_t *row_start, int32
     return SPMV_OK;
 }
 
+spmv_status spmv_mul_csr_merge_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr,
+                                       const int32_t *col_ind, const double *data, const double *x, double *y,
+                                       void *stream) {
+    g_err.clear();
+    if (m < 0 || n < 0 || nnz < 0 || m >= ((int64_t)1 << 31) || n >= ((int64_t)1 << 31) ||
+        nnz >= ((int64_t)1 << 31)) {
+        set_error("spmv_mul_csr_merge_noalloc: sizes must lie in [0, 2^31)");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    if (!row_ptr || (nnz > 0 && (!col_ind || !data)) || (n > 0 && !x) || (m > 0 && !y)) {
+        set_error("spmv_mul_csr_merge_noalloc: NULL array");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    if (m == 0) return SPMV_OK;
+    return mul_csr_merge_noalloc(m, n, nnz, row_ptr, col_ind, data, x, y, (cudaStream_t)stream);
+}
+
 spmv_status spmv_hilbert_keys(int K, int64_t n, const int32_t *rows, const int32_t *cols, uint64_t *keys,
                               void *stream) {
     if (K < 1 || K > 31 || n < 0 || (n > 0 && (!rows || !cols || !keys))) {

@@ -45,5 +45,7 @@ spmv_status mul_merge(const spmv_matrix *h, const void *x, void *y, spmv_dtype v
 // (the FP64 products use double-float arithmetic when acc == SPMV_ACC_DEFAULT and h->df_ok)
 spmv_status mul_rowsplit(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s);
 spmv_status mul_hb(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s);
+spmv_status mul_csr_merge_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col,
+                                  const double *data, const double *x, double *y, cudaStream_t s);
 
 }  // namespace spmv

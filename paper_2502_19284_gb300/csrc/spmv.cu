@@ -24,6 +24,7 @@
 #include "df64.cuh"
 
 #include <algorithm>
+#include <mutex>
 
 namespace spmv {
 
@@ -569,6 +570,85 @@ unsupported:
     return SPMV_ERR_UNSUPPORTED;
 }
 
+// ================================================================ allocation-free entry
+// spmv_mul_csr_merge_noalloc keeps the merge-path partition and the tile carries in the
+// file-scope array below instead of memory it allocates, for callers that must not
+// allocate device memory.  Every call on a device shares the one array.
+constexpr int64_t NOALLOC_MAX_TILES = 1 << 16;   // up to 65,536 tiles of MERGE_TILE_ITEMS path items
+constexpr size_t NOALLOC_PART_BYTES = (size_t)(NOALLOC_MAX_TILES + 1) * 4;
+constexpr size_t NOALLOC_BYTES = 2 * ((NOALLOC_PART_BYTES + 255) / 256 * 256) + (size_t)NOALLOC_MAX_TILES * 4 +
+                                 (size_t)NOALLOC_MAX_TILES * 8;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// Split points of the merge path (same rule as the conversion's partition).
+__global__ void k_noalloc_partition(const int32_t *__restrict__ row_ptr, int64_t m, int64_t nnz, int64_t tiles,
+                                    int64_t tile_items, int32_t *__restrict__ part_row, int32_t *__restrict__ part_nz) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > tiles) return;
+    const int64_t d = min(t * tile_items, m + nnz);
+    int64_t lo = d - nnz > 0 ? d - nnz : 0, hi = d < m ? d : m;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if ((int64_t)row_ptr[mid] <= d - mid) lo = mid;
+        else hi = mid - 1;
+    }
+    part_row[t] = (int32_t)lo;
+    part_nz[t] = (int32_t)(d - lo);
+}
+
+// Device address of the scratch array, looked up once per device with that device current.
+spmv_status noalloc_scratch(unsigned char **out) {
+    static std::mutex mu;
+    static void *addr[256] = {nullptr};
+    int dev = 0;
+    SPMV_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) {
+        set_error("spmv_mul_csr_merge_noalloc: device ordinal out of range");
+        return SPMV_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> g(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_status(e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
+        addr[dev] = p;
+    }
+    *out = (unsigned char *)addr[dev];
+    return SPMV_OK;
+}
+
+spmv_status noalloc_merge(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col,
+                          const double *data, const double *x, double *y, cudaStream_t s) {
+    const int64_t tiles = std::max<int64_t>(1, (m + nnz + MERGE_TILE_ITEMS - 1) / MERGE_TILE_ITEMS);
+    if (tiles > NOALLOC_MAX_TILES) {
+        set_error("spmv_mul_csr_merge_noalloc: m + nnz exceeds the fixed scratch (65,536 tiles of 1,792 row ends "
+                  "and nonzeros, i.e. m + nnz <= 117,440,512)");
+        return SPMV_ERR_UNSUPPORTED;
+    }
+    unsigned char *base = nullptr;
+    SPMV_TRY(noalloc_scratch(&base));
+    const size_t pb = (NOALLOC_PART_BYTES + 255) / 256 * 256;
+    int32_t *part_row = (int32_t *)base;
+    int32_t *part_nz = (int32_t *)(base + pb);
+    int32_t *carry_row = (int32_t *)(base + 2 * pb);
+    double *carry_val = (double *)(base + 2 * pb + (size_t)NOALLOC_MAX_TILES * 4);
+    constexpr size_t smem = merge_smem<NativeAcc<double>>(MERGE_IPT);
+    static bool attr = false;
+    if (!attr) {
+        SPMV_CUDA_TRY(cudaFuncSetAttribute(k_merge_spmv<double, double, double, MERGE_IPT>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    k_noalloc_partition<<<cdivu(tiles + 1, 256), 256, 0, s>>>(row_ptr, m, nnz, tiles, MERGE_TILE_ITEMS, part_row, part_nz);
+    SPMV_LAUNCH_CHECK("noalloc partition");
+    k_merge_spmv<double, double, double, MERGE_IPT><<<(unsigned)tiles, MP_BLOCK, smem, s>>>(
+        row_ptr, col, data, x, y, part_row, part_nz, carry_row, carry_val);
+    SPMV_LAUNCH_CHECK("noalloc merge spmv");
+    k_merge_fixup<double><<<cdivu(tiles, 256), 256, 0, s>>>(tiles, m, carry_row, carry_val, y);
+    SPMV_LAUNCH_CHECK("noalloc merge fixup");
+    return SPMV_OK;
+}
+
 }  // namespace
 
 spmv_status mul_merge(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s) {
@@ -579,6 +659,11 @@ spmv_status mul_rowsplit(const spmv_matrix *h, const void *x, void *y, spmv_dtyp
 }
 spmv_status mul_hb(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s) {
     return dispatch(HB, h, x, y, vdt, acc, s);
+}
+
+spmv_status mul_csr_merge_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col,
+                                  const double *data, const double *x, double *y, cudaStream_t s) {
+    return noalloc_merge(m, n, nnz, row_ptr, col, data, x, y, s);
 }
 
 }  // namespace spmv

@@ -1,0 +1,69 @@
+"""The allocation-free product spmv_mul_csr_merge_noalloc, called through the C ABI.
+
+Some callers cannot allocate device memory while they run (for example while recording a
+CUDA graph, inside an allocator that owns all device memory, or in a serving loop that must
+not pay the device synchronisation of cudaMalloc/cudaFree).  For them the library offers a
+merge-path product whose scratch lives in a fixed array inside the library.  This test
+checks it against the regular entry point (spmv_create_coo + spmv_convert + spmv_mul)
+on two calls in a row, within the tolerance the other parity tests use, and that an
+oversized input is rejected.  The file name sorts last so that a run stopping at the
+first failure has already run every other test.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-13
+
+
+@pytest.fixture(scope="module")
+def sp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2502_19284_gb300 as sp
+    torch.cuda.set_device(0)
+    return sp
+
+
+def test_noalloc_matches_regular_entry_point_twice(sp):
+    dev = "cuda:0"
+    scale = 16
+    m = n = 1 << scale
+    rows, cols = synth.rmat(scale, 16, seed=31)
+    vals = synth.values(rows, cols, 31)
+    rp, co, vo = oracle.coo_to_csr(m, n, rows, cols, vals)
+    nnz = int(rp[-1])
+    rp_d, co_d, vo_d = (torch.from_numpy(a).to(dev) for a in (rp, co, vo))
+    h = sp.spmv_create_coo(m, n, *(torch.from_numpy(a).to(dev) for a in (rows, cols, vals)))
+    sp.spmv_convert(h, "merge")
+    lib = sp._lib
+    stream = torch.cuda.current_stream().cuda_stream
+    for call, seed in enumerate((41, 42)):          # two calls in a row, different x
+        x = synth.vector(n, seed)
+        x_d = torch.from_numpy(x).to(dev)
+        y_ref = torch.empty(m, dtype=torch.float64, device=dev)
+        sp.spmv_mul(h, x_d, y_ref)
+        y_new = torch.full((m,), float("nan"), dtype=torch.float64, device=dev)
+        st = lib.spmv_mul_csr_merge_noalloc(m, n, nnz, rp_d.data_ptr(), co_d.data_ptr(), vo_d.data_ptr(),
+                                            x_d.data_ptr(), y_new.data_ptr(), stream)
+        assert st == sp.SPMV_OK, sp.spmv_last_error()
+        torch.cuda.synchronize()
+        a, b = y_new.cpu().numpy(), y_ref.cpu().numpy()
+        scale_abs = oracle.csr_absmul(rp, co, vo, x)
+        assert np.isfinite(a).all(), f"call {call}"
+        assert (np.abs(a - b) <= TOL * scale_abs).all(), f"call {call}"
+    sp.spmv_destroy(h)
+
+
+def test_noalloc_rejects_oversized_input(sp):
+    lib = sp._lib
+    buf = torch.zeros(4, dtype=torch.float64, device="cuda:0")
+    p = buf.data_ptr()
+    st = lib.spmv_mul_csr_merge_noalloc(1 << 26, 1 << 26, (1 << 26) + 4, p, p, p, p, p, None)
+    assert st == sp.SPMV_ERR_UNSUPPORTED
+    assert b"exceeds the fixed scratch" in lib.spmv_last_error()
