@@ -153,8 +153,8 @@ bool is_device_ptr(const void *p) {
 
 void free_all(spmv_matrix *h) {
     void *ptrs[] = {h->coo_row, h->coo_col, h->coo_val, h->row_ptr, h->col, h->val, h->bin_rows,
-                    h->part_row, h->part_nz, h->carry_row, h->carry_val, h->hb_idx, h->hb_val,
-                    h->blk_ptr, h->blk_row, h->blk_col, h->xsplit, h->xsplit_flag, h->status_dev};
+                    h->part_row, h->part_nz, h->carry_row, h->carry_val, h->merge_desc, h->hb_idx, h->hb_val,
+                    h->blk_ptr, h->blk_row, h->blk_col, h->val2, h->xsplit, h->xsplit_flag, h->status_dev};
     for (void *p : ptrs) dev_free(p);
     if (h->status_host) cudaFreeHost(h->status_host);
 }
@@ -325,13 +325,13 @@ spmv_status spmv_convert(spmv_handle h, spmv_format f, const spmv_convert_opts *
         set_error("spmv_convert: log2_beta must be in [1, 16] (0 = Eq. 2 rule)");
         return SPMV_ERR_INVALID_ARG;
     }
-    if (o.tile != 0 && o.tile != MERGE_TILE_ITEMS) {
-        set_error("spmv_convert: only the default merge tile (1792 path items) is built in");
+    if (o.tile != 0 && o.tile != MERGE_WARP_ITEMS) {
+        set_error("spmv_convert: only the default merge tile (224 path items per warp) is built in");
         return SPMV_ERR_UNSUPPORTED;
     }
     if (!h->has_csr) SPMV_TRY(build_csr(h, s));
     if (f == SPMV_FMT_CSR_ROWSPLIT && !h->has_bins) SPMV_TRY(build_bins(h, s));
-    if (f == SPMV_FMT_CSR_MERGE && !h->has_merge) SPMV_TRY(build_merge(h, MERGE_TILE_ITEMS, s));
+    if (f == SPMV_FMT_CSR_MERGE && !h->has_merge) SPMV_TRY(build_merge(h, MERGE_WARP_ITEMS, s));
     if (f != SPMV_FMT_HB) SPMV_TRY(build_df(h, s));
     if (f == SPMV_FMT_HB) {
         int lb = o.log2_beta ? o.log2_beta : default_log2_beta(h->n, h->dt == SPMV_F64 ? 8 : 4);

@@ -142,6 +142,7 @@ struct spmv_matrix {
     int32_t *part_row = nullptr, *part_nz = nullptr;
     int32_t *carry_row = nullptr;
     double *carry_val = nullptr;
+    uint32_t *merge_desc = nullptr;   // per-lane descriptors of the warp tiles (32 words per tile)
 
     // Hilbert-ordered blocked format
     bool has_hb = false;
@@ -154,6 +155,7 @@ struct spmv_matrix {
     // FP64 through double-float arithmetic (df64.cuh): set when every stored value lies in
     // the double-float window; x is split into float pairs per product (scratch below)
     bool df_checked = false, df_ok = false;
+    float2 *val2 = nullptr;           // CRS values split into float pairs (when df_ok)
     float2 *xsplit = nullptr;
     uint32_t *xsplit_flag = nullptr;
 

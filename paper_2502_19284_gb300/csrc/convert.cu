@@ -22,6 +22,8 @@ namespace spmv {
 namespace {
 
 constexpr int CB = 256;   // block size of the simple element-wise kernels
+// Slack after the CRS arrays: the merge product's bulk copies read whole 16-byte units.
+constexpr size_t TMA_PAD = 64;
 
 inline unsigned grid_for(int64_t n, int per_block = CB) {
     int64_t g = (n + per_block - 1) / per_block;
@@ -195,6 +197,38 @@ __device__ __forceinline__ int64_t merge_split(int64_t d, int64_t m, int64_t nnz
     return lo;
 }
 
+// Per-lane descriptors of the warp tiles (MERGE_WARP_ITEMS path items, MERGE_WARP_IPT per
+// lane).  Row end r of a tile sits at path position r + (nonzeros of the tile before it); for
+// lane l, covering positions [7l, 7l + 7): bits 0-7 the number of row ends before its range
+// (its first row), bits 8-15 the number of nonzeros before it (its first nonzero), bits
+// 16-22 which of its items are row ends, bits 24-26 how many items it has.
+__global__ void k_merge_desc(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ part_row,
+                             const int32_t *__restrict__ part_nz, int64_t tiles, uint32_t *__restrict__ desc) {
+    __shared__ uint32_t s_bits[8][8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t t = (int64_t)blockIdx.x * 8 + w;
+    if (t >= tiles) return;
+    const int64_t i0 = part_row[t], j0 = part_nz[t];
+    const int nrows = (int)(part_row[t + 1] - i0), nnzt = (int)(part_nz[t + 1] - j0);
+    if (lane < 8) s_bits[w][lane] = 0u;
+    __syncwarp();
+    for (int r = lane; r < nrows; r += 32) {
+        const int pos = r + (int)(row_ptr[i0 + r + 1] - j0);
+        atomicOr(&s_bits[w][pos >> 5], 1u << (pos & 31));
+    }
+    __syncwarp();
+    const int total = nrows + nnzt;
+    const int d0 = min(lane * MERGE_WARP_IPT, total), d1 = min(d0 + MERGE_WARP_IPT, total);
+    const int w0 = d0 >> 5, b0 = d0 & 31;
+    int before = 0;
+    for (int q = 0; q < w0; ++q) before += __popc(s_bits[w][q]);
+    const uint32_t lo = s_bits[w][w0], hi = s_bits[w][w0 + 1];
+    before += __popc(lo & ((1u << b0) - 1u));
+    const uint32_t span = b0 ? (lo >> b0) | (hi << (32 - b0)) : lo;
+    const uint32_t bits = span & ((1u << (d1 - d0)) - 1u);
+    desc[t * 32 + lane] = (uint32_t)before | ((uint32_t)(d0 - before) << 8) | (bits << 16) | ((uint32_t)(d1 - d0) << 24);
+}
+
 __global__ void k_merge_partition(const int32_t *__restrict__ row_ptr, int64_t m, int64_t nnz, int64_t tiles,
                                   int64_t tile_items, int32_t *__restrict__ part_row, int32_t *__restrict__ part_nz) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -338,6 +372,15 @@ __global__ void k_df_window(const double *__restrict__ v, int64_t n, uint32_t *_
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
 }
 
+__global__ void k_df_split_vals(const double *__restrict__ v, int64_t n, float2 *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        float2 r;
+        df_split(v[i], &r.x, &r.y);
+        out[i] = r;
+    }
+}
+
 // ---------------------------------------------------------------- helpers
 spmv_status read_status(spmv_matrix *h, cudaStream_t s, uint32_t *out) {
     SPMV_CUDA_TRY(cudaMemcpyAsync(h->status_host, h->status_dev, 4, cudaMemcpyDeviceToHost, s));
@@ -398,7 +441,7 @@ spmv_status build_csr(spmv_matrix *h, cudaStream_t s) {
     const int64_t m = h->m, nnz = h->nnz_in;
     const int es = elem_size(h->dt);
     DevBuf row_ptr(s), col(s), val(s);
-    SPMV_TRY(row_ptr.alloc((size_t)(m + 1) * 4, "row_ptr"));
+    SPMV_TRY(row_ptr.alloc((size_t)(m + 1) * 4 + TMA_PAD, "row_ptr"));
     int64_t nout = 0;
     if (nnz == 0) {
         SPMV_CUDA_TRY(cudaMemsetAsync(row_ptr.p, 0, (size_t)(m + 1) * 4, s));
@@ -439,8 +482,8 @@ spmv_status build_csr(spmv_matrix *h, cudaStream_t s) {
             SPMV_CUDA_TRY(cudaMemcpyAsync(&last[1], head.as<uint32_t>() + nnz - 1, 4, cudaMemcpyDeviceToHost, s));
             SPMV_CUDA_TRY(cudaStreamSynchronize(s));
             nout = (int64_t)last[0] + last[1];
-            SPMV_TRY(col.alloc((size_t)nout * 4, "col_ind"));
-            if (es) SPMV_TRY(val.alloc((size_t)nout * es, "values"));
+            SPMV_TRY(col.alloc((size_t)nout * 4 + TMA_PAD, "col_ind"));
+            if (es) SPMV_TRY(val.alloc((size_t)nout * es + TMA_PAD, "values"));
             SPMV_LAUNCH("k_dup_compact", s, (k_dup_compact<<<grid_for(nnz), CB, 0, s>>>(K, P, head.as<uint32_t>(), pos, nnz, cbits,
                                                        es ? h->coo_val : nullptr, h->dt, Kspare,
                                                        col.as<int32_t>(), val.p)));
@@ -448,8 +491,8 @@ spmv_status build_csr(spmv_matrix *h, cudaStream_t s) {
             rowkeys = Kspare;
         } else {
             nout = nnz;
-            SPMV_TRY(col.alloc((size_t)nnz * 4, "col_ind"));
-            if (es) SPMV_TRY(val.alloc((size_t)nnz * es, "values"));
+            SPMV_TRY(col.alloc((size_t)nnz * 4 + TMA_PAD, "col_ind"));
+            if (es) SPMV_TRY(val.alloc((size_t)nnz * es + TMA_PAD, "values"));
             SPMV_LAUNCH("k_key_cols", s, (k_key_cols<<<grid_for(nnz), CB, 0, s>>>(K, nnz, cbits, col.as<int32_t>())));
             SPMV_LAUNCH_CHECK("key cols");
             if (es) SPMV_TRY(gather_values(h->coo_val, h->dt, P, nnz, val.p, s));
@@ -488,6 +531,15 @@ spmv_status build_df(spmv_matrix *h, cudaStream_t s) {
     SPMV_CUDA_TRY(cudaMemcpyAsync(h->status_host + 2, h->status_dev + 2, 4, cudaMemcpyDeviceToHost, s));
     SPMV_CUDA_TRY(cudaStreamSynchronize(s));
     h->df_ok = h->status_host[2] == 0;
+    if (h->df_ok && h->nnz > 0) {
+        DevBuf v2(s);
+        SPMV_TRY(v2.alloc((size_t)h->nnz * sizeof(float2) + TMA_PAD, "split values"));
+        SPMV_LAUNCH("k_df_split_vals", s, (k_df_split_vals<<<grid_for(h->nnz), CB, 0, s>>>((const double *)h->val, h->nnz,
+                                                                                           v2.as<float2>())));
+        SPMV_LAUNCH_CHECK("split values");
+        h->val2 = (float2 *)v2.release();
+        h->bytes += h->nnz * 8;
+    }
     h->xsplit = (float2 *)xs.release();
     h->xsplit_flag = (uint32_t *)fl.release();
     h->bytes += std::max<int64_t>(h->n, 1) * 8 + 16;
@@ -533,7 +585,8 @@ spmv_status build_bins(spmv_matrix *h, cudaStream_t s) {
 spmv_status build_merge(spmv_matrix *h, int tile_items, cudaStream_t s) {
     const int64_t total = h->m + h->nnz;
     const int64_t tiles = std::max<int64_t>(1, (total + tile_items - 1) / tile_items);
-    DevBuf pr(s), pn(s), cr(s), cv(s);
+    DevBuf pr(s), pn(s), cr(s), cv(s), ds(s);
+    SPMV_TRY(ds.alloc((size_t)tiles * 32 * 4, "merge descriptors"));
     SPMV_TRY(pr.alloc((size_t)(tiles + 1) * 4, "merge partition"));
     SPMV_TRY(pn.alloc((size_t)(tiles + 1) * 4, "merge partition"));
     SPMV_TRY(cr.alloc((size_t)tiles * 4, "merge carries"));
@@ -541,11 +594,15 @@ spmv_status build_merge(spmv_matrix *h, int tile_items, cudaStream_t s) {
     SPMV_LAUNCH("k_merge_partition", s, (k_merge_partition<<<grid_for(tiles + 1), CB, 0, s>>>(h->row_ptr, h->m, h->nnz, tiles, tile_items,
                                                          pr.as<int32_t>(), pn.as<int32_t>())));
     SPMV_LAUNCH_CHECK("merge partition");
+    SPMV_LAUNCH("k_merge_desc", s, (k_merge_desc<<<(unsigned)((tiles + 7) / 8), 256, 0, s>>>(
+                                       h->row_ptr, pr.as<int32_t>(), pn.as<int32_t>(), tiles, ds.as<uint32_t>())));
+    SPMV_LAUNCH_CHECK("merge descriptors");
     if (h->has_merge) {
         dev_free_async(h->part_row, s); dev_free_async(h->part_nz, s);
-        dev_free_async(h->carry_row, s); dev_free_async(h->carry_val, s);
-        h->bytes -= (h->tiles + 1) * 8 + h->tiles * 12;
+        dev_free_async(h->carry_row, s); dev_free_async(h->carry_val, s); dev_free_async(h->merge_desc, s);
+        h->bytes -= (h->tiles + 1) * 8 + h->tiles * 12 + h->tiles * 128;
     }
+    h->merge_desc = (uint32_t *)ds.release();
     h->part_row = (int32_t *)pr.release();
     h->part_nz = (int32_t *)pn.release();
     h->carry_row = (int32_t *)cr.release();
@@ -553,7 +610,7 @@ spmv_status build_merge(spmv_matrix *h, int tile_items, cudaStream_t s) {
     h->tiles = tiles;
     h->tile_items = tile_items;
     h->has_merge = true;
-    h->bytes += (tiles + 1) * 8 + tiles * 12;
+    h->bytes += (tiles + 1) * 8 + tiles * 12 + tiles * 128;
     return SPMV_OK;
 }
 

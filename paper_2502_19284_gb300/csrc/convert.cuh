@@ -14,7 +14,10 @@ constexpr int NUM_ROW_CLASSES = 7;
 // threads' shared-memory walks start in different banks.
 constexpr int MERGE_BLOCK = 256;
 constexpr int MERGE_IPT = 7;
-constexpr int MERGE_TILE_ITEMS = MERGE_BLOCK * MERGE_IPT;
+constexpr int MERGE_TILE_ITEMS = MERGE_BLOCK * MERGE_IPT;   // CTA tile (allocation-free entry)
+// The library's merge product cuts the path into warp tiles of MERGE_WARP_ITEMS items.
+constexpr int MERGE_WARP_IPT = 7;
+constexpr int MERGE_WARP_ITEMS = 32 * MERGE_WARP_IPT;
 
 __host__ __device__ __forceinline__ int class_lanes(int c) {
     return c == 0 ? 1 : c == 1 ? 2 : c == 2 ? 4 : c == 3 ? 8 : c == 4 ? 16 : 32;

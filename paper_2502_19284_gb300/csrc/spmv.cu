@@ -91,14 +91,6 @@ struct NativeLoad {
     __device__ __forceinline__ static AT val(const VT *v, int64_t k) { return ld_val<VT, AT>(v, k); }
     template <typename XT> __device__ __forceinline__ static AT xg(const XT *x, int64_t j) { return ld_x<XT, AT>(x, j); }
 };
-struct DfLoad {   // values: FP64 split on the fly; x: pre-split float pairs
-    __device__ __forceinline__ static float2 val(const double *v, int64_t k) {
-        float2 r;
-        df_split(__ldg(v + k), &r.x, &r.y);
-        return r;
-    }
-    __device__ __forceinline__ static float2 xg(const float2 *x2, int64_t j) { return __ldg(x2 + j); }
-};
 
 // One merge-path tile (Section 3.3).  Only row ends and finished rows are staged in shared
 // memory.  Each thread locates both ends of its share of the tile's path, loads the values
@@ -252,27 +244,347 @@ __global__ __launch_bounds__(MP_BLOCK) void k_merge_spmv(const int32_t *__restri
                                                                   carry_row, carry_val, smem_raw);
 }
 
-// FP64 values and vectors through double-float arithmetic; x2 holds x split into float
-// pairs and *xflag is non-zero when some x fell outside the window, in which case the
-// tile is computed with native FP64 instead.
-template <int IPT>
-__global__ __launch_bounds__(MP_BLOCK) void k_merge_spmv_df(const int32_t *__restrict__ row_ptr,
-                                                            const int32_t *__restrict__ col,
-                                                            const double *__restrict__ val,
-                                                            const double *__restrict__ x,
-                                                            const float2 *__restrict__ x2,
-                                                            const uint32_t *__restrict__ xflag, double *__restrict__ y,
-                                                            const int32_t *__restrict__ part_row,
-                                                            const int32_t *__restrict__ part_nz,
-                                                            int32_t *__restrict__ carry_row,
-                                                            double *__restrict__ carry_val) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (*xflag == 0u)
-        merge_tile<DfAcc, DfLoad, double, float2, double, IPT>(row_ptr, col, val, x2, y, part_row, part_nz, carry_row,
-                                                               carry_val, smem_raw);
+// ---------------------------------------------------------------- warp-tile merge path
+// Each warp owns one tile of MW_ITEMS path items (Section 3.3's merge path cut into equal
+// shares at the conversion) and runs independently of the other warps of its CTA: no block
+// barrier, so one warp's memory latency never stalls another.  The tile's row ends, column
+// indices and values are contiguous ranges of the CRS arrays; lane 0 brings them into the
+// warp's shared-memory slot with 1-D TMA bulk copies (cp.async.bulk, completion counted on
+// an mbarrier; source ranges widened to 16-byte boundaries, which the conversion's padding
+// keeps inside the allocations).  Lanes then split the tile by the merge rule, gather x,
+// accumulate their contiguous nonzero range, write every row they finish directly to y, and
+// hold back only their first finished row, which may need the sum of the preceding lanes'
+// carries (a segmented scan over lanes).  The last run of lanes becomes the tile's carry.
+
+constexpr int MW_WARPS = 4;
+constexpr int MW_IPT = MERGE_WARP_IPT;
+constexpr int MW_ITEMS = 32 * MW_IPT;
+constexpr long long MW_SPIN_LIMIT = 1ll << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// L2 eviction policies: the streamed matrix arrays are read once (evict first), the gathered
+// x is reused across the whole product (evict last), so the stream does not push x out of L2.
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// 1-D bulk copy global -> shared (TMA), completion counted on an mbarrier.
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+        :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol) : "memory");
+}
+
+// Widen the element range [e0, e1) of an array of `es`-byte elements to 16-byte boundaries:
+// returns the first element copied and the byte count.
+__device__ __forceinline__ void widen16(int64_t e0, int64_t e1, int es, int64_t *first, uint32_t *bytes) {
+    const int64_t per = 16 / es;
+    const int64_t a0 = e0 & ~(per - 1), a1 = (e1 + per - 1) & ~(per - 1);
+    *first = a0;
+    *bytes = e1 > e0 ? (uint32_t)((a1 - a0) * es) : 0u;
+}
+
+template <typename VT, typename AT>
+__device__ __forceinline__ AT sval(const VT *v, int k) {
+    if constexpr (std::is_same<VT, Pattern>::value) return AT(1);
+    else if constexpr (std::is_same<VT, __nv_bfloat16>::value) return AT(__bfloat162float(v[k]));
+    else return AT(v[k]);
+}
+
+// Operand loaders from a tile slot (values as stored, x from the gather buffer).
+template <typename VT, typename AT>
+struct NativeSLoad {
+    __device__ __forceinline__ static AT val(const VT *v, int k) { return sval<VT, AT>(v, k); }
+    template <typename XT> __device__ __forceinline__ static AT xs(const XT *xb, int k) { return AT(xb[k]); }
+};
+struct DfSLoad {   // values arrive pre-split into float pairs
+    __device__ __forceinline__ static float2 val(const float2 *v, int k) { return v[k]; }
+    __device__ __forceinline__ static float2 xs(const float2 *xb, int k) { return xb[k]; }
+};
+
+// Shared-memory slot of one warp tile: mbarrier, lane descriptors, column indices, values,
+// and the gathered x of the tile's nonzeros (reused for the finished rows once the lanes
+// hold their operands in registers).
+template <typename VT>
+struct WarpSlot {
+    static constexpr int DESC = 32;                                // uint32 per lane
+    static constexpr int COL = MW_ITEMS + 8;                       // int32 column indices
+    static constexpr int VAL = MW_ITEMS + 16;                      // values (VT)
+    static constexpr int VAL_BYTES = std::is_same<VT, Pattern>::value ? 0 : ((VAL * (int)sizeof(VT) + 15) / 16) * 16;
+    static constexpr int XB_BYTES = MW_ITEMS * 8;                  // gathered x, then finished rows
+    static constexpr int OFF_DESC = 16, OFF_COL = OFF_DESC + DESC * 4, OFF_VAL = OFF_COL + COL * 4,
+                         OFF_XB = OFF_VAL + VAL_BYTES;
+    static constexpr int BYTES = OFF_XB + XB_BYTES;
+};
+
+__device__ __forceinline__ void cp_async_gather(void *dst, const void *src, uint64_t pol, int bytes) {
+    if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;" :: "r"(smem_u32(dst)), "l"(src),
+                     "l"(pol) : "memory");
     else
-        merge_tile<NativeAcc<double>, NativeLoad<double, double>, double, double, double, IPT>(
-            row_ptr, col, val, x, y, part_row, part_nz, carry_row, carry_val, smem_raw);
+        asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" :: "r"(smem_u32(dst)), "l"(src),
+                     "l"(pol) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+// Bulk copies of one warp tile into a slot (lane 0): descriptors, column indices, values.
+// Completion is counted on the slot's mbarrier.
+template <typename VT>
+__device__ __forceinline__ void merge_warp_issue(const uint32_t *__restrict__ desc, const int32_t *__restrict__ col,
+                                                 const VT *__restrict__ val, int64_t t, int64_t j0, int nnzt,
+                                                 unsigned char *slot, uint64_t pol) {
+    using Slot = WarpSlot<VT>;
+    uint64_t *bar = (uint64_t *)slot;
+    int64_t col_first, val_first = j0;
+    uint32_t col_bytes, val_bytes = 0;
+    widen16(j0, j0 + nnzt, 4, &col_first, &col_bytes);
+    if constexpr (Slot::VAL_BYTES > 0) widen16(j0, j0 + nnzt, (int)sizeof(VT), &val_first, &val_bytes);
+    const uint32_t total = 128u + col_bytes + val_bytes;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(total) : "memory");
+    tma_load_1d(slot + Slot::OFF_DESC, desc + t * 32, 128u, bar, pol);
+    if (col_bytes) tma_load_1d(slot + Slot::OFF_COL, col + col_first, col_bytes, bar, pol);
+    if constexpr (Slot::VAL_BYTES > 0)
+        if (val_bytes) tma_load_1d(slot + Slot::OFF_VAL, val + val_first, val_bytes, bar, pol);
+}
+
+// Bounded wait for phase `parity` of a slot barrier (all lanes); false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (long long it = 0; it < MW_SPIN_LIMIT && !done; ++it)
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return __all_sync(0xffffffffu, done);
+}
+
+// Lane descriptor fields (see k_merge_desc in the conversion).
+__device__ __forceinline__ int desc_row(uint32_t d) { return (int)(d & 0xFFu); }
+__device__ __forceinline__ int desc_nz(uint32_t d) { return (int)((d >> 8) & 0xFFu); }
+__device__ __forceinline__ uint32_t desc_bits(uint32_t d) { return (d >> 16) & 0x7Fu; }
+__device__ __forceinline__ int desc_items(uint32_t d) { return (int)(d >> 24); }
+
+// Issue this lane's asynchronous gathers of x for its nonzeros of the tile in `slot`.
+template <typename VT, typename XG>
+__device__ __forceinline__ void merge_warp_gather(uint32_t d, int64_t j0, const XG *__restrict__ xg,
+                                                  unsigned char *slot, uint64_t keep_pol) {
+    using Slot = WarpSlot<VT>;
+    const int32_t *s_col = (const int32_t *)(slot + Slot::OFF_COL);
+    XG *xb = (XG *)(slot + Slot::OFF_XB);
+    const int col_off = (int)(j0 & 3), jb = desc_nz(d), items = desc_items(d);
+    const uint32_t bits = desc_bits(d);
+#pragma unroll
+    for (int k = 0; k < MW_IPT; ++k) {
+        if (k < items && !((bits >> k) & 1u)) {
+            const int jn = jb + k - __popc(bits & ((1u << k) - 1u));
+            cp_async_gather(xb + jn, xg + s_col[col_off + jn], keep_pol, (int)sizeof(XG));
+        }
+    }
+    cp_async_commit();
+}
+
+// Compute one warp tile whose operands are in `slot` (x already gathered).
+template <typename Acc, typename Load, typename VT, typename XG, typename XT>
+__device__ __forceinline__ void merge_warp_compute(uint32_t d, int64_t t, int64_t i0, int64_t j0, int nrows,
+                                                   XT *__restrict__ y, int32_t *__restrict__ carry_row,
+                                                   double *__restrict__ carry_val, unsigned char *slot) {
+    using Op = typename Acc::Op;
+    using Slot = WarpSlot<VT>;
+    const int lane = threadIdx.x & 31;
+    const VT *s_val = (const VT *)(slot + Slot::OFF_VAL);
+    const XG *xb = (const XG *)(slot + Slot::OFF_XB);
+    Acc *s_rows = (Acc *)(slot + Slot::OFF_XB);
+    const int perv = 16 / (int)(Slot::VAL_BYTES > 0 ? sizeof(VT) : 16);
+    const int val_off = (int)(j0 & (perv - 1));
+    const int istart = desc_row(d), jb = desc_nz(d), items = desc_items(d);
+    const uint32_t bits = desc_bits(d);
+    const int iend = istart + __popc(bits);
+    Op a[MW_IPT], xv[MW_IPT];
+#pragma unroll
+    for (int k = 0; k < MW_IPT; ++k) {
+        if (k < items && !((bits >> k) & 1u)) {
+            const int jn = jb + k - __popc(bits & ((1u << k) - 1u));
+            a[k] = Load::val(s_val, val_off + jn);
+            xv[k] = Load::xs(xb, jn);
+        }
+    }
+    __syncwarp();   // the x buffer becomes the finished-row buffer
+    Acc acc;
+    acc.zero();
+    int i = istart;
+#pragma unroll
+    for (int k = 0; k < MW_IPT; ++k) {
+        if (k < items) {
+            if ((bits >> k) & 1u) {   // row i ends here: stash it
+                s_rows[i] = acc;
+                acc.zero();
+                ++i;
+            } else {
+                acc.mad(a[k], xv[k]);
+            }
+        }
+    }
+    // segmented inclusive scan of the lanes' trailing partial sums (segments: equal end rows)
+    const int prev_end = __shfl_up_sync(0xffffffffu, iend, 1);
+    const bool head = lane == 0 || prev_end != iend;
+    Acc sv = acc;
+    bool f = head;
+    if (!__all_sync(0xffffffffu, head)) {
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            Acc ov = sv.shfl_up(o);
+            const bool of = __shfl_up_sync(0xffffffffu, f, o);
+            if (lane >= o) {
+                if (!f) {
+                    ov.add(sv);
+                    sv = ov;
+                }
+                f = f || of;
+            }
+        }
+    }
+    // lane l's first finished row takes the run sum of the lanes ending in that row (the
+    // run that ends at lane l-1), added before the lane's own part
+    const Acc cin = sv.shfl_up(1);
+    __syncwarp();
+    if (lane > 0 && istart < iend) {
+        Acc v = cin;
+        v.add(s_rows[istart]);
+        s_rows[istart] = v;
+    }
+    if (lane == 31) {
+        carry_row[t] = (int32_t)(i0 + nrows);
+        carry_val[t] = sv.to_double();
+    }
+    __syncwarp();
+    for (int r = lane; r < nrows; r += 32) y[i0 + r] = s_rows[r].template out<XT>();
+}
+
+// Persistent warp over tiles w, w + W, w + 2W, ... with two slots: while tile k is computed,
+// the gathers of x for tile k+1 (asynchronous copies into its slot) and the bulk copies of
+// tile k+2 are in flight.
+template <typename Acc, typename Load, typename VT, typename XG, typename XT>
+__device__ __forceinline__ void merge_warp_run(int64_t ntiles, const uint32_t *__restrict__ desc,
+                                               const int32_t *__restrict__ col, const VT *__restrict__ val,
+                                               const XG *__restrict__ xg, XT *__restrict__ y,
+                                               const int32_t *__restrict__ part_row,
+                                               const int32_t *__restrict__ part_nz, int32_t *__restrict__ carry_row,
+                                               double *__restrict__ carry_val, uint32_t *__restrict__ err,
+                                               unsigned char *wslots) {
+    using Slot = WarpSlot<VT>;
+    const int lane = threadIdx.x & 31;
+    const int64_t W = (int64_t)gridDim.x * MW_WARPS;
+    const int64_t w = (int64_t)blockIdx.x * MW_WARPS + (threadIdx.x >> 5);
+    if (w >= ntiles) return;
+    auto slot = [&](int i) { return wslots + i * Slot::BYTES; };
+    auto bar = [&](int i) { return (uint64_t *)(wslots + i * Slot::BYTES); };
+    const uint64_t stream_pol = l2_policy_evict_first(), keep_pol = l2_policy_evict_last();
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bar(0))) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bar(1))) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    auto part = [&](int64_t tt, int64_t &i0, int64_t &j0, int &nr, int &nz) {
+        i0 = part_row[tt];
+        j0 = part_nz[tt];
+        nr = (int)(part_row[tt + 1] - i0);
+        nz = (int)(part_nz[tt + 1] - j0);
+    };
+    int64_t t = w;
+    int64_t ci0, cj0, ni0 = 0, nj0 = 0;
+    int cnr, cnz, nnr = 0, nnz_ = 0;
+    part(t, ci0, cj0, cnr, cnz);
+    if (lane == 0) merge_warp_issue<VT>(desc, col, val, t, cj0, cnz, slot(0), stream_pol);
+    if (!mbar_wait(bar(0), 0u)) {
+        if (lane == 0) atomicOr(err, ST_TIMEOUT);
+        return;
+    }
+    uint32_t dcur = ((const uint32_t *)(slot(0) + Slot::OFF_DESC))[lane];
+    merge_warp_gather<VT, XG>(dcur, cj0, xg, slot(0), keep_pol);
+    if (t + W < ntiles) {
+        part(t + W, ni0, nj0, nnr, nnz_);
+        if (lane == 0) merge_warp_issue<VT>(desc, col, val, t + W, nj0, nnz_, slot(1), stream_pol);
+    }
+    for (int64_t k = 0; t < ntiles; ++k, t += W) {
+        const int cs = (int)(k & 1), ns = cs ^ 1;
+        const bool has_next = t + W < ntiles;
+        uint32_t dnxt = 0;
+        if (has_next) {   // the next tile's copies have landed: start its gathers
+            if (!mbar_wait(bar(ns), (uint32_t)(((k + 1) >> 1) & 1))) {
+                if (lane == 0) atomicOr(err, ST_TIMEOUT);
+                cp_async_wait<0>();
+                return;
+            }
+            dnxt = ((const uint32_t *)(slot(ns) + Slot::OFF_DESC))[lane];
+            merge_warp_gather<VT, XG>(dnxt, nj0, xg, slot(ns), keep_pol);
+            cp_async_wait<1>();   // this lane's gathers of tile t are complete
+        } else {
+            cp_async_wait<0>();
+        }
+        merge_warp_compute<Acc, Load, VT, XG, XT>(dcur, t, ci0, cj0, cnr, y, carry_row, carry_val, slot(cs));
+        __syncwarp();   // slot cs is free
+        int64_t fi0 = 0, fj0 = 0;
+        int fnr = 0, fnz = 0;
+        if (t + 2 * W < ntiles) {
+            part(t + 2 * W, fi0, fj0, fnr, fnz);
+            if (lane == 0) merge_warp_issue<VT>(desc, col, val, t + 2 * W, fj0, fnz, slot(cs), stream_pol);
+        }
+        dcur = dnxt;
+        ci0 = ni0; cj0 = nj0; cnr = nnr; cnz = nnz_;
+        ni0 = fi0; nj0 = fj0; nnr = fnr; nnz_ = fnz;
+    }
+}
+
+template <typename VT, typename XT, typename AT>
+__global__ __launch_bounds__(MW_WARPS * 32) void k_merge_warp(const uint32_t *__restrict__ desc,
+                                                              const int32_t *__restrict__ col,
+                                                              const VT *__restrict__ val, const XT *__restrict__ x,
+                                                              XT *__restrict__ y, const int32_t *__restrict__ part_row,
+                                                              const int32_t *__restrict__ part_nz,
+                                                              int32_t *__restrict__ carry_row,
+                                                              double *__restrict__ carry_val, int64_t ntiles,
+                                                              uint32_t *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    merge_warp_run<NativeAcc<AT>, NativeSLoad<VT, AT>, VT, XT, XT>(ntiles, desc, col, val, x, y, part_row, part_nz,
+                                                                  carry_row, carry_val, err,
+                                                                  smem_raw + (threadIdx.x >> 5) * 2 * WarpSlot<VT>::BYTES);
+}
+
+// FP64 through double-float: val2 holds the stored values split into float pairs at the
+// conversion, x2 holds x split per product; *xflag non-zero (some x outside the window)
+// makes the product use native FP64 on val and x instead.
+static_assert(WarpSlot<float2>::BYTES == WarpSlot<double>::BYTES, "same slot for both paths");
+
+__global__ __launch_bounds__(MW_WARPS * 32) void k_merge_warp_df(const uint32_t *__restrict__ desc,
+                                                                 const int32_t *__restrict__ col,
+                                                                 const double *__restrict__ val,
+                                                                 const float2 *__restrict__ val2,
+                                                                 const double *__restrict__ x,
+                                                                 const float2 *__restrict__ x2,
+                                                                 const uint32_t *__restrict__ xflag,
+                                                                 double *__restrict__ y,
+                                                                 const int32_t *__restrict__ part_row,
+                                                                 const int32_t *__restrict__ part_nz,
+                                                                 int32_t *__restrict__ carry_row,
+                                                                 double *__restrict__ carry_val, int64_t ntiles,
+                                                                 uint32_t *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *ws = smem_raw + (threadIdx.x >> 5) * 2 * WarpSlot<double>::BYTES;
+    if (*xflag == 0u)
+        merge_warp_run<DfAcc, DfSLoad, float2, float2, double>(ntiles, desc, col, val2, x2, y, part_row, part_nz,
+                                                               carry_row, carry_val, err, ws);
+    else
+        merge_warp_run<NativeAcc<double>, NativeSLoad<double, double>, double, double, double>(
+            ntiles, desc, col, val, x, y, part_row, part_nz, carry_row, carry_val, err, ws);
 }
 
 // x -> (hi, lo) float pairs; flags values outside the double-float window.
@@ -301,6 +613,25 @@ __global__ void k_merge_fixup(int64_t tiles, int64_t m, const int32_t *__restric
     if (row < m) y[row] = XT((double)y[row] + s);
 }
 
+// Persistent grid: resident CTAs on every SM (occupancy from the runtime), never more
+// warps than tiles.
+inline unsigned persistent_grid(const void *kernel, int block, size_t smem, int64_t tiles) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const int64_t want = (tiles + MW_WARPS - 1) / MW_WARPS;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per_sm));
+}
+
 template <typename Acc>
 constexpr size_t merge_smem(int ipt) {
     return (size_t)MP_BLOCK * ipt * (sizeof(Acc) + 4) + (MP_BLOCK + 32) * 4 + (MP_BLOCK + 32) * sizeof(Acc);
@@ -310,14 +641,15 @@ template <typename VT, typename XT, typename AT, int IPT>
 spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allow_df, cudaStream_t s) {
     constexpr bool FP64 = std::is_same<VT, double>::value && std::is_same<XT, double>::value &&
                           std::is_same<AT, double>::value;
+    constexpr size_t smem = (size_t)MW_WARPS * 2 * WarpSlot<VT>::BYTES;
     if constexpr (FP64) {
-        if (allow_df && h->df_ok && h->xsplit) {
-            constexpr size_t smem = merge_smem<NativeAcc<double>>(IPT);   // >= the double-float layout
-            static_assert(sizeof(DfAcc) == sizeof(NativeAcc<double>), "same staging layout");
+        if (allow_df && h->df_ok && h->xsplit && h->val2) {
+            constexpr size_t smem_df = (size_t)MW_WARPS * 2 * WarpSlot<double>::BYTES;
+            const unsigned grid = persistent_grid((const void *)k_merge_warp_df, MW_WARPS * 32, smem_df, h->tiles);
             static bool attr = false;
             if (!attr) {
-                SPMV_CUDA_TRY(cudaFuncSetAttribute(k_merge_spmv_df<IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)smem));
+                SPMV_CUDA_TRY(cudaFuncSetAttribute(k_merge_warp_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem_df));
                 attr = true;
             }
             SPMV_CUDA_TRY(cudaMemsetAsync(h->xsplit_flag, 0, 4, s));
@@ -328,9 +660,11 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
                 SPMV_LAUNCH_CHECK("x split");
             }
             SPMV_LAUNCH("k_merge_spmv", s,
-                        (k_merge_spmv_df<IPT><<<(unsigned)h->tiles, MP_BLOCK, smem, s>>>(
-                            h->row_ptr, h->col, (const double *)h->val, (const double *)x, h->xsplit, h->xsplit_flag,
-                            (double *)y, h->part_row, h->part_nz, h->carry_row, h->carry_val)));
+                        (k_merge_warp_df<<<grid, MW_WARPS * 32, smem_df, s>>>(
+                            h->merge_desc, h->col, (const double *)h->val, h->val2, (const double *)x, h->xsplit,
+                            h->xsplit_flag,
+                            (double *)y, h->part_row, h->part_nz, h->carry_row, h->carry_val, h->tiles,
+                            h->status_dev + 3)));
             SPMV_LAUNCH_CHECK("merge spmv");
             SPMV_LAUNCH("k_merge_fixup", s, (k_merge_fixup<double><<<cdivu(h->tiles, 256), 256, 0, s>>>(
                                                 h->tiles, h->m, h->carry_row, h->carry_val, (double *)y)));
@@ -338,16 +672,16 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
             return SPMV_OK;
         }
     }
-    constexpr size_t smem = merge_smem<NativeAcc<AT>>(IPT);
     static bool attr = false;
     if (!attr) {
-        SPMV_CUDA_TRY(cudaFuncSetAttribute(k_merge_spmv<VT, XT, AT, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        SPMV_CUDA_TRY(cudaFuncSetAttribute(k_merge_warp<VT, XT, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem));
         attr = true;
     }
-    SPMV_LAUNCH("k_merge_spmv", s, (k_merge_spmv<VT, XT, AT, IPT><<<(unsigned)h->tiles, MP_BLOCK, smem, s>>>(
-                                       h->row_ptr, h->col, (const VT *)h->val, (const XT *)x, (XT *)y, h->part_row,
-                                       h->part_nz, h->carry_row, h->carry_val)));
+    const unsigned grid = persistent_grid((const void *)k_merge_warp<VT, XT, AT>, MW_WARPS * 32, smem, h->tiles);
+    SPMV_LAUNCH("k_merge_spmv", s, (k_merge_warp<VT, XT, AT><<<grid, MW_WARPS * 32, smem, s>>>(
+                                       h->merge_desc, h->col, (const VT *)h->val, (const XT *)x, (XT *)y, h->part_row,
+                                       h->part_nz, h->carry_row, h->carry_val, h->tiles, h->status_dev + 3)));
     SPMV_LAUNCH_CHECK("merge spmv");
     SPMV_LAUNCH("k_merge_fixup", s, (k_merge_fixup<XT><<<cdivu(h->tiles, 256), 256, 0, s>>>(
                                         h->tiles, h->m, h->carry_row, h->carry_val, (XT *)y)));
