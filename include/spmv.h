@@ -85,7 +85,11 @@ typedef struct {
  *                     4e-14 * (|A||x|)_i), otherwise with native FP64.  Other data: F32.
  *   SPMV_ACC_F64      native FP64 arithmetic throughout.
  *   SPMV_ACC_F32      FP32 accumulation.
- *   SPMV_ACC_COMPENSATED  FP32 with two-sum compensation on long rows.
+ *   SPMV_ACC_COMPENSATED  FP32 vectors and values: FP32 products and sums whose rounding
+ *                     errors are collected in a second FP32 term (FMA product errors,
+ *                     TwoSum addition errors); CSR_MERGE only.  The compensation runs on
+ *                     every row: on GB300 its extra FP32 operations cost less than the
+ *                     memory traffic they overlap, so no row-length threshold is applied.
  */
 #define SPMV_ACC_DEFAULT 0u
 #define SPMV_ACC_F32 1u
@@ -198,6 +202,24 @@ const char *spmv_status_string(spmv_status s);
  * points (device arrays rows, cols -> keys).  Exposed for testing the key kernel. */
 spmv_status spmv_hilbert_keys(int K, int64_t n, const int32_t *rows, const int32_t *cols, uint64_t *keys,
                               void *stream);
+
+/* ---------------------------------------------------------------- PageRank */
+
+/*
+ * spmv_pagerank -- PageRank by power iteration on the square matrix of h (Section 1 names
+ * PageRank among the applications built on SpMV; the paper does not define it, so the
+ * iteration is stated here).  Stored values are ignored: a stored entry (i, j) is an edge
+ * j -> i, and the out-degree of j is the number of stored entries in column j.
+ *   x0 = 1/n;  for each iteration:  dangling = sum of x_j over columns of out-degree 0,
+ *   x_i <- damping * ( sum_j A_ij x_j / outdeg_j + dangling / n ) + (1 - damping) / n.
+ *   damping     in [0, 1] (0.85 is customary);  iters: number of iterations, 0..10000.
+ *   x           device array of n doubles; receives the final vector (it is also the
+ *               working vector of the iteration).
+ * Builds the CRS arrays and the merge-path partition if needed.  The iterations are
+ * captured into a CUDA graph on the first call for a given (x, iters, damping) and the
+ * graph is replayed on `stream` (asynchronously) by this and later calls.
+ */
+spmv_status spmv_pagerank(spmv_handle h, double damping, int iters, double *x, void *stream);
 
 /* ---------------------------------------------------------------- no allocation */
 

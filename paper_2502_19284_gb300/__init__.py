@@ -61,6 +61,7 @@ _SIG = {
     "spmv_export_merge_partition": [_p, _p, _p],
     "spmv_hilbert_keys": [_i32, _i64, _p, _p, _p, _p],
     "spmv_mul_csr_merge_noalloc": [_i64, _i64, _i64, _p, _p, _p, _p, _p, _p],
+    "spmv_pagerank": [_p, ctypes.c_double, _i32, _p, _p],
 }
 for _name, _args in _SIG.items():
     _f = getattr(_lib, _name)
@@ -240,6 +241,12 @@ def spmv_mul_csr_merge_noalloc(m, n, nnz, row_ptr, col_ind, data, x, y, stream=N
     _check(_lib.spmv_mul_csr_merge_noalloc(m, n, nnz, _addr(row_ptr), _addr(col_ind), _addr(data), _addr(x),
                                            _addr(y), _stream(stream)), "spmv_mul_csr_merge_noalloc")
     return y
+
+
+def spmv_pagerank(h: Handle, x, damping=0.85, iters=20, stream=None):
+    """PageRank power iteration into the device float64 tensor x (n entries); see spmv.h."""
+    _check(_lib.spmv_pagerank(h.ptr, float(damping), int(iters), _addr(x), _stream(stream)), "spmv_pagerank")
+    return x
 
 
 def spmv_trace_enable(on: bool = True):

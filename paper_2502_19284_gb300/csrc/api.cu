@@ -90,6 +90,8 @@ bool trace_on() { return g_trace.load(std::memory_order_relaxed); }
 
 TraceScope::TraceScope(const char *n, cudaStream_t st) : name(n), s(st) {
     if (!trace_on()) return;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventRecord(a, s) != cudaSuccess) {
         if (a) cudaEventDestroy(a);
         a = nullptr;
@@ -154,7 +156,9 @@ bool is_device_ptr(const void *p) {
 void free_all(spmv_matrix *h) {
     void *ptrs[] = {h->coo_row, h->coo_col, h->coo_val, h->row_ptr, h->col, h->val, h->bin_rows,
                     h->part_row, h->part_nz, h->carry_row, h->carry_val, h->merge_desc, h->hb_idx, h->hb_val,
-                    h->blk_ptr, h->blk_row, h->blk_col, h->val2, h->xsplit, h->xsplit_flag, h->status_dev};
+                    h->blk_ptr, h->blk_row, h->blk_col, h->val2, h->xsplit, h->xsplit_flag,
+                    h->pr_inv, h->pr_z, h->pr_z2, h->pr_y, h->pr_part, h->status_dev};
+    if (h->pr_graph) cudaGraphExecDestroy((cudaGraphExec_t)h->pr_graph);
     for (void *p : ptrs) dev_free(p);
     if (h->status_host) cudaFreeHost(h->status_host);
 }
@@ -358,10 +362,6 @@ spmv_status spmv_mul(spmv_handle h, const void *x, void *y, spmv_dtype vec_dt, u
         set_error("spmv_mul: unknown vector dtype or accumulation mode");
         return SPMV_ERR_INVALID_ARG;
     }
-    if (accum == SPMV_ACC_COMPENSATED) {
-        set_error("spmv_mul: compensated accumulation is not built in");
-        return SPMV_ERR_UNSUPPORTED;
-    }
     if (h->m == 0) return SPMV_OK;
     cudaStream_t s = (cudaStream_t)stream;
     switch (h->format) {
@@ -472,6 +472,20 @@ spmv_status spmv_mul_csr_merge_noalloc(int64_t m, int64_t n, int64_t nnz, const 
     }
     if (m == 0) return SPMV_OK;
     return mul_csr_merge_noalloc(m, n, nnz, row_ptr, col_ind, data, x, y, (cudaStream_t)stream);
+}
+
+spmv_status spmv_pagerank(spmv_handle h, double damping, int iters, double *x, void *stream) {
+    g_err.clear();
+    SPMV_TRY(check_handle(h));
+    if (h->m != h->n || !(damping >= 0.0 && damping <= 1.0) || iters < 0 || iters > 10000 || (h->n > 0 && !x)) {
+        set_error("spmv_pagerank: needs a square matrix, damping in [0, 1], 0 <= iters <= 10000 and x");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    if (h->n == 0) return SPMV_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!h->has_csr) SPMV_TRY(build_csr(h, s));
+    if (!h->has_merge) SPMV_TRY(build_merge(h, MERGE_WARP_ITEMS, s));
+    return pagerank(h, damping, iters, x, s);
 }
 
 spmv_status spmv_hilbert_keys(int K, int64_t n, const int32_t *rows, const int32_t *cols, uint64_t *keys,

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <algorithm>
 #include <string>
 
 #include "../../include/spmv.h"
@@ -141,7 +142,8 @@ struct spmv_matrix {
     int64_t tiles = 0;
     int32_t *part_row = nullptr, *part_nz = nullptr;
     int32_t *carry_row = nullptr;
-    double *carry_val = nullptr;
+    double *carry_val = nullptr;      // tiles carries, then tiles head partials (a tile's first
+                                      // row when it began in an earlier tile)
     uint32_t *merge_desc = nullptr;   // per-lane descriptors of the warp tiles (32 words per tile)
 
     // Hilbert-ordered blocked format
@@ -158,6 +160,14 @@ struct spmv_matrix {
     float2 *val2 = nullptr;           // CRS values split into float pairs (when df_ok)
     float2 *xsplit = nullptr;
     uint32_t *xsplit_flag = nullptr;
+
+    // PageRank buffers and the captured iteration graph
+    double *pr_inv = nullptr, *pr_z = nullptr, *pr_y = nullptr, *pr_part = nullptr;
+    float2 *pr_z2 = nullptr;
+    void *pr_graph = nullptr;         // cudaGraphExec_t
+    const double *pr_graph_x = nullptr;
+    int pr_graph_iters = 0;
+    double pr_graph_damping = 0.0;
 
     uint32_t *status_dev = nullptr;   // device status word
     uint32_t *status_host = nullptr;  // pinned read-back slot

@@ -201,7 +201,8 @@ __device__ __forceinline__ int64_t merge_split(int64_t d, int64_t m, int64_t nnz
 // lane).  Row end r of a tile sits at path position r + (nonzeros of the tile before it); for
 // lane l, covering positions [7l, 7l + 7): bits 0-7 the number of row ends before its range
 // (its first row), bits 8-15 the number of nonzeros before it (its first nonzero), bits
-// 16-22 which of its items are row ends, bits 24-26 how many items it has.
+// 16-22 which of its items are row ends, bits 24-26 how many items it has; bit 31 (lane 0)
+// marks a tile whose first row began in an earlier tile.
 __global__ void k_merge_desc(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ part_row,
                              const int32_t *__restrict__ part_nz, int64_t tiles, uint32_t *__restrict__ desc) {
     __shared__ uint32_t s_bits[8][8];
@@ -226,7 +227,11 @@ __global__ void k_merge_desc(const int32_t *__restrict__ row_ptr, const int32_t 
     before += __popc(lo & ((1u << b0) - 1u));
     const uint32_t span = b0 ? (lo >> b0) | (hi << (32 - b0)) : lo;
     const uint32_t bits = span & ((1u << (d1 - d0)) - 1u);
-    desc[t * 32 + lane] = (uint32_t)before | ((uint32_t)(d0 - before) << 8) | (bits << 16) | ((uint32_t)(d1 - d0) << 24);
+    // bit 31 of lane 0: the tile's first row started in an earlier tile (its value is
+    // completed by the carry fix-up)
+    const uint32_t cont = (lane == 0 && nrows > 0 && row_ptr[i0] < j0) ? (1u << 31) : 0u;
+    desc[t * 32 + lane] =
+        (uint32_t)before | ((uint32_t)(d0 - before) << 8) | (bits << 16) | ((uint32_t)(d1 - d0) << 24) | cont;
 }
 
 __global__ void k_merge_partition(const int32_t *__restrict__ row_ptr, int64_t m, int64_t nnz, int64_t tiles,
@@ -590,7 +595,7 @@ spmv_status build_merge(spmv_matrix *h, int tile_items, cudaStream_t s) {
     SPMV_TRY(pr.alloc((size_t)(tiles + 1) * 4, "merge partition"));
     SPMV_TRY(pn.alloc((size_t)(tiles + 1) * 4, "merge partition"));
     SPMV_TRY(cr.alloc((size_t)tiles * 4, "merge carries"));
-    SPMV_TRY(cv.alloc((size_t)tiles * 8, "merge carries"));
+    SPMV_TRY(cv.alloc((size_t)tiles * 16, "merge carries"));   // tile carries, then head partials
     SPMV_LAUNCH("k_merge_partition", s, (k_merge_partition<<<grid_for(tiles + 1), CB, 0, s>>>(h->row_ptr, h->m, h->nnz, tiles, tile_items,
                                                          pr.as<int32_t>(), pn.as<int32_t>())));
     SPMV_LAUNCH_CHECK("merge partition");
@@ -600,7 +605,7 @@ spmv_status build_merge(spmv_matrix *h, int tile_items, cudaStream_t s) {
     if (h->has_merge) {
         dev_free_async(h->part_row, s); dev_free_async(h->part_nz, s);
         dev_free_async(h->carry_row, s); dev_free_async(h->carry_val, s); dev_free_async(h->merge_desc, s);
-        h->bytes -= (h->tiles + 1) * 8 + h->tiles * 12 + h->tiles * 128;
+        h->bytes -= (h->tiles + 1) * 8 + h->tiles * 20 + h->tiles * 128;
     }
     h->merge_desc = (uint32_t *)ds.release();
     h->part_row = (int32_t *)pr.release();
@@ -610,7 +615,7 @@ spmv_status build_merge(spmv_matrix *h, int tile_items, cudaStream_t s) {
     h->tiles = tiles;
     h->tile_items = tile_items;
     h->has_merge = true;
-    h->bytes += (tiles + 1) * 8 + tiles * 12 + tiles * 128;
+    h->bytes += (tiles + 1) * 8 + tiles * 20 + tiles * 128;
     return SPMV_OK;
 }
 

@@ -48,6 +48,11 @@ spmv_status mul_merge(const spmv_matrix *h, const void *x, void *y, spmv_dtype v
 // (the FP64 products use double-float arithmetic when acc == SPMV_ACC_DEFAULT and h->df_ok)
 spmv_status mul_rowsplit(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s);
 spmv_status mul_hb(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s);
+// Pattern product (values taken as 1) y = A x through the merge warp tiles, with x already
+// split into float pairs in x2 (*xflag non-zero: use native FP64 on x).
+spmv_status mul_merge_pattern_split(const spmv_matrix *h, const double *x, const float2 *x2, const uint32_t *xflag,
+                                    double *y, cudaStream_t s);
+spmv_status pagerank(spmv_matrix *h, double damping, int iters, double *x, cudaStream_t s);
 spmv_status mul_csr_merge_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col,
                                   const double *data, const double *x, double *y, cudaStream_t s);
 

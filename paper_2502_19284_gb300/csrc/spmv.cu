@@ -85,6 +85,26 @@ struct DfAcc {
     template <typename XT> __device__ __forceinline__ XT out() const { return XT(df_to_double(s, c)); }
 };
 
+// FP32 sum with compensation (SPMV_ACC_COMPENSATED): the rounding error of every product
+// (FMA) and of every addition (TwoSum, Knuth) is collected in a second float, as in
+// Neumaier's compensated summation; the result carries ~2^-46 relative error in the sum of
+// |terms| instead of FP32's L * 2^-24.
+struct CompAcc {
+    using Op = float;
+    float s, c;
+    __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
+    __device__ __forceinline__ void mad(float a, float x) { df_fma(a, 0.f, x, 0.f, s, c); }
+    __device__ __forceinline__ void add(const CompAcc &o) { df_add(s, c, o.s, o.c); }
+    __device__ __forceinline__ CompAcc shfl_up(int o) const {
+        CompAcc r;
+        r.s = __shfl_up_sync(0xffffffffu, s, o);
+        r.c = __shfl_up_sync(0xffffffffu, c, o);
+        return r;
+    }
+    __device__ __forceinline__ double to_double() const { return df_to_double(s, c); }
+    template <typename XT> __device__ __forceinline__ XT out() const { return XT(__fadd_rn(s, c)); }
+};
+
 // Operand loaders: native (value converted to AT) or split into double-float pairs.
 template <typename VT, typename AT>
 struct NativeLoad {
@@ -395,7 +415,8 @@ __device__ __forceinline__ void merge_warp_gather(uint32_t d, int64_t j0, const 
 template <typename Acc, typename Load, typename VT, typename XG, typename XT>
 __device__ __forceinline__ void merge_warp_compute(uint32_t d, int64_t t, int64_t i0, int64_t j0, int nrows,
                                                    XT *__restrict__ y, int32_t *__restrict__ carry_row,
-                                                   double *__restrict__ carry_val, unsigned char *slot) {
+                                                   double *__restrict__ carry_val, double *__restrict__ head_val,
+                                                   unsigned char *slot) {
     using Op = typename Acc::Op;
     using Slot = WarpSlot<VT>;
     const int lane = threadIdx.x & 31;
@@ -465,7 +486,10 @@ __device__ __forceinline__ void merge_warp_compute(uint32_t d, int64_t t, int64_
         carry_val[t] = sv.to_double();
     }
     __syncwarp();
-    for (int r = lane; r < nrows; r += 32) y[i0 + r] = s_rows[r].template out<XT>();
+    // a first row that began in an earlier tile is completed by the fix-up: park its partial
+    const bool cont = (__shfl_sync(0xffffffffu, d, 0) >> 31) != 0u;
+    if (cont && lane == 0 && nrows > 0) head_val[t] = s_rows[0].to_double();
+    for (int r = (cont ? 1 : 0) + lane; r < nrows; r += 32) y[i0 + r] = s_rows[r].template out<XT>();
 }
 
 // Persistent warp over tiles w, w + W, w + 2W, ... with two slots: while tile k is computed,
@@ -530,7 +554,8 @@ __device__ __forceinline__ void merge_warp_run(int64_t ntiles, const uint32_t *_
         } else {
             cp_async_wait<0>();
         }
-        merge_warp_compute<Acc, Load, VT, XG, XT>(dcur, t, ci0, cj0, cnr, y, carry_row, carry_val, slot(cs));
+        merge_warp_compute<Acc, Load, VT, XG, XT>(dcur, t, ci0, cj0, cnr, y, carry_row, carry_val, carry_val + ntiles,
+                                                  slot(cs));
         __syncwarp();   // slot cs is free
         int64_t fi0 = 0, fj0 = 0;
         int fnr = 0, fnz = 0;
@@ -559,6 +584,23 @@ __global__ __launch_bounds__(MW_WARPS * 32) void k_merge_warp(const uint32_t *__
                                                                   smem_raw + (threadIdx.x >> 5) * 2 * WarpSlot<VT>::BYTES);
 }
 
+// FP32 or bfloat16 values with FP32 vectors, compensated FP32 accumulation.
+template <typename VT>
+__global__ __launch_bounds__(MW_WARPS * 32) void k_merge_warp_comp(const uint32_t *__restrict__ desc,
+                                                                   const int32_t *__restrict__ col,
+                                                                   const VT *__restrict__ val,
+                                                                   const float *__restrict__ x, float *__restrict__ y,
+                                                                   const int32_t *__restrict__ part_row,
+                                                                   const int32_t *__restrict__ part_nz,
+                                                                   int32_t *__restrict__ carry_row,
+                                                                   double *__restrict__ carry_val, int64_t ntiles,
+                                                                   uint32_t *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    merge_warp_run<CompAcc, NativeSLoad<VT, float>, VT, float, float>(ntiles, desc, col, val, x, y, part_row, part_nz,
+                                                                     carry_row, carry_val, err,
+                                                                     smem_raw + (threadIdx.x >> 5) * 2 * WarpSlot<VT>::BYTES);
+}
+
 // FP64 through double-float: val2 holds the stored values split into float pairs at the
 // conversion, x2 holds x split per product; *xflag non-zero (some x outside the window)
 // makes the product use native FP64 on val and x instead.
@@ -585,6 +627,34 @@ __global__ __launch_bounds__(MW_WARPS * 32) void k_merge_warp_df(const uint32_t 
     else
         merge_warp_run<NativeAcc<double>, NativeSLoad<double, double>, double, double, double>(
             ntiles, desc, col, val, x, y, part_row, part_nz, carry_row, carry_val, err, ws);
+}
+
+// Pattern matrix (every stored value 1) with an FP64 vector through double-float: the value
+// operand is the constant pair (1, 0).
+struct DfPatLoad {
+    __device__ __forceinline__ static float2 val(const Pattern *, int) { return make_float2(1.f, 0.f); }
+    __device__ __forceinline__ static float2 xs(const float2 *xb, int k) { return xb[k]; }
+};
+
+__global__ __launch_bounds__(MW_WARPS * 32) void k_merge_warp_pat_df(const uint32_t *__restrict__ desc,
+                                                                     const int32_t *__restrict__ col,
+                                                                     const double *__restrict__ x,
+                                                                     const float2 *__restrict__ x2,
+                                                                     const uint32_t *__restrict__ xflag,
+                                                                     double *__restrict__ y,
+                                                                     const int32_t *__restrict__ part_row,
+                                                                     const int32_t *__restrict__ part_nz,
+                                                                     int32_t *__restrict__ carry_row,
+                                                                     double *__restrict__ carry_val, int64_t ntiles,
+                                                                     uint32_t *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *ws = smem_raw + (threadIdx.x >> 5) * 2 * WarpSlot<Pattern>::BYTES;
+    if (*xflag == 0u)
+        merge_warp_run<DfAcc, DfPatLoad, Pattern, float2, double>(ntiles, desc, col, nullptr, x2, y, part_row, part_nz,
+                                                                  carry_row, carry_val, err, ws);
+    else
+        merge_warp_run<NativeAcc<double>, NativeSLoad<Pattern, double>, Pattern, double, double>(
+            ntiles, desc, col, nullptr, x, y, part_row, part_nz, carry_row, carry_val, err, ws);
 }
 
 // x -> (hi, lo) float pairs; flags values outside the double-float window.
@@ -632,6 +702,26 @@ inline unsigned persistent_grid(const void *kernel, int block, size_t smem, int6
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per_sm));
 }
 
+// Carry fix-up of the warp tiles: the first tile of each run of equal carry rows sums the
+// run's carries in tile order; the tile after the run finished that row: if it marked the
+// row as begun earlier, its parked partial is added and the row written once (one rounding
+// to the output type); otherwise the run's carries are all zero and y is left as written.
+template <typename XT>
+__global__ void k_merge_fixup_tiles(int64_t tiles, int64_t m, const int32_t *__restrict__ carry_row,
+                                    const double *__restrict__ carry_val, const uint32_t *__restrict__ desc,
+                                    XT *__restrict__ y) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tiles) return;
+    const int32_t row = carry_row[t];
+    if (t > 0 && carry_row[t - 1] == row) return;
+    double s = carry_val[t];
+    int64_t u = t + 1;
+    for (; u < tiles && carry_row[u] == row; ++u) s = s + carry_val[u];
+    if (row >= m || u >= tiles) return;
+    if (desc[u * 32] >> 31) y[row] = XT(s + carry_val[tiles + u]);
+    else if (s != 0.0) y[row] = XT((double)y[row] + s);
+}
+
 template <typename Acc>
 constexpr size_t merge_smem(int ipt) {
     return (size_t)MP_BLOCK * ipt * (sizeof(Acc) + 4) + (MP_BLOCK + 32) * 4 + (MP_BLOCK + 32) * sizeof(Acc);
@@ -645,13 +735,13 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
     if constexpr (FP64) {
         if (allow_df && h->df_ok && h->xsplit && h->val2) {
             constexpr size_t smem_df = (size_t)MW_WARPS * 2 * WarpSlot<double>::BYTES;
-            const unsigned grid = persistent_grid((const void *)k_merge_warp_df, MW_WARPS * 32, smem_df, h->tiles);
             static bool attr = false;
             if (!attr) {
                 SPMV_CUDA_TRY(cudaFuncSetAttribute(k_merge_warp_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)smem_df));
                 attr = true;
             }
+            const unsigned grid = persistent_grid((const void *)k_merge_warp_df, MW_WARPS * 32, smem_df, h->tiles);
             SPMV_CUDA_TRY(cudaMemsetAsync(h->xsplit_flag, 0, 4, s));
             if (h->n > 0) {
                 SPMV_LAUNCH("k_df_split_x", s,
@@ -666,8 +756,9 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
                             (double *)y, h->part_row, h->part_nz, h->carry_row, h->carry_val, h->tiles,
                             h->status_dev + 3)));
             SPMV_LAUNCH_CHECK("merge spmv");
-            SPMV_LAUNCH("k_merge_fixup", s, (k_merge_fixup<double><<<cdivu(h->tiles, 256), 256, 0, s>>>(
-                                                h->tiles, h->m, h->carry_row, h->carry_val, (double *)y)));
+            SPMV_LAUNCH("k_merge_fixup", s, (k_merge_fixup_tiles<double><<<cdivu(h->tiles, 256), 256, 0, s>>>(
+                                                h->tiles, h->m, h->carry_row, h->carry_val, h->merge_desc,
+                                                (double *)y)));
             SPMV_LAUNCH_CHECK("merge fixup");
             return SPMV_OK;
         }
@@ -683,8 +774,8 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
                                        h->merge_desc, h->col, (const VT *)h->val, (const XT *)x, (XT *)y, h->part_row,
                                        h->part_nz, h->carry_row, h->carry_val, h->tiles, h->status_dev + 3)));
     SPMV_LAUNCH_CHECK("merge spmv");
-    SPMV_LAUNCH("k_merge_fixup", s, (k_merge_fixup<XT><<<cdivu(h->tiles, 256), 256, 0, s>>>(
-                                        h->tiles, h->m, h->carry_row, h->carry_val, (XT *)y)));
+    SPMV_LAUNCH("k_merge_fixup", s, (k_merge_fixup_tiles<XT><<<cdivu(h->tiles, 256), 256, 0, s>>>(
+                                        h->tiles, h->m, h->carry_row, h->carry_val, h->merge_desc, (XT *)y)));
     SPMV_LAUNCH_CHECK("merge fixup");
     return SPMV_OK;
 }
@@ -870,6 +961,26 @@ spmv_status launch_hb(const spmv_matrix *h, const void *x, void *y, cudaStream_t
 // BF16/F32/F32; BF16/F32/F64; PATTERN/F64/F64; PATTERN/F32/F32.
 enum Algo { MERGE, ROWSPLIT, HB };
 
+template <typename VT>
+spmv_status launch_merge_comp(const spmv_matrix *h, const void *x, void *y, cudaStream_t s) {
+    constexpr size_t smem = (size_t)MW_WARPS * 2 * WarpSlot<VT>::BYTES;
+    static bool attr = false;
+    if (!attr) {
+        SPMV_CUDA_TRY(cudaFuncSetAttribute(k_merge_warp_comp<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    const unsigned grid = persistent_grid((const void *)k_merge_warp_comp<VT>, MW_WARPS * 32, smem, h->tiles);
+    SPMV_LAUNCH("k_merge_spmv", s, (k_merge_warp_comp<VT><<<grid, MW_WARPS * 32, smem, s>>>(
+                                       h->merge_desc, h->col, (const VT *)h->val, (const float *)x, (float *)y,
+                                       h->part_row, h->part_nz, h->carry_row, h->carry_val, h->tiles,
+                                       h->status_dev + 3)));
+    SPMV_LAUNCH_CHECK("merge spmv");
+    SPMV_LAUNCH("k_merge_fixup", s, (k_merge_fixup_tiles<float><<<cdivu(h->tiles, 256), 256, 0, s>>>(
+                                        h->tiles, h->m, h->carry_row, h->carry_val, h->merge_desc, (float *)y)));
+    SPMV_LAUNCH_CHECK("merge fixup");
+    return SPMV_OK;
+}
+
 template <typename VT, typename XT, typename AT>
 spmv_status run_algo(Algo a, const spmv_matrix *h, const void *x, void *y, bool allow_df, cudaStream_t s) {
     if (a == MERGE) return launch_merge<VT, XT, AT, MERGE_IPT>(h, x, y, allow_df, s);
@@ -888,6 +999,11 @@ spmv_status dispatch(Algo a, const spmv_matrix *h, const void *x, void *y, spmv_
         if (dt == SPMV_PATTERN) return run_algo<Pattern, double, double>(a, h, x, y, allow_df, s);
         if (dt == SPMV_F32) return run_algo<float, double, double>(a, h, x, y, allow_df, s);
         goto unsupported;
+    }
+    if (vdt == SPMV_F32 && acc == SPMV_ACC_COMPENSATED && a == MERGE) {
+        if (dt == SPMV_F32) return launch_merge_comp<float>(h, x, y, s);
+        if (dt == SPMV_BF16) return launch_merge_comp<__nv_bfloat16>(h, x, y, s);
+        if (dt == SPMV_PATTERN) return launch_merge_comp<Pattern>(h, x, y, s);
     }
     if (vdt == SPMV_F32) {
         if (acc == SPMV_ACC_F32) {
@@ -998,6 +1114,25 @@ spmv_status mul_hb(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt,
 spmv_status mul_csr_merge_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col,
                                   const double *data, const double *x, double *y, cudaStream_t s) {
     return noalloc_merge(m, n, nnz, row_ptr, col, data, x, y, s);
+}
+
+spmv_status mul_merge_pattern_split(const spmv_matrix *h, const double *x, const float2 *x2, const uint32_t *xflag,
+                                    double *y, cudaStream_t s) {
+    constexpr size_t smem = (size_t)MW_WARPS * 2 * WarpSlot<Pattern>::BYTES;
+    static bool attr = false;
+    if (!attr) {
+        SPMV_CUDA_TRY(cudaFuncSetAttribute(k_merge_warp_pat_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    const unsigned grid = persistent_grid((const void *)k_merge_warp_pat_df, MW_WARPS * 32, smem, h->tiles);
+    SPMV_LAUNCH("k_merge_spmv", s, (k_merge_warp_pat_df<<<grid, MW_WARPS * 32, smem, s>>>(
+                                       h->merge_desc, h->col, x, x2, xflag, y, h->part_row, h->part_nz, h->carry_row,
+                                       h->carry_val, h->tiles, h->status_dev + 3)));
+    SPMV_LAUNCH_CHECK("pattern merge spmv");
+    SPMV_LAUNCH("k_merge_fixup", s, (k_merge_fixup_tiles<double><<<cdivu(h->tiles, 256), 256, 0, s>>>(
+                                        h->tiles, h->m, h->carry_row, h->carry_val, h->merge_desc, y)));
+    SPMV_LAUNCH_CHECK("merge fixup");
+    return SPMV_OK;
 }
 
 }  // namespace spmv

@@ -159,3 +159,32 @@ def random_coo(m: int, n: int, nnz: int, seed: int = 0, dup_frac: float = 0.0):
         perm = rng.permutation(r.size)
         r, c = r[perm], c[perm]
     return r.astype(np.int32), c.astype(np.int32)
+
+
+def round_bf16_bits(values: np.ndarray) -> np.ndarray:
+    """Input preparation for bfloat16 matrices: each double rounded to the nearest bfloat16
+    (ties to even) directly from its 52-bit mantissa, returned as uint16 bit patterns.
+    Normal-range values only (zero allowed)."""
+    v = np.ascontiguousarray(values, dtype=np.float64)
+    b = v.view(np.uint64)
+    sign = (b >> np.uint64(63)).astype(np.uint64)
+    exp = ((b >> np.uint64(52)) & np.uint64(0x7FF)).astype(np.int64)
+    mant = b & np.uint64((1 << 52) - 1)
+    q = mant >> np.uint64(45)
+    rem = mant & np.uint64((1 << 45) - 1)
+    half = np.uint64(1 << 44)
+    up = (rem > half) | ((rem == half) & ((q & np.uint64(1)) == np.uint64(1)))
+    q = q + up.astype(np.uint64)
+    carry = q >> np.uint64(7)
+    q = q & np.uint64(0x7F)
+    bexp = exp - 1023 + 127 + carry.astype(np.int64)
+    zero = (b & np.uint64((1 << 63) - 1)) == 0
+    if np.any(~zero & ((bexp < 1) | (bexp > 254))):
+        raise ValueError("round_bf16_bits: value outside the normal bfloat16 range")
+    out = (sign << np.uint64(15)) | (np.clip(bexp, 0, 255).astype(np.uint64) << np.uint64(7)) | q
+    out = np.where(zero, sign << np.uint64(15), out)
+    return out.astype(np.uint16)
+
+
+def bf16_bits_to_float64(bits: np.ndarray) -> np.ndarray:
+    return (np.asarray(bits, np.uint16).astype(np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)
