@@ -140,13 +140,25 @@ spmv_status spmv_convert(spmv_handle h, spmv_format f, const spmv_convert_opts *
 spmv_status spmv_mul(spmv_handle h, const void *x, void *y, spmv_dtype vec_dt, uint32_t accum, void *stream);
 
 /*
- * spmv_mul_batch -- Y_i := A_i X_i for `count` handles and k right-hand sides each.
- *   hs          count converted handles (formats may differ).
+ * spmv_mul_batch -- Y_i := A_i X_i for `count` handles and k right-hand sides each
+ * (the multiple-vector product of Section 3; the batch over many matrices has no
+ * counterpart in the paper).
+ *   hs          count converted handles of one matrix dtype (any format: the merge-path
+ *               tiles of Section 3.3 are built on first use for handles that lack them).
  *   k           right-hand sides per product, 1 <= k <= 16.
  *   X, Y        count device pointers; X[i] is n_i x k row-major (the k values of
- *               x_j contiguous), Y[i] is m_i x k row-major.
- * All products run in one persistent launch over a work table built per batch shape;
- * the launch is captured once into a CUDA graph and replayed for the same shape.
+ *               x_j contiguous), Y[i] is m_i x k row-major (overwritten).
+ *   vec_dt, accum  as spmv_mul's merge path: F64 vectors accumulate in native FP64;
+ *               F32 vectors in FP32, compensated FP32, or (F32/BF16 matrices) FP64.
+ * Every product runs in one persistent launch over the concatenated tiles of all
+ * matrices, followed by one carry fix-up launch.  Both are captured into a CUDA graph
+ * the first time a batch shape (the handles, k, dtypes, accumulation and 16-byte
+ * alignment of X/Y) is seen, and replayed after that; only the table of X/Y pointers is
+ * copied per call.  Per column, the result is bitwise the one spmv_mul gives for the
+ * same accumulation on the merge path.  Calls with the same batch shape share scratch
+ * and must be ordered.  Not capturable into a caller's graph (the pointer table is
+ * uploaded from pageable memory).  A handle's plans are dropped when it is converted
+ * again or destroyed.
  */
 spmv_status spmv_mul_batch(int count, const spmv_handle *hs, int k, const void *const *X, void *const *Y,
                            spmv_dtype vec_dt, uint32_t accum, void *stream);

@@ -91,6 +91,8 @@ def load(path: str | None = None):
 
 
 def _p(a):
+    # the caller keeps `a` referenced until the C call returns (bind converted arrays to a
+    # name first: a temporary passed through here would be freed before the call)
     return None if a is None else a.ctypes.data
 
 
@@ -125,35 +127,38 @@ def csr_spmv(row_ptr, col, val, x, lib=None):
     """Algorithm 1."""
     lib = lib or load()
     m = row_ptr.shape[0] - 1
+    row_ptr, col, val, x = _i32(row_ptr), _i32(col), _f64(val), _f64(x)
     y = np.empty(m, np.float64)
-    lib.oracle_csr_spmv(m, _p(_i32(row_ptr)), _p(_i32(col)), _p(_f64(val)), _p(_f64(x)), _p(y))
+    lib.oracle_csr_spmv(m, _p(row_ptr), _p(col), _p(val), _p(x), _p(y))
     return y
 
 
 def csr_spmm(row_ptr, col, val, X, lib=None):
     lib = lib or load()
     m = row_ptr.shape[0] - 1
+    row_ptr, col, val = _i32(row_ptr), _i32(col), _f64(val)
     X = np.ascontiguousarray(X, np.float64)
     k = X.shape[1]
     Y = np.empty((m, k), np.float64)
-    lib.oracle_csr_spmm(m, k, _p(_i32(row_ptr)), _p(_i32(col)), _p(_f64(val)), _p(X), _p(Y))
+    lib.oracle_csr_spmm(m, k, _p(row_ptr), _p(col), _p(val), _p(X), _p(Y))
     return Y
 
 
 def coo_spmv(m, rows, cols, vals, x, lib=None):
     """Eq. 1 (triplet SpMV)."""
     lib = lib or load()
-    rows, cols = _i32(rows), _i32(cols)
+    rows, cols, vals, x = _i32(rows), _i32(cols), _f64(vals), _f64(x)
     y = np.empty(m, np.float64)
-    lib.oracle_coo_spmv(m, rows.shape[0], _p(rows), _p(cols), _p(_f64(vals)), _p(_f64(x)), _p(y))
+    lib.oracle_coo_spmv(m, rows.shape[0], _p(rows), _p(cols), _p(vals), _p(x), _p(y))
     return y
 
 
 def csr_spmv_neumaier(row_ptr, col, val, x, lib=None):
     lib = lib or load()
     m = row_ptr.shape[0] - 1
+    row_ptr, col, val, x = _i32(row_ptr), _i32(col), _f64(val), _f64(x)
     y = np.empty(m, np.float64)
-    lib.oracle_csr_spmv_neumaier(m, _p(_i32(row_ptr)), _p(_i32(col)), _p(_f64(val)), _p(_f64(x)), _p(y))
+    lib.oracle_csr_spmv_neumaier(m, _p(row_ptr), _p(col), _p(val), _p(x), _p(y))
     return y
 
 
@@ -161,18 +166,20 @@ def csr_absmul(row_ptr, col, val, x, lib=None):
     """(|A| |x|)_i, the scale in the tolerance |y - y_ref| <= tol * (|A||x|)_i."""
     lib = lib or load()
     m = row_ptr.shape[0] - 1
+    row_ptr, col, val, x = _i32(row_ptr), _i32(col), _f64(val), _f64(x)
     y = np.empty(m, np.float64)
-    lib.oracle_csr_absmul(m, _p(_i32(row_ptr)), _p(_i32(col)), _p(_f64(val)), _p(_f64(x)), _p(y))
+    lib.oracle_csr_absmul(m, _p(row_ptr), _p(col), _p(val), _p(x), _p(y))
     return y
 
 
 def csr_transpose(m, n, row_ptr, col, val, lib=None):
     lib = lib or load()
+    row_ptr, col, val = _i32(row_ptr), _i32(col), _f64(val)
     nnz = int(row_ptr[m])
     trp = np.empty(n + 1, np.int32)
     tc = np.empty(max(nnz, 1), np.int32)
     tv = np.empty(max(nnz, 1), np.float64) if val is not None else None
-    st = lib.oracle_csr_transpose(m, n, _p(_i32(row_ptr)), _p(_i32(col)), _p(_f64(val)), _p(trp), _p(tc), _p(tv))
+    st = lib.oracle_csr_transpose(m, n, _p(row_ptr), _p(col), _p(val), _p(trp), _p(tc), _p(tv))
     if st != OK:
         raise OracleError(st, "csr_transpose")
     return trp, tc[:nnz].copy(), (tv[:nnz].copy() if tv is not None else None)
@@ -228,9 +235,11 @@ def csr_to_hb(m, n, row_ptr, col, val, log2beta, inner_order=0, lib=None):
 
 def hb_spmv(m, hb, x, lib=None):
     lib = lib or load()
+    bp, br, bc = _i32(hb["blk_ptr"]), _i32(hb["blk_row"]), _i32(hb["blk_col"])
+    idx = np.ascontiguousarray(hb["idx"], np.uint32)
+    val, x = _f64(hb["val"]), _f64(x)
     y = np.empty(m, np.float64)
-    lib.oracle_hb_spmv(m, hb["nblk"], hb["log2beta"], _p(hb["blk_ptr"]), _p(hb["blk_row"]), _p(hb["blk_col"]),
-                       _p(hb["idx"]), _p(_f64(hb["val"])), _p(_f64(x)), _p(y))
+    lib.oracle_hb_spmv(m, hb["nblk"], hb["log2beta"], _p(bp), _p(br), _p(bc), _p(idx), _p(val), _p(x), _p(y))
     return y
 
 
@@ -260,8 +269,8 @@ def merge_spmv(row_ptr, col, val, x, parts, lib=None):
     y = np.empty(m, np.float64)
     cr = np.empty(max(parts, 1), np.int64)
     cv = np.empty(max(parts, 1), np.float64)
-    lib.oracle_merge_spmv(m, _p(_i32(row_ptr)), _p(_i32(col)), _p(_f64(val)), _p(_f64(x)), _p(y), parts,
-                          _p(cr), _p(cv))
+    row_ptr, col, val, x = _i32(row_ptr), _i32(col), _f64(val), _f64(x)
+    lib.oracle_merge_spmv(m, _p(row_ptr), _p(col), _p(val), _p(x), _p(y), parts, _p(cr), _p(cv))
     return y, cr, cv
 
 
@@ -288,8 +297,9 @@ def round_array_bf16(a, lib=None):
 def pagerank(row_ptr, col, damping=0.85, iters=20, lib=None):
     lib = lib or load()
     n = row_ptr.shape[0] - 1
+    row_ptr, col = _i32(row_ptr), _i32(col)
     x = np.empty(n, np.float64)
-    st = lib.oracle_pagerank(n, _p(_i32(row_ptr)), _p(_i32(col)), damping, iters, _p(x))
+    st = lib.oracle_pagerank(n, _p(row_ptr), _p(col), damping, iters, _p(x))
     if st != OK:
         raise OracleError(st, "pagerank")
     return x

@@ -307,6 +307,7 @@ spmv_status spmv_create_coo(int64_t m, int64_t n, int64_t nnz, const int32_t *ro
 spmv_status spmv_convert(spmv_handle h, spmv_format f, const spmv_convert_opts *opt, void *stream) {
     g_err.clear();
     SPMV_TRY(check_handle(h));
+    forget_batch_plans(h);
     cudaStream_t s = (cudaStream_t)stream;
     spmv_convert_opts o = {0, SPMV_INNER_HILBERT, 0};
     if (opt) o = *opt;
@@ -379,17 +380,31 @@ spmv_status spmv_mul_batch(int count, const spmv_handle *hs, int k, const void *
         set_error("spmv_mul_batch: bad arguments");
         return SPMV_ERR_INVALID_ARG;
     }
-    if (k != 1) {
-        set_error("spmv_mul_batch: k > 1 is not built in yet");
-        return SPMV_ERR_UNSUPPORTED;
+    if (vec_dt != SPMV_F64 && vec_dt != SPMV_F32) {
+        set_error("spmv_mul_batch: vectors are SPMV_F64 or SPMV_F32");
+        return SPMV_ERR_INVALID_ARG;
     }
-    for (int i = 0; i < count; ++i) SPMV_TRY(spmv_mul(hs[i], X[i], Y[i], vec_dt, accum, stream));
-    return SPMV_OK;
+    for (int i = 0; i < count; ++i) {
+        SPMV_TRY(check_handle(hs[i]));
+        if (!X[i] || !Y[i]) {
+            set_error("spmv_mul_batch: null vector pointer");
+            return SPMV_ERR_INVALID_ARG;
+        }
+        if (!hs[i]->has_csr) {
+            set_error("spmv_mul_batch: handle not converted (call spmv_convert first)");
+            return SPMV_ERR_NOT_CONVERTED;
+        }
+        // the batch runs on the merge-path tiles; build them for handles converted to
+        // another format
+        if (!hs[i]->has_merge) SPMV_TRY(build_merge(hs[i], MERGE_WARP_ITEMS, (cudaStream_t)stream));
+    }
+    return mul_batch(count, (spmv_matrix *const *)hs, k, X, Y, vec_dt, accum, (cudaStream_t)stream);
 }
 
 spmv_status spmv_destroy(spmv_handle h) {
     if (!h) return SPMV_OK;
     cudaError_t e = cudaDeviceSynchronize();
+    forget_batch_plans(h);
     free_all(h);
     delete h;
     if (e != cudaSuccess) return cuda_status(e, "spmv_destroy");

@@ -55,5 +55,10 @@ spmv_status mul_merge_pattern_split(const spmv_matrix *h, const double *x, const
 spmv_status pagerank(spmv_matrix *h, double damping, int iters, double *x, cudaStream_t s);
 spmv_status mul_csr_merge_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col,
                                   const double *data, const double *x, double *y, cudaStream_t s);
+// Batched multi-RHS merge-path products (batch.cu); plans that name a handle are dropped
+// when it is converted again or destroyed.
+spmv_status mul_batch(int count, spmv_matrix *const *hs, int k, const void *const *X, void *const *Y,
+                      spmv_dtype vdt, uint32_t acc, cudaStream_t s);
+void forget_batch_plans(const spmv_matrix *h);
 
 }  // namespace spmv

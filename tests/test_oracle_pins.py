@@ -519,3 +519,23 @@ def test_planted_wrong_tie_rule_fails_merge_figure(orc):
             j += 1
         walk.append((i, j))
     assert walk != nodes
+
+
+def test_csr_spmm_matches_dense_brute_force():
+    """Multiple right-hand sides (Section 3): Y = A X against a dense product written out
+    element by element, with integer data so that every sum is exact."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    m, n, k = 23, 17, 5
+    dense = np.where(rng.random((m, n)) < 0.3, rng.integers(-8, 9, (m, n)), 0).astype(np.float64)
+    dense[4] = 0.0                                    # an empty row
+    r, c = np.nonzero(dense)
+    rp, co, vo = oracle.coo_to_csr(m, n, r.astype(np.int32), c.astype(np.int32), dense[r, c])
+    X = rng.integers(-8, 9, (n, k)).astype(np.float64)
+    Y = oracle.csr_spmm(rp, co, vo, X)
+    want = np.zeros((m, k))
+    for i in range(m):
+        for j in range(n):
+            for q in range(k):
+                want[i, q] += dense[i, j] * X[j, q]
+    assert Y.shape == (m, k)
+    assert np.array_equal(Y, want)
