@@ -70,28 +70,43 @@ def sort_passes(bits):
 
 
 def kernel_bytes(name, m, n, nnz, nblk):
-    """Algorithmic bytes per step that each traced kernel moves (for the roofline of the
-    dominant kernel): radix passes read and write (key, payload) = 12 B per item each way."""
+    """Algorithmic bytes that each traced kernel moves in one step (FP64 values, int32
+    indices), or None for kernels without a stated figure.  A radix pass reads and writes
+    one (64-bit key, 32-bit payload) pair per item: 24 B in the scatter, 8 B (keys) in the
+    count.  Sorted items per step: nnz per pass of the COO->CSR sort (row and column bits),
+    nnz per pass of the Hilbert-key sort (2K bits), m in the one pass of the row-class sort."""
     K = max(1, (max(m, n, 2) - 1).bit_length())
     cbits = max(1, (n - 1).bit_length()) if n > 1 else 1
     rbits = max(1, (m - 1).bit_length()) if m > 1 else 1
-    p_csr, p_hb, p_bins = sort_passes(cbits + rbits), sort_passes(2 * K), 1
-    sort_items = (p_csr + p_hb) * nnz + p_bins * m
+    sort_items = (sort_passes(cbits + rbits) + sort_passes(2 * K)) * nnz + m
     spmv_csr = nnz * 12 + (m + 1) * 4 + n * 8 + m * 8
     table = {
-        "k_rs_downsweep": (24 * sort_items, p_csr + p_hb + p_bins),
-        "k_rs_upsweep": (8 * sort_items, p_csr + p_hb + p_bins),
-        "k_merge_spmv": (spmv_csr, 1),
-        "k_rowsplit": (spmv_csr, 1),
-        "k_hb_spmv": (nnz * 12 + nblk * 12 + n * 8 + m * 8, 1),
+        "k_rs_scatter": 24 * sort_items,
+        "k_rs_count": 8 * sort_items,
+        "k_gather": 2 * 20 * nnz,                  # perm 4 B + value 8 B read, value 8 B written; twice
+        "k_coo_keys": 20 * nnz,                    # row + col read, key + perm written
+        "k_hb_keys": 16 * nnz + (m + 1) * 4,       # col read (+ row_ptr), key + perm written
+        "k_hb_fill": 16 * nnz,                     # key read, packed index + block head written
+        "k_merge_spmv": spmv_csr,
+        "k_rowsplit": spmv_csr,
+        "k_hb_spmv": nnz * 12 + nblk * 12 + n * 8 + m * 8,
     }
     return table.get(name)
+
+
+def kernel_units(name, m, n, nnz):
+    """Units per step by which a kernel's captured DRAM traffic is scaled to this workload."""
+    K = max(1, (max(m, n, 2) - 1).bit_length())
+    cbits = max(1, (n - 1).bit_length()) if n > 1 else 1
+    rbits = max(1, (m - 1).bit_length()) if m > 1 else 1
+    return {"k_rs_scatter": (sort_passes(cbits + rbits) + sort_passes(2 * K)) * nnz + m,
+            "k_merge_spmv": nnz}.get(name)
 
 
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -105,7 +120,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             threading.Thread(target=self._read, daemon=True).start()
         except (OSError, ValueError):
@@ -184,7 +199,7 @@ def cpu_baseline(scale, rows, cols, vals, x, frac, reps=1):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=RMAT["scale"])
@@ -319,6 +334,14 @@ def main():
             d["gflops"] = round(flops[nm] / (t_ms * 1e-3) / 1e9, 1)
         rows_out[nm] = d
 
+    # ---- break-even count of the blocked format against the faster CRS product
+    from paper_2502_19284_gb300 import breakeven
+    t_csr_best = min(rows_out["spmv_rowsplit"]["ms"], rows_out["spmv_merge"]["ms"])
+    ns = breakeven.n_star_times(rows_out["csr_to_hb"]["ms"], 0.0, t_csr_best, rows_out["spmv_hb"]["ms"])
+    break_even = {"n_star_gpu": None if ns is None else round(ns, 1),
+                  "meaning": "SpMVs after which CSR->HB conversion pays back against the faster CRS product "
+                             "(None: the blocked product is not faster)"}
+
     # ---- roofline of the dominant kernel (device time from the trace)
     peaks = {}
     try:
@@ -337,23 +360,22 @@ def main():
     def roofline_for(kname):
         cnt, kms = trace[kname]
         kb = kernel_bytes(kname, m, n, nnz, nblk)
-        if kb is None:
+        if kb is None or cnt == 0:
             return None
-        bytes_per_step, launches_per_step = kb
-        per_launch = bytes_per_step / launches_per_step
-        dur = kms / cnt
+        per_launch = kb * args.steps / cnt          # algorithmic bytes of an average launch
+        dur = kms / cnt                             # its average duration (CUDA events, ms)
         ach = per_launch / (dur * 1e-3) / 1e9
         traffic = None
         t = traffic_db.get(kname)
-        if t and t.get("source_sha") == source_sha(t.get("source")) and t.get("scale") == scale:
-            traffic = t.get("bytes_per_launch")
+        units = kernel_units(kname, m, n, nnz)
+        if t and units and t.get("source_sha") == source_sha(t.get("source")):
+            traffic = int(t["bytes_per_unit"] * units * args.steps / cnt)   # ncu DRAM bytes, scaled per launch
         return {"kernel": kname, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "peak_note": peak_src, "traffic": traffic,
                 "algorithmic_bytes_per_launch": int(per_launch), "launches": cnt, "avg_launch_ms": round(dur, 5)}
 
-    known = [k for k in trace if kernel_bytes(k, m, n, nnz, nblk)]
     dominant = max(trace, key=lambda k: trace[k][1])
-    roof = roofline_for(dominant) if dominant in known else None
+    roof = roofline_for(dominant)
     roof_spmv = roofline_for("k_merge_spmv") if "k_merge_spmv" in trace else None
     launches = sum(c for c, _ in trace.values())
     shares = {k: round(v[1] / sum(u[1] for u in trace.values()), 4) for k, v in
@@ -411,6 +433,7 @@ def main():
         "roofline": roof,
         "roofline_spmv_merge": roof_spmv,
         "kernel_shares": shares,
+        "break_even": break_even,
         "cpu_baseline": cpu,
         "wall_s_timed": round(wall_s, 3),
     }

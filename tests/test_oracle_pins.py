@@ -539,3 +539,4 @@ def test_csr_spmm_matches_dense_brute_force():
                 want[i, q] += dense[i, j] * X[j, q]
     assert Y.shape == (m, k)
     assert np.array_equal(Y, want)
+
