@@ -42,6 +42,25 @@ static void configure_pool() {
     }
 }
 
+spmv_status set_smem_ctas(const void *kernel, size_t bytes, int ctas) {
+    int dev = 0, per_sm = 0, reserved = 0;
+    SPMV_CUDA_TRY(cudaGetDevice(&dev));
+    SPMV_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    SPMV_CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    const size_t need = (size_t)ctas * (bytes + (size_t)reserved);
+    const int pct = per_sm > 0 ? (int)std::min<size_t>(100, (need * 100 + per_sm - 1) / per_sm) : 100;
+    SPMV_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    SPMV_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    return SPMV_OK;
+}
+
+spmv_status set_smem(const void *kernel, size_t bytes) {
+    SPMV_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    SPMV_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared));
+    return SPMV_OK;
+}
+
 spmv_status dev_alloc(void **p, size_t bytes, const char *what, cudaStream_t s) {
     *p = nullptr;
     long long left = g_fail_after.load();
@@ -156,7 +175,7 @@ bool is_device_ptr(const void *p) {
 void free_all(spmv_matrix *h) {
     void *ptrs[] = {h->coo_row, h->coo_col, h->coo_val, h->row_ptr, h->col, h->val, h->bin_rows,
                     h->part_row, h->part_nz, h->carry_row, h->carry_val, h->merge_desc, h->hb_idx, h->hb_val,
-                    h->blk_ptr, h->blk_row, h->blk_col, h->val2, h->xsplit, h->xsplit_flag,
+                    h->blk_ptr, h->blk_row, h->blk_col, h->xsplit, h->xsplit_flag, h->slot_desc, h->slot_col, h->slot_val2,
                     h->pr_inv, h->pr_z, h->pr_z2, h->pr_y, h->pr_part, h->status_dev};
     if (h->pr_graph) cudaGraphExecDestroy((cudaGraphExec_t)h->pr_graph);
     for (void *p : ptrs) dev_free(p);

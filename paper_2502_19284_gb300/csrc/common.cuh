@@ -55,6 +55,13 @@ struct TraceScope {
 // allocation fail for tests.  dev_free releases synchronously (safe after any work);
 // dev_free_async releases in the order of stream s.
 spmv_status dev_alloc(void **p, size_t bytes, const char *what, cudaStream_t s);
+// Dynamic shared memory limit of a kernel, with the carveout at its maximum so that the
+// residency the occupancy calculator reports is the one the launch gets (a persistent grid
+// sized for more CTAs than fit would run a second, late wave).
+spmv_status set_smem(const void *kernel, size_t bytes);
+// The same with the smallest carveout that holds `ctas` CTAs per SM: the rest of the SM's
+// on-chip memory stays L1 cache (which the x gathers of the products hit).
+spmv_status set_smem_ctas(const void *kernel, size_t bytes, int ctas);
 void dev_free(void *p);
 void dev_free_async(void *p, cudaStream_t s);
 
@@ -145,6 +152,12 @@ struct spmv_matrix {
     double *carry_val = nullptr;      // tiles carries, then tiles head partials (a tile's first
                                       // row when it began in an earlier tile)
     uint32_t *merge_desc = nullptr;   // per-lane descriptors of the warp tiles (32 words per tile)
+    // lane-slotted copy of the warp tiles: path item k of lane l of tile t sits in slot
+    // t * 224 + k * 32 + l (a row end or a tail slot holds column 0 and value 0), so a lane
+    // finds its operands at fixed offsets; 40 words of header and lane descriptors per tile
+    uint32_t *slot_desc = nullptr;
+    int32_t *slot_col = nullptr;
+    float2 *slot_val2 = nullptr;      // FP64 values split into float pairs (when df_ok)
 
     // Hilbert-ordered blocked format
     bool has_hb = false;
@@ -157,7 +170,6 @@ struct spmv_matrix {
     // FP64 through double-float arithmetic (df64.cuh): set when every stored value lies in
     // the double-float window; x is split into float pairs per product (scratch below)
     bool df_checked = false, df_ok = false;
-    float2 *val2 = nullptr;           // CRS values split into float pairs (when df_ok)
     float2 *xsplit = nullptr;
     uint32_t *xsplit_flag = nullptr;
 

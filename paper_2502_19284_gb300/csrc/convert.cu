@@ -234,6 +234,67 @@ __global__ void k_merge_desc(const int32_t *__restrict__ row_ptr, const int32_t 
         (uint32_t)before | ((uint32_t)(d0 - before) << 8) | (bits << 16) | ((uint32_t)(d1 - d0) << 24) | cont;
 }
 
+// Lane-slotted layout of the warp tiles: one warp per tile writes the tile's header and
+// lane descriptors (same fields as k_merge_desc) and, for every slot k * 32 + lane, the CRS
+// index of the nonzero at path item k of the lane, or -1 for a row end or a tail slot.
+__global__ void k_merge_slots(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ part_row,
+                              const int32_t *__restrict__ part_nz, int64_t tiles, uint32_t *__restrict__ sdesc,
+                              int32_t *__restrict__ src) {
+    __shared__ uint32_t s_bits[8][8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t t = (int64_t)blockIdx.x * 8 + w;
+    if (t >= tiles) return;
+    const int64_t i0 = part_row[t], j0 = part_nz[t];
+    const int nrows = (int)(part_row[t + 1] - i0), nnzt = (int)(part_nz[t + 1] - j0);
+    if (lane < 8) s_bits[w][lane] = 0u;
+    __syncwarp();
+    for (int r = lane; r < nrows; r += 32) {
+        const int pos = r + (int)(row_ptr[i0 + r + 1] - j0);
+        atomicOr(&s_bits[w][pos >> 5], 1u << (pos & 31));
+    }
+    __syncwarp();
+    const int total = nrows + nnzt;
+    const int d0 = min(lane * MERGE_WARP_IPT, total), d1 = min(d0 + MERGE_WARP_IPT, total);
+    const int w0 = d0 >> 5, b0 = d0 & 31;
+    int before = 0;
+    for (int q = 0; q < w0; ++q) before += __popc(s_bits[w][q]);
+    const uint32_t lo = s_bits[w][w0], hi = s_bits[w][w0 + 1];
+    before += __popc(lo & ((1u << b0) - 1u));
+    const uint32_t span = b0 ? (lo >> b0) | (hi << (32 - b0)) : lo;
+    const uint32_t bits = span & ((1u << (d1 - d0)) - 1u);
+    uint32_t *hd = sdesc + t * SLOT_DESC_WORDS;
+    hd[4 + lane] = (uint32_t)before | (bits << 16) | ((uint32_t)(d1 - d0) << 24);
+    if (lane < 4) {
+        const uint32_t cont = (nrows > 0 && row_ptr[i0] < j0) ? 1u : 0u;
+        hd[lane] = lane == 0 ? (uint32_t)i0 : lane == 1 ? (uint32_t)nrows : lane == 2 ? cont : 0u;
+        hd[36 + lane] = 0u;
+    }
+    // nonzero index of path item d0 + k: j0 + (d0 + k) - (row ends before it)
+    int ends = before;
+    int32_t *out = src + t * MERGE_WARP_ITEMS + lane;
+#pragma unroll
+    for (int k = 0; k < MERGE_WARP_IPT; ++k) {
+        const bool in = k < d1 - d0;
+        const bool end = in && ((bits >> k) & 1u);
+        out[k * 32] = (in && !end) ? (int32_t)(j0 + d0 + k - ends) : -1;
+        ends += end ? 1 : 0;
+    }
+}
+
+// slot arrays from the CRS arrays through the slot -> CRS index map
+__global__ void k_slot_fill(const int32_t *__restrict__ src, int64_t n, const int32_t *__restrict__ col,
+                            const double *__restrict__ val, int32_t *__restrict__ scol, float2 *__restrict__ sval2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t j = src[i];
+    scol[i] = j >= 0 ? col[j] : 0;
+    if (sval2) {
+        float2 r = make_float2(0.f, 0.f);
+        if (j >= 0) df_split(val[j], &r.x, &r.y);
+        sval2[i] = r;
+    }
+}
+
 __global__ void k_merge_partition(const int32_t *__restrict__ row_ptr, int64_t m, int64_t nnz, int64_t tiles,
                                   int64_t tile_items, int32_t *__restrict__ part_row, int32_t *__restrict__ part_nz) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -375,15 +436,6 @@ __global__ void k_df_window(const double *__restrict__ v, int64_t n, uint32_t *_
         bad |= !df_split(v[i], &h, &l);
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
-}
-
-__global__ void k_df_split_vals(const double *__restrict__ v, int64_t n, float2 *__restrict__ out) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        float2 r;
-        df_split(v[i], &r.x, &r.y);
-        out[i] = r;
-    }
 }
 
 // ---------------------------------------------------------------- helpers
@@ -536,15 +588,6 @@ spmv_status build_df(spmv_matrix *h, cudaStream_t s) {
     SPMV_CUDA_TRY(cudaMemcpyAsync(h->status_host + 2, h->status_dev + 2, 4, cudaMemcpyDeviceToHost, s));
     SPMV_CUDA_TRY(cudaStreamSynchronize(s));
     h->df_ok = h->status_host[2] == 0;
-    if (h->df_ok && h->nnz > 0) {
-        DevBuf v2(s);
-        SPMV_TRY(v2.alloc((size_t)h->nnz * sizeof(float2) + TMA_PAD, "split values"));
-        SPMV_LAUNCH("k_df_split_vals", s, (k_df_split_vals<<<grid_for(h->nnz), CB, 0, s>>>((const double *)h->val, h->nnz,
-                                                                                           v2.as<float2>())));
-        SPMV_LAUNCH_CHECK("split values");
-        h->val2 = (float2 *)v2.release();
-        h->bytes += h->nnz * 8;
-    }
     h->xsplit = (float2 *)xs.release();
     h->xsplit_flag = (uint32_t *)fl.release();
     h->bytes += std::max<int64_t>(h->n, 1) * 8 + 16;
@@ -587,6 +630,34 @@ spmv_status build_bins(spmv_matrix *h, cudaStream_t s) {
     return SPMV_OK;
 }
 
+// Lane-slotted copy of the merge tiles (column indices, and for FP64 matrices inside the
+// double-float window the split values).
+spmv_status build_slots(spmv_matrix *h, cudaStream_t s) {
+    const int64_t tiles = h->tiles, slots = tiles * MERGE_WARP_ITEMS;
+    if (h->dt == SPMV_F64) SPMV_TRY(build_df(h, s));
+    const bool vals = h->dt == SPMV_F64 && h->df_ok;
+    DevBuf sd(s), sc(s), sv(s), src(s);
+    SPMV_TRY(sd.alloc((size_t)tiles * SLOT_DESC_WORDS * 4, "slot descriptors"));
+    SPMV_TRY(sc.alloc((size_t)slots * 4, "slot columns"));
+    if (vals) SPMV_TRY(sv.alloc((size_t)slots * sizeof(float2), "slot values"));
+    SPMV_TRY(src.alloc((size_t)slots * 4, "slot map"));
+    SPMV_LAUNCH("k_merge_slots", s, (k_merge_slots<<<(unsigned)((tiles + 7) / 8), 256, 0, s>>>(
+                                        h->row_ptr, h->part_row, h->part_nz, tiles, sd.as<uint32_t>(), src.as<int32_t>())));
+    SPMV_LAUNCH_CHECK("merge slots");
+    SPMV_LAUNCH("k_slot_fill", s, (k_slot_fill<<<grid_for(slots), CB, 0, s>>>(src.as<int32_t>(), slots, h->col,
+                                      (const double *)h->val, sc.as<int32_t>(), vals ? sv.as<float2>() : nullptr)));
+    SPMV_LAUNCH_CHECK("slot fill");
+    if (h->slot_desc) {
+        dev_free_async(h->slot_desc, s); dev_free_async(h->slot_col, s);
+        if (h->slot_val2) dev_free_async(h->slot_val2, s);
+    }
+    h->slot_desc = (uint32_t *)sd.release();
+    h->slot_col = (int32_t *)sc.release();
+    h->slot_val2 = vals ? (float2 *)sv.release() : nullptr;
+    h->bytes += tiles * SLOT_DESC_WORDS * 4 + slots * (vals ? 12 : 4);
+    return SPMV_OK;
+}
+
 spmv_status build_merge(spmv_matrix *h, int tile_items, cudaStream_t s) {
     const int64_t total = h->m + h->nnz;
     const int64_t tiles = std::max<int64_t>(1, (total + tile_items - 1) / tile_items);
@@ -616,6 +687,7 @@ spmv_status build_merge(spmv_matrix *h, int tile_items, cudaStream_t s) {
     h->tile_items = tile_items;
     h->has_merge = true;
     h->bytes += (tiles + 1) * 8 + tiles * 20 + tiles * 128;
+    if (tile_items == MERGE_WARP_ITEMS) SPMV_TRY(build_slots(h, s));
     return SPMV_OK;
 }
 

@@ -18,6 +18,9 @@ constexpr int MERGE_TILE_ITEMS = MERGE_BLOCK * MERGE_IPT;   // CTA tile (allocat
 // The library's merge product cuts the path into warp tiles of MERGE_WARP_ITEMS items.
 constexpr int MERGE_WARP_IPT = 7;
 constexpr int MERGE_WARP_ITEMS = 32 * MERGE_WARP_IPT;
+// Lane-slotted tile header: words 0..3 = first row, row count, continuation flag, 0;
+// words 4..35 = the 32 lane descriptors; words 36..39 = 0 (a tile's block is 160 bytes).
+constexpr int SLOT_DESC_WORDS = 40;
 
 __host__ __device__ __forceinline__ int class_lanes(int c) {
     return c == 0 ? 1 : c == 1 ? 2 : c == 2 ? 4 : c == 3 ? 8 : c == 4 ? 16 : 32;

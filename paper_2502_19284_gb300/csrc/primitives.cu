@@ -285,7 +285,7 @@ spmv_status radix_sort_pairs(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals,
     if (n <= 1 || end_bit <= begin_bit) return SPMV_OK;
     static bool attr_set = false;
     if (!attr_set) {
-        SPMV_CUDA_TRY(cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_SMEM));
+        SPMV_TRY(set_smem((const void *)k_rs_scatter, RS_SMEM));
         attr_set = true;
     }
     const int64_t ntiles = cdiv(n, RS_TILE);

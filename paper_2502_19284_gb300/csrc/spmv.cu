@@ -325,10 +325,6 @@ struct NativeSLoad {
     __device__ __forceinline__ static AT val(const VT *v, int k) { return sval<VT, AT>(v, k); }
     template <typename XT> __device__ __forceinline__ static AT xs(const XT *xb, int k) { return AT(xb[k]); }
 };
-struct DfSLoad {   // values arrive pre-split into float pairs
-    __device__ __forceinline__ static float2 val(const float2 *v, int k) { return v[k]; }
-    __device__ __forceinline__ static float2 xs(const float2 *xb, int k) { return xb[k]; }
-};
 
 // Shared-memory slot of one warp tile: mbarrier, lane descriptors, column indices, values,
 // and the gathered x of the tile's nonzeros (reused for the finished rows once the lanes
@@ -601,32 +597,220 @@ __global__ __launch_bounds__(MW_WARPS * 32) void k_merge_warp_comp(const uint32_
                                                                      smem_raw + (threadIdx.x >> 5) * 2 * WarpSlot<VT>::BYTES);
 }
 
-// FP64 through double-float: val2 holds the stored values split into float pairs at the
-// conversion, x2 holds x split per product; *xflag non-zero (some x outside the window)
-// makes the product use native FP64 on val and x instead.
-static_assert(WarpSlot<float2>::BYTES == WarpSlot<double>::BYTES, "same slot for both paths");
+// ---------------------------------------------------------------- lane-slotted warp tiles
+// FP64 product on the lane-slotted copy of the tiles (build_slots): path item k of lane l
+// sits in slot k * 32 + l, so every operand of a lane is at a fixed offset and the shared
+// memory accesses of a warp are contiguous.  A row end or tail slot holds value 0 and is
+// neither gathered nor accumulated.  Values are split into float pairs at the conversion.
+struct SlotTile {
+    static constexpr int OFF_HDR = 16;                                   // after the mbarrier
+    static constexpr int OFF_COL = OFF_HDR + SLOT_DESC_WORDS * 4;
+    static constexpr int OFF_VAL = OFF_COL + MW_ITEMS * 4;
+    static constexpr int OFF_XB = OFF_VAL + MW_ITEMS * 8;                // gathered x, then finished rows
+    static constexpr int BYTES = OFF_XB + MW_ITEMS * 8;
+    static constexpr uint32_t TX = SLOT_DESC_WORDS * 4 + MW_ITEMS * 12;   // bytes brought by TMA
+};
+static_assert(SlotTile::BYTES % 16 == 0 && SlotTile::OFF_VAL % 16 == 0 && SlotTile::OFF_XB % 16 == 0, "16-byte slots");
 
-__global__ __launch_bounds__(MW_WARPS * 32) void k_merge_warp_df(const uint32_t *__restrict__ desc,
-                                                                 const int32_t *__restrict__ col,
-                                                                 const double *__restrict__ val,
-                                                                 const float2 *__restrict__ val2,
-                                                                 const double *__restrict__ x,
-                                                                 const float2 *__restrict__ x2,
-                                                                 const uint32_t *__restrict__ xflag,
-                                                                 double *__restrict__ y,
-                                                                 const int32_t *__restrict__ part_row,
-                                                                 const int32_t *__restrict__ part_nz,
-                                                                 int32_t *__restrict__ carry_row,
-                                                                 double *__restrict__ carry_val, int64_t ntiles,
-                                                                 uint32_t *__restrict__ err) {
+// Operand forms: double-float (values and x as float pairs), or native FP64 with the value
+// rebuilt from its pair (|a - hi - lo| <= 2^-48 |a|) when x is outside the double-float window.
+template <typename Acc, typename XG> struct SlotOps;
+template <> struct SlotOps<DfAcc, float2> {
+    __device__ __forceinline__ static float2 a(float2 v) { return v; }
+};
+template <> struct SlotOps<NativeAcc<double>, double> {
+    __device__ __forceinline__ static double a(float2 v) { return (double)v.x + (double)v.y; }
+};
+
+__device__ __forceinline__ void slot_issue(const uint32_t *__restrict__ sdesc, const int32_t *__restrict__ scol,
+                                           const float2 *__restrict__ sval, int64_t t, unsigned char *slot,
+                                           uint64_t pol) {
+    uint64_t *bar = (uint64_t *)slot;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(SlotTile::TX)
+                 : "memory");
+    tma_load_1d(slot + SlotTile::OFF_HDR, sdesc + t * SLOT_DESC_WORDS, SLOT_DESC_WORDS * 4, bar, pol);
+    tma_load_1d(slot + SlotTile::OFF_COL, scol + t * MW_ITEMS, MW_ITEMS * 4, bar, pol);
+    tma_load_1d(slot + SlotTile::OFF_VAL, sval + t * MW_ITEMS, MW_ITEMS * 8, bar, pol);
+}
+
+// nonzero items of a lane descriptor: not a row end and inside the lane's item count
+__device__ __forceinline__ uint32_t slot_nz(uint32_t d) { return ~(d >> 16) & ((1u << ((d >> 24) & 7u)) - 1u); }
+
+template <typename XG>
+__device__ __forceinline__ void slot_gather(unsigned char *slot, const XG *__restrict__ xg, uint64_t pol) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t nz = slot_nz(((const uint32_t *)(slot + SlotTile::OFF_HDR))[4 + lane]);
+    const int32_t *sc = (const int32_t *)(slot + SlotTile::OFF_COL) + lane;
+    XG *xb = (XG *)(slot + SlotTile::OFF_XB) + lane;
+#pragma unroll
+    for (int k = 0; k < MW_IPT; ++k)
+        if ((nz >> k) & 1u) cp_async_gather(xb + k * 32, xg + sc[k * 32], pol, 8);
+    cp_async_commit();
+}
+
+template <typename Acc, typename XG>
+__device__ __forceinline__ void slot_compute(int64_t t, unsigned char *slot, double *__restrict__ y,
+                                             int32_t *__restrict__ carry_row, double *__restrict__ carry_val,
+                                             double *__restrict__ head_val) {
+    using Op = typename Acc::Op;
+    const int lane = threadIdx.x & 31;
+    const uint32_t *hd = (const uint32_t *)(slot + SlotTile::OFF_HDR);
+    const uint32_t d = hd[4 + lane];
+    const int64_t i0 = (int32_t)hd[0];
+    const int nrows = (int)hd[1];
+    const bool cont = hd[2] != 0u;
+    const int istart = (int)(d & 0xFFu);
+    const uint32_t bits = (d >> 16) & 0x7Fu, nz = slot_nz(d);
+    const float2 *sv = (const float2 *)(slot + SlotTile::OFF_VAL) + lane;
+    const XG *xb = (const XG *)(slot + SlotTile::OFF_XB) + lane;
+    Op a[MW_IPT], xv[MW_IPT];
+#pragma unroll
+    for (int k = 0; k < MW_IPT; ++k) {
+        a[k] = SlotOps<Acc, XG>::a(sv[k * 32]);
+        xv[k] = xb[k * 32];
+    }
+    __syncwarp();   // the x buffer becomes the finished-row buffer
+    Acc *s_rows = (Acc *)(slot + SlotTile::OFF_XB);
+    Acc acc;
+    acc.zero();
+    int i = istart;
+#pragma unroll
+    for (int k = 0; k < MW_IPT; ++k) {
+        if ((nz >> k) & 1u) {
+            acc.mad(a[k], xv[k]);
+        } else if ((bits >> k) & 1u) {   // row i ends here: stash it
+            s_rows[i] = acc;
+            acc.zero();
+            ++i;
+        }
+    }
+    // segmented inclusive scan of the lanes' trailing partial sums (segments: equal end rows)
+    const int iend = istart + __popc(bits);
+    const int prev_end = __shfl_up_sync(0xffffffffu, iend, 1);
+    const bool head = lane == 0 || prev_end != iend;
+    Acc run = acc;
+    bool f = head;
+    if (!__all_sync(0xffffffffu, head)) {
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            Acc ov = run.shfl_up(o);
+            const bool of = __shfl_up_sync(0xffffffffu, f, o);
+            if (lane >= o) {
+                if (!f) {
+                    ov.add(run);
+                    run = ov;
+                }
+                f = f || of;
+            }
+        }
+    }
+    // a lane's first finished row takes the run of the lanes before it that end in that row
+    const Acc cin = run.shfl_up(1);
+    __syncwarp();
+    if (lane > 0 && istart < iend) {
+        Acc v = cin;
+        v.add(s_rows[istart]);
+        s_rows[istart] = v;
+    }
+    __syncwarp();
+    // lane 31: the tile's carry; lane 0: the partial of a first row begun in an earlier tile
+    if (lane == 31 || (lane == 0 && cont && nrows > 0)) {
+        const double dv = (lane == 31 ? run : s_rows[0]).to_double();
+        if (lane == 31) {
+            carry_row[t] = (int32_t)(i0 + nrows);
+            carry_val[t] = dv;
+        } else {
+            head_val[t] = dv;
+        }
+    }
+    for (int r = (cont ? 1 : 0) + lane; r < nrows; r += 32) y[i0 + r] = s_rows[r].template out<double>();
+}
+
+// Persistent warp over tiles w, w + W, ... with SLOT_STAGES slots: while tile k is computed,
+// the gathers of x for tile k+1 and the bulk copies of tiles k+2 .. k+SLOT_STAGES-1 are in
+// flight.
+constexpr int SLOT_STAGES = 2;
+
+template <int NW, typename Acc, typename XG>
+__device__ __forceinline__ void slot_run(int64_t ntiles, const uint32_t *__restrict__ sdesc,
+                                         const int32_t *__restrict__ scol, const float2 *__restrict__ sval,
+                                         const XG *__restrict__ xg, double *__restrict__ y,
+                                         int32_t *__restrict__ carry_row, double *__restrict__ carry_val,
+                                         uint32_t *__restrict__ err, unsigned char *wslots) {
+    const int lane = threadIdx.x & 31;
+    const int64_t W = (int64_t)gridDim.x * NW;
+    int64_t t = (int64_t)blockIdx.x * NW + (threadIdx.x >> 5);
+    if (t >= ntiles) return;
+    auto slot = [&](int i) { return wslots + i * SlotTile::BYTES; };
+    auto bar = [&](int i) { return (uint64_t *)(wslots + i * SlotTile::BYTES); };
+    const uint64_t stream_pol = l2_policy_evict_first(), keep_pol = l2_policy_evict_last();
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < SLOT_STAGES; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bar(i))) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < SLOT_STAGES; ++i)
+            if (t + i * W < ntiles) slot_issue(sdesc, scol, sval, t + i * W, slot(i), stream_pol);
+    }
+    __syncwarp();
+    uint32_t parity = 0;   // bit i: phase parity of the next completion of slot i
+    if (!mbar_wait(bar(0), 0u)) {
+        if (lane == 0) atomicOr(err, ST_TIMEOUT);
+        return;
+    }
+    parity ^= 1u;
+    slot_gather<XG>(slot(0), xg, keep_pol);
+    int cs = 0;
+    for (; t < ntiles; t += W) {
+        const int ns = cs + 1 == SLOT_STAGES ? 0 : cs + 1;
+        if (t + W < ntiles) {   // the next tile's copies have landed: start its gathers
+            if (!mbar_wait(bar(ns), (parity >> ns) & 1u)) {
+                if (lane == 0) atomicOr(err, ST_TIMEOUT);
+                cp_async_wait<0>();
+                return;
+            }
+            parity ^= 1u << ns;
+            slot_gather<XG>(slot(ns), xg, keep_pol);
+            cp_async_wait<1>();   // this lane's gathers of tile t are complete
+        } else {
+            cp_async_wait<0>();
+        }
+        slot_compute<Acc, XG>(t, slot(cs), y, carry_row, carry_val, carry_val + ntiles);
+        __syncwarp();   // slot cs is free
+        if (lane == 0 && t + SLOT_STAGES * W < ntiles)
+            slot_issue(sdesc, scol, sval, t + SLOT_STAGES * W, slot(cs), stream_pol);
+        cs = ns;
+    }
+}
+
+// SLOT_WARPS warps per CTA, SLOT_CTAS CTAs per SM: enough warps to cover the latencies,
+// and a carveout that leaves ~60 KB of the SM's on-chip memory to the L1 cache, where the
+// gathers of frequently used x entries hit (measured on R-MAT scale 22: 381 us with 60-92 KB
+// of L1 against 524 us with 28 KB).
+// x2 holds x split per product; *xflag non-zero (some x outside the window) switches to
+// native FP64 on x with the values rebuilt from their pairs.
+constexpr int SLOT_WARPS = 4;
+constexpr int SLOT_CTAS = 5;
+constexpr size_t SLOT_SMEM = (size_t)SLOT_WARPS * SLOT_STAGES * SlotTile::BYTES;
+
+__global__ __launch_bounds__(SLOT_WARPS * 32) void k_merge_slot_df(const uint32_t *__restrict__ sdesc,
+                                                                   const int32_t *__restrict__ scol,
+                                                                   const float2 *__restrict__ sval2,
+                                                                   const double *__restrict__ x,
+                                                                   const float2 *__restrict__ x2,
+                                                                   const uint32_t *__restrict__ xflag,
+                                                                   double *__restrict__ y,
+                                                                   int32_t *__restrict__ carry_row,
+                                                                   double *__restrict__ carry_val, int64_t ntiles,
+                                                                   uint32_t *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned char *ws = smem_raw + (threadIdx.x >> 5) * 2 * WarpSlot<double>::BYTES;
+    unsigned char *ws = smem_raw + (threadIdx.x >> 5) * SLOT_STAGES * SlotTile::BYTES;
     if (*xflag == 0u)
-        merge_warp_run<DfAcc, DfSLoad, float2, float2, double>(ntiles, desc, col, val2, x2, y, part_row, part_nz,
-                                                               carry_row, carry_val, err, ws);
+        slot_run<SLOT_WARPS, DfAcc, float2>(ntiles, sdesc, scol, sval2, x2, y, carry_row, carry_val, err, ws);
     else
-        merge_warp_run<NativeAcc<double>, NativeSLoad<double, double>, double, double, double>(
-            ntiles, desc, col, val, x, y, part_row, part_nz, carry_row, carry_val, err, ws);
+        slot_run<SLOT_WARPS, NativeAcc<double>, double>(ntiles, sdesc, scol, sval2, x, y, carry_row, carry_val,
+                                                        err, ws);
 }
 
 // Pattern matrix (every stored value 1) with an FP64 vector through double-float: the value
@@ -733,15 +917,13 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
                           std::is_same<AT, double>::value;
     constexpr size_t smem = (size_t)MW_WARPS * 2 * WarpSlot<VT>::BYTES;
     if constexpr (FP64) {
-        if (allow_df && h->df_ok && h->xsplit && h->val2) {
-            constexpr size_t smem_df = (size_t)MW_WARPS * 2 * WarpSlot<double>::BYTES;
+        if (allow_df && h->df_ok && h->xsplit && h->slot_val2) {
             static bool attr = false;
             if (!attr) {
-                SPMV_CUDA_TRY(cudaFuncSetAttribute(k_merge_warp_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)smem_df));
+                SPMV_TRY(set_smem_ctas((const void *)k_merge_slot_df, SLOT_SMEM, SLOT_CTAS));
                 attr = true;
             }
-            const unsigned grid = persistent_grid((const void *)k_merge_warp_df, MW_WARPS * 32, smem_df, h->tiles);
+            const unsigned grid = persistent_grid((const void *)k_merge_slot_df, SLOT_WARPS * 32, SLOT_SMEM, h->tiles);
             SPMV_CUDA_TRY(cudaMemsetAsync(h->xsplit_flag, 0, 4, s));
             if (h->n > 0) {
                 SPMV_LAUNCH("k_df_split_x", s,
@@ -750,11 +932,9 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
                 SPMV_LAUNCH_CHECK("x split");
             }
             SPMV_LAUNCH("k_merge_spmv", s,
-                        (k_merge_warp_df<<<grid, MW_WARPS * 32, smem_df, s>>>(
-                            h->merge_desc, h->col, (const double *)h->val, h->val2, (const double *)x, h->xsplit,
-                            h->xsplit_flag,
-                            (double *)y, h->part_row, h->part_nz, h->carry_row, h->carry_val, h->tiles,
-                            h->status_dev + 3)));
+                        (k_merge_slot_df<<<grid, SLOT_WARPS * 32, SLOT_SMEM, s>>>(
+                            h->slot_desc, h->slot_col, h->slot_val2, (const double *)x, h->xsplit, h->xsplit_flag,
+                            (double *)y, h->carry_row, h->carry_val, h->tiles, h->status_dev + 3)));
             SPMV_LAUNCH_CHECK("merge spmv");
             SPMV_LAUNCH("k_merge_fixup", s, (k_merge_fixup_tiles<double><<<cdivu(h->tiles, 256), 256, 0, s>>>(
                                                 h->tiles, h->m, h->carry_row, h->carry_val, h->merge_desc,
@@ -765,8 +945,7 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
     }
     static bool attr = false;
     if (!attr) {
-        SPMV_CUDA_TRY(cudaFuncSetAttribute(k_merge_warp<VT, XT, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
+        SPMV_TRY(set_smem((const void *)k_merge_warp<VT, XT, AT>, smem));
         attr = true;
     }
     const unsigned grid = persistent_grid((const void *)k_merge_warp<VT, XT, AT>, MW_WARPS * 32, smem, h->tiles);
@@ -966,7 +1145,7 @@ spmv_status launch_merge_comp(const spmv_matrix *h, const void *x, void *y, cuda
     constexpr size_t smem = (size_t)MW_WARPS * 2 * WarpSlot<VT>::BYTES;
     static bool attr = false;
     if (!attr) {
-        SPMV_CUDA_TRY(cudaFuncSetAttribute(k_merge_warp_comp<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SPMV_TRY(set_smem((const void *)k_merge_warp_comp<VT>, smem));
         attr = true;
     }
     const unsigned grid = persistent_grid((const void *)k_merge_warp_comp<VT>, MW_WARPS * 32, smem, h->tiles);
@@ -1121,7 +1300,7 @@ spmv_status mul_merge_pattern_split(const spmv_matrix *h, const double *x, const
     constexpr size_t smem = (size_t)MW_WARPS * 2 * WarpSlot<Pattern>::BYTES;
     static bool attr = false;
     if (!attr) {
-        SPMV_CUDA_TRY(cudaFuncSetAttribute(k_merge_warp_pat_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SPMV_TRY(set_smem((const void *)k_merge_warp_pat_df, smem));
         attr = true;
     }
     const unsigned grid = persistent_grid((const void *)k_merge_warp_pat_df, MW_WARPS * 32, smem, h->tiles);
