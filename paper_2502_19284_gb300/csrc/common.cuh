@@ -149,6 +149,11 @@ struct spmv_matrix {
     int64_t tiles = 0;
     int32_t *part_row = nullptr, *part_nz = nullptr;
     int32_t *carry_row = nullptr;
+    // static run structure of the carries (a run: consecutive tiles ending inside one row):
+    // fix_len[t] = run length at a run's first tile, else 0; fix_long lists the runs longer
+    // than FIX_SHORT tiles (fix_long_count of them), which a whole warp sums
+    int32_t *fix_len = nullptr, *fix_long = nullptr;
+    int64_t fix_long_count = 0;
     double *carry_val = nullptr;      // tiles carries, then tiles head partials (a tile's first
                                       // row when it began in an earlier tile)
     uint32_t *merge_desc = nullptr;   // per-lane descriptors of the warp tiles (32 words per tile)

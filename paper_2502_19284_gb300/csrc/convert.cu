@@ -281,6 +281,29 @@ __global__ void k_merge_slots(const int32_t *__restrict__ row_ptr, const int32_t
     }
 }
 
+// Static carry runs: the row in progress at the end of tile t is part_row[t + 1] (it is the
+// tile's carry row), a run starts where that row changes, and its length comes from a
+// bisection for the last tile ending in the same row (part_row is non-decreasing).
+__global__ void k_fix_runs(const int32_t *__restrict__ part_row, int64_t tiles, int32_t *__restrict__ fix_len,
+                           int32_t *__restrict__ fix_long, unsigned long long *__restrict__ nlong) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tiles) return;
+    const int32_t r = part_row[t + 1];
+    if (t > 0 && part_row[t] == r) {
+        fix_len[t] = 0;
+        return;
+    }
+    int64_t lo = t + 1, hi = tiles;   // largest j in [t+1, tiles] with part_row[j] == r
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (part_row[mid] <= r) lo = mid;
+        else hi = mid - 1;
+    }
+    const int32_t len = (int32_t)(lo - t);
+    fix_len[t] = len;
+    if (len > FIX_SHORT) fix_long[atomicAdd(nlong, 1ull)] = (int32_t)t;
+}
+
 // slot arrays from the CRS arrays through the slot -> CRS index map
 __global__ void k_slot_fill(const int32_t *__restrict__ src, int64_t n, const int32_t *__restrict__ col,
                             const double *__restrict__ val, int32_t *__restrict__ scol, float2 *__restrict__ sval2) {
@@ -658,6 +681,32 @@ spmv_status build_slots(spmv_matrix *h, cudaStream_t s) {
     return SPMV_OK;
 }
 
+spmv_status build_fix_runs(spmv_matrix *h, const int32_t *part_row, int64_t tiles, int64_t old_tiles,
+                           cudaStream_t s) {
+    DevBuf fl(s), fg(s), cnt(s);
+    SPMV_TRY(fl.alloc((size_t)tiles * 4, "carry runs"));
+    SPMV_TRY(fg.alloc((size_t)tiles * 4, "long carry runs"));
+    SPMV_TRY(cnt.alloc(16, "long run count"));
+    SPMV_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, 8, s));
+    SPMV_LAUNCH("k_fix_runs", s, (k_fix_runs<<<grid_for(tiles), CB, 0, s>>>(part_row, tiles, fl.as<int32_t>(),
+                                                                           fg.as<int32_t>(),
+                                                                           (unsigned long long *)cnt.p)));
+    SPMV_LAUNCH_CHECK("carry runs");
+    unsigned long long nlong = 0;
+    SPMV_CUDA_TRY(cudaMemcpyAsync(&nlong, cnt.p, 8, cudaMemcpyDeviceToHost, s));
+    SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h->fix_len) {
+        dev_free_async(h->fix_len, s);
+        dev_free_async(h->fix_long, s);
+        h->bytes -= old_tiles * 8;
+    }
+    h->fix_len = (int32_t *)fl.release();
+    h->fix_long = (int32_t *)fg.release();
+    h->fix_long_count = (int64_t)nlong;
+    h->bytes += tiles * 8;
+    return SPMV_OK;
+}
+
 spmv_status build_merge(spmv_matrix *h, int tile_items, cudaStream_t s) {
     const int64_t total = h->m + h->nnz;
     const int64_t tiles = std::max<int64_t>(1, (total + tile_items - 1) / tile_items);
@@ -683,10 +732,16 @@ spmv_status build_merge(spmv_matrix *h, int tile_items, cudaStream_t s) {
     h->part_nz = (int32_t *)pn.release();
     h->carry_row = (int32_t *)cr.release();
     h->carry_val = (double *)cv.release();
+    const int64_t old_tiles = h->tiles;
     h->tiles = tiles;
     h->tile_items = tile_items;
     h->has_merge = true;
     h->bytes += (tiles + 1) * 8 + tiles * 20 + tiles * 128;
+    const spmv_status fst = build_fix_runs(h, h->part_row, tiles, old_tiles, s);
+    if (fst != SPMV_OK) {
+        h->has_merge = false;
+        return fst;
+    }
     if (tile_items == MERGE_WARP_ITEMS) SPMV_TRY(build_slots(h, s));
     return SPMV_OK;
 }

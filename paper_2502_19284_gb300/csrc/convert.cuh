@@ -21,6 +21,8 @@ constexpr int MERGE_WARP_ITEMS = 32 * MERGE_WARP_IPT;
 // Lane-slotted tile header: words 0..3 = first row, row count, continuation flag, 0;
 // words 4..35 = the 32 lane descriptors; words 36..39 = 0 (a tile's block is 160 bytes).
 constexpr int SLOT_DESC_WORDS = 40;
+// Carry runs up to FIX_SHORT tiles are summed by one thread, longer ones by a warp.
+constexpr int FIX_SHORT = 16;
 
 __host__ __device__ __forceinline__ int class_lanes(int c) {
     return c == 0 ? 1 : c == 1 ? 2 : c == 2 ? 4 : c == 3 ? 8 : c == 4 ? 16 : 32;

@@ -886,24 +886,65 @@ inline unsigned persistent_grid(const void *kernel, int block, size_t smem, int6
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per_sm));
 }
 
-// Carry fix-up of the warp tiles: the first tile of each run of equal carry rows sums the
-// run's carries in tile order; the tile after the run finished that row: if it marked the
-// row as begun earlier, its parked partial is added and the row written once (one rounding
-// to the output type); otherwise the run's carries are all zero and y is left as written.
+// Carry fix-up of the warp tiles.  A run is a maximal sequence of tiles that end inside
+// one row r (their carry row); the tile after the run finishes r.  If that tile marked r as
+// begun earlier, it parked r's partial instead of writing y[r]: y[r] = run sum + partial
+// (one rounding to the output type); otherwise the run's carries are all zero and y[r]
+// stays as written.  The run structure is static (conversion); short runs are summed in
+// tile order by one thread, long ones by a warp (lane-strided partial sums, then a fixed
+// shuffle tree), so every result is the same from call to call.
+struct spmv_matrix_view {   // what the fix-up kernels read of a handle
+    int64_t m, tiles, fix_long_count;
+    const uint32_t *desc;
+    const int32_t *carry_row, *fix_len, *fix_long;
+    const double *carry_val;
+};
+inline spmv_matrix_view view_of(const spmv_matrix *h) {
+    return {h->m, h->tiles, h->fix_long_count, h->merge_desc, h->carry_row, h->fix_len, h->fix_long, h->carry_val};
+}
+
 template <typename XT>
-__global__ void k_merge_fixup_tiles(int64_t tiles, int64_t m, const int32_t *__restrict__ carry_row,
-                                    const double *__restrict__ carry_val, const uint32_t *__restrict__ desc,
-                                    XT *__restrict__ y) {
+__device__ __forceinline__ void fix_finish(const spmv_matrix_view &v, int64_t u, int32_t row, double sum, XT *y) {
+    if (row >= v.m || u >= v.tiles) return;
+    if (v.desc[u * 32] >> 31) y[row] = XT(sum + v.carry_val[v.tiles + u]);
+    else if (sum != 0.0) y[row] = XT((double)y[row] + sum);
+}
+
+template <typename XT>
+__global__ void k_fix_short(spmv_matrix_view v, XT *__restrict__ y) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= tiles) return;
-    const int32_t row = carry_row[t];
-    if (t > 0 && carry_row[t - 1] == row) return;
-    double s = carry_val[t];
-    int64_t u = t + 1;
-    for (; u < tiles && carry_row[u] == row; ++u) s = s + carry_val[u];
-    if (row >= m || u >= tiles) return;
-    if (desc[u * 32] >> 31) y[row] = XT(s + carry_val[tiles + u]);
-    else if (s != 0.0) y[row] = XT((double)y[row] + s);
+    if (t >= v.tiles) return;
+    const int len = v.fix_len[t];
+    if (len == 0 || len > FIX_SHORT) return;
+    double s = v.carry_val[t];
+    for (int k = 1; k < len; ++k) s = s + v.carry_val[t + k];
+    fix_finish<XT>(v, t + len, v.carry_row[t], s, y);
+}
+
+template <typename XT>
+__global__ void k_fix_long(spmv_matrix_view v, XT *__restrict__ y) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= v.fix_long_count) return;
+    const int64_t t0 = v.fix_long[w];
+    const int len = v.fix_len[t0];
+    double s = 0.0;
+    for (int k = lane; k < len; k += 32) s = s + v.carry_val[t0 + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = s + __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) fix_finish<XT>(v, t0 + len, v.carry_row[t0], s, y);
+}
+
+template <typename XT>
+spmv_status launch_fixup(const spmv_matrix *h, XT *y, cudaStream_t s) {
+    const spmv_matrix_view v = view_of(h);
+    SPMV_LAUNCH("k_merge_fixup", s, (k_fix_short<XT><<<cdivu(h->tiles, 256), 256, 0, s>>>(v, y)));
+    SPMV_LAUNCH_CHECK("merge fixup");
+    if (h->fix_long_count > 0) {
+        SPMV_LAUNCH("k_merge_fixup_long", s, (k_fix_long<XT><<<cdivu(h->fix_long_count * 32, 256), 256, 0, s>>>(v, y)));
+        SPMV_LAUNCH_CHECK("merge fixup long");
+    }
+    return SPMV_OK;
 }
 
 template <typename Acc>
@@ -936,10 +977,7 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
                             h->slot_desc, h->slot_col, h->slot_val2, (const double *)x, h->xsplit, h->xsplit_flag,
                             (double *)y, h->carry_row, h->carry_val, h->tiles, h->status_dev + 3)));
             SPMV_LAUNCH_CHECK("merge spmv");
-            SPMV_LAUNCH("k_merge_fixup", s, (k_merge_fixup_tiles<double><<<cdivu(h->tiles, 256), 256, 0, s>>>(
-                                                h->tiles, h->m, h->carry_row, h->carry_val, h->merge_desc,
-                                                (double *)y)));
-            SPMV_LAUNCH_CHECK("merge fixup");
+            SPMV_TRY(launch_fixup<double>(h, (double *)y, s));
             return SPMV_OK;
         }
     }
@@ -953,9 +991,7 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
                                        h->merge_desc, h->col, (const VT *)h->val, (const XT *)x, (XT *)y, h->part_row,
                                        h->part_nz, h->carry_row, h->carry_val, h->tiles, h->status_dev + 3)));
     SPMV_LAUNCH_CHECK("merge spmv");
-    SPMV_LAUNCH("k_merge_fixup", s, (k_merge_fixup_tiles<XT><<<cdivu(h->tiles, 256), 256, 0, s>>>(
-                                        h->tiles, h->m, h->carry_row, h->carry_val, h->merge_desc, (XT *)y)));
-    SPMV_LAUNCH_CHECK("merge fixup");
+    SPMV_TRY(launch_fixup<XT>(h, (XT *)y, s));
     return SPMV_OK;
 }
 
@@ -1154,9 +1190,7 @@ spmv_status launch_merge_comp(const spmv_matrix *h, const void *x, void *y, cuda
                                        h->part_row, h->part_nz, h->carry_row, h->carry_val, h->tiles,
                                        h->status_dev + 3)));
     SPMV_LAUNCH_CHECK("merge spmv");
-    SPMV_LAUNCH("k_merge_fixup", s, (k_merge_fixup_tiles<float><<<cdivu(h->tiles, 256), 256, 0, s>>>(
-                                        h->tiles, h->m, h->carry_row, h->carry_val, h->merge_desc, (float *)y)));
-    SPMV_LAUNCH_CHECK("merge fixup");
+    SPMV_TRY(launch_fixup<float>(h, (float *)y, s));
     return SPMV_OK;
 }
 
@@ -1308,9 +1342,7 @@ spmv_status mul_merge_pattern_split(const spmv_matrix *h, const double *x, const
                                        h->merge_desc, h->col, x, x2, xflag, y, h->part_row, h->part_nz, h->carry_row,
                                        h->carry_val, h->tiles, h->status_dev + 3)));
     SPMV_LAUNCH_CHECK("pattern merge spmv");
-    SPMV_LAUNCH("k_merge_fixup", s, (k_merge_fixup_tiles<double><<<cdivu(h->tiles, 256), 256, 0, s>>>(
-                                        h->tiles, h->m, h->carry_row, h->carry_val, h->merge_desc, y)));
-    SPMV_LAUNCH_CHECK("merge fixup");
+    SPMV_TRY(launch_fixup<double>(h, y, s));
     return SPMV_OK;
 }
 
