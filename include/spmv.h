@@ -155,7 +155,8 @@ spmv_status spmv_mul(spmv_handle h, const void *x, void *y, spmv_dtype vec_dt, u
  * the first time a batch shape (the handles, k, dtypes, accumulation and 16-byte
  * alignment of X/Y) is seen, and replayed after that; only the table of X/Y pointers is
  * copied per call.  Per column, the result is bitwise the one spmv_mul gives for the
- * same accumulation on the merge path.  Calls with the same batch shape share scratch
+ * same accumulation on the merge path (FP64 vectors accumulate in native FP64 here, so
+ * SPMV_ACC_DEFAULT matches spmv_mul with SPMV_ACC_F64).  Calls with the same batch shape share scratch
  * and must be ordered.  Not capturable into a caller's graph (the pointer table is
  * uploaded from pageable memory).  A handle's plans are dropped when it is converted
  * again or destroyed.
@@ -232,6 +233,84 @@ spmv_status spmv_hilbert_keys(int K, int64_t n, const int32_t *rows, const int32
  * graph is replayed on `stream` (asynchronously) by this and later calls.
  */
 spmv_status spmv_pagerank(spmv_handle h, double damping, int iters, double *x, void *stream);
+
+/* ---------------------------------------------------------------- serving */
+
+/*
+ * A request loop over a resident set of converted matrices (the paper has no counterpart;
+ * its introduction names PageRank as an application built on SpMV).  A worker thread admits
+ * queued requests in arrival order as launch slots and the memory budget allow: the first
+ * request that fits opens a group; a SpMV group then takes every later queued SpMV request
+ * with the same vector type and accumulation (up to max_batch) that still fits and runs
+ * them as one batched launch (the product of spmv_mul_batch, without capture); a PageRank
+ * request runs alone, at most one per matrix at a time.  Slots run concurrently on their
+ * own CUDA streams, so requests arriving while others run start as soon as a slot and
+ * memory free up.  Every SpMV result is bitwise the spmv_mul_batch result (and so the
+ * spmv_mul result with the same accumulation on the merge path; FP64 vectors accumulate in
+ * native FP64), and every PageRank result the spmv_pagerank result, whatever else is in
+ * flight.
+ *
+ * Memory: the budget covers the resident matrices (their spmv_info bytes at spmv_server_add,
+ * plus the PageRank scratch of a matrix from its first PageRank request on) and, per admitted
+ * SpMV request, its device x and y and batch scratch.  A request that cannot fit even with
+ * nothing else in flight completes with SPMV_ERR_OOM.
+ * Host buffers: x and y may be device pointers, pinned host memory (copied by DMA), or
+ * pageable host memory (staged through pinned buffers of the slot).  The caller keeps them
+ * valid until the request completes.  Latency = completion - arrival on the host's steady
+ * clock; completion is the moment the worker sees the request's work (including the copy of
+ * y) finished.
+ */
+typedef struct spmv_server *spmv_server_t;
+
+typedef struct {
+    int64_t budget_bytes;   /* device memory for resident matrices and admitted requests */
+    int32_t slots;          /* concurrent launches, one CUDA stream each: 1..64 */
+    int32_t max_batch;      /* SpMV requests grouped into one launch: 1..1024 */
+} spmv_server_opts;
+
+enum { SPMV_REQ_SPMV = 0, SPMV_REQ_PAGERANK = 1 };
+
+typedef struct {
+    int32_t kind;        /* SPMV_REQ_SPMV or SPMV_REQ_PAGERANK */
+    int32_t matrix;      /* id returned by spmv_server_add */
+    int32_t vec_dt;      /* SpMV: SPMV_F64 or SPMV_F32 (type of x and y) */
+    uint32_t accum;      /* SpMV: SPMV_ACC_* as in spmv_mul (merge path) */
+    int32_t iters;       /* PageRank: iterations (0..10000) */
+    int32_t pad_;        /* 0 */
+    double damping;      /* PageRank: in [0, 1] */
+    const void *x;       /* SpMV: n elements of vec_dt; unused for PageRank */
+    void *y;             /* SpMV: m elements of vec_dt; PageRank: n doubles */
+} spmv_request;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t launches;            /* batched SpMV launches */
+    int64_t batched_requests;    /* SpMV requests those launches carried */
+    int64_t resident_bytes;      /* resident set */
+    int64_t peak_bytes;          /* peak of resident set + admitted requests */
+    int64_t deferred;            /* admissions postponed because memory was short */
+} spmv_server_stats_t;
+
+/* Start the worker thread on the current device.  Errors: SPMV_ERR_INVALID_ARG (limits
+ * above), SPMV_ERR_CUDA. */
+spmv_status spmv_server_create(const spmv_server_opts *opts, spmv_server_t *out);
+/* Add a converted handle (any format; its merge-path tiles are built if missing) to the
+ * resident set.  The caller keeps ownership and destroys it after spmv_server_destroy.
+ * SPMV_ERR_OOM if the resident set would exceed the budget. */
+spmv_status spmv_server_add(spmv_server_t srv, spmv_handle h, int32_t *matrix_id);
+/* Queue a request (arrival = now); *ticket identifies it for spmv_server_wait. */
+spmv_status spmv_server_submit(spmv_server_t srv, const spmv_request *req, int64_t *ticket);
+/* Block until the request completes; returns its status and (if latency_s) its latency in
+ * seconds.  A ticket can be waited for once. */
+spmv_status spmv_server_wait(spmv_server_t srv, int64_t ticket, double *latency_s);
+/* Open-loop replay: submit reqs[i] at arrival_s[i] seconds (non-decreasing) after the call
+ * starts, from the calling thread, then wait for all; latency_s[i] receives each latency
+ * (-1 for requests not submitted after an error).  Returns the first error. */
+spmv_status spmv_server_replay(spmv_server_t srv, int64_t n, const spmv_request *reqs, const double *arrival_s,
+                               double *latency_s);
+spmv_status spmv_server_stats(spmv_server_t srv, spmv_server_stats_t *out);
+/* Finish queued and running requests, stop the worker, free the server's memory. */
+spmv_status spmv_server_destroy(spmv_server_t srv);
 
 /* ---------------------------------------------------------------- no allocation */
 

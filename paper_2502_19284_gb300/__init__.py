@@ -48,6 +48,24 @@ class spmv_info_t(ctypes.Structure):
                 ("pad_", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
 
 
+class spmv_server_opts(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int32), ("max_batch", ctypes.c_int32)]
+
+
+SPMV_REQ_SPMV, SPMV_REQ_PAGERANK = 0, 1
+
+
+class spmv_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("matrix", ctypes.c_int32), ("vec_dt", ctypes.c_int32),
+                ("accum", ctypes.c_uint32), ("iters", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("damping", ctypes.c_double), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p)]
+
+
+class spmv_server_stats_t(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "failed", "launches", "batched_requests",
+                                              "resident_bytes", "peak_bytes", "deferred")]
+
+
 _p, _i64, _i32, _u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32
 _SIG = {
     "spmv_create_coo": [_i64, _i64, _i64, _p, _p, _p, _i32, _u32, _p, ctypes.POINTER(_p)],
@@ -62,6 +80,13 @@ _SIG = {
     "spmv_hilbert_keys": [_i32, _i64, _p, _p, _p, _p],
     "spmv_mul_csr_merge_noalloc": [_i64, _i64, _i64, _p, _p, _p, _p, _p, _p],
     "spmv_pagerank": [_p, ctypes.c_double, _i32, _p, _p],
+    "spmv_server_create": [ctypes.POINTER(spmv_server_opts), ctypes.POINTER(_p)],
+    "spmv_server_add": [_p, _p, ctypes.POINTER(ctypes.c_int32)],
+    "spmv_server_submit": [_p, ctypes.POINTER(spmv_request), ctypes.POINTER(ctypes.c_int64)],
+    "spmv_server_wait": [_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)],
+    "spmv_server_replay": [_p, ctypes.c_int64, ctypes.POINTER(spmv_request), _p, _p],
+    "spmv_server_stats": [_p, ctypes.POINTER(spmv_server_stats_t)],
+    "spmv_server_destroy": [_p],
 }
 for _name, _args in _SIG.items():
     _f = getattr(_lib, _name)
@@ -282,6 +307,61 @@ def _host_values(dt, nnz):
     if dt == SPMV_BF16:
         return np.empty(max(nnz, 1), np.uint16)
     return None
+
+
+class Server:
+    """Serving loop (spmv_server_*): resident matrices, admission by slots and memory,
+    continuous batching of SpMV requests, PageRank requests."""
+
+    def __init__(self, budget_bytes: int, slots: int = 4, max_batch: int = 64):
+        opts = spmv_server_opts(int(budget_bytes), int(slots), int(max_batch))
+        out = ctypes.c_void_p()
+        _check(_lib.spmv_server_create(ctypes.byref(opts), ctypes.byref(out)), "spmv_server_create")
+        self.ptr = out.value
+
+    def add(self, h: Handle) -> int:
+        mid = ctypes.c_int32()
+        _check(_lib.spmv_server_add(self.ptr, h.ptr, ctypes.byref(mid)), "spmv_server_add")
+        return mid.value
+
+    @staticmethod
+    def request(kind, matrix, y, x=None, accum=SPMV_ACC_DEFAULT, iters=20, damping=0.85) -> spmv_request:
+        vdt = dtype_code(y) if kind == SPMV_REQ_SPMV else SPMV_F64
+        return spmv_request(kind, matrix, vdt, accum, iters, 0, damping, _addr(x), _addr(y))
+
+    def submit(self, req: spmv_request) -> int:
+        t = ctypes.c_int64()
+        _check(_lib.spmv_server_submit(self.ptr, ctypes.byref(req), ctypes.byref(t)), "spmv_server_submit")
+        return t.value
+
+    def wait(self, ticket: int) -> float:
+        lat = ctypes.c_double()
+        _check(_lib.spmv_server_wait(self.ptr, int(ticket), ctypes.byref(lat)), "spmv_server_wait")
+        return lat.value
+
+    def replay(self, reqs, arrival_s) -> np.ndarray:
+        n = len(reqs)
+        arr = (spmv_request * max(n, 1))(*reqs)
+        t = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        lat = np.empty(max(n, 1), np.float64)
+        _check(_lib.spmv_server_replay(self.ptr, n, arr, t.ctypes.data, lat.ctypes.data), "spmv_server_replay")
+        return lat[:n]
+
+    def stats(self) -> dict:
+        st = spmv_server_stats_t()
+        _check(_lib.spmv_server_stats(self.ptr, ctypes.byref(st)), "spmv_server_stats")
+        return {k: getattr(st, k) for k, _ in spmv_server_stats_t._fields_}
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            p, self.ptr = self.ptr, None
+            _check(_lib.spmv_server_destroy(p), "spmv_server_destroy")
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def library_path() -> str:

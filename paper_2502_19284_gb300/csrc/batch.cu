@@ -385,6 +385,95 @@ spmv_status enqueue_plan(Plan *p, cudaStream_t s) {
 
 }  // namespace
 
+// ---------------------------------------------------------------- direct batches
+// A batch launched without capture, on caller-owned scratch (one per concurrent stream): the
+// serving loop groups whatever requests are admitted together, so shapes rarely repeat.
+struct BatchSlot {
+    Plan plan;
+    int64_t cap_mats = 0, cap_tiles = 0, cap_carry = 0;   // device capacities (entries)
+};
+
+BatchSlot *batch_slot_new() { return new BatchSlot(); }
+
+void batch_slot_free(BatchSlot *b) {
+    if (!b) return;
+    dev_free(b->plan.d_mats);
+    dev_free(b->plan.d_prefix);
+    dev_free(b->plan.d_carry);
+    dev_free(b->plan.d_crow);
+    b->plan.d_mats = nullptr;
+    delete b;
+}
+
+int64_t batch_scratch_bytes(int count, spmv_matrix *const *hs, int k) {
+    int64_t tiles = 0;
+    for (int i = 0; i < count; ++i) tiles += hs[i]->tiles;
+    return (int64_t)count * (int64_t)sizeof(MatEntry) + (count + 1) * 8 + tiles * (16 * k + 4);
+}
+
+spmv_status batch_direct(BatchSlot *b, int count, spmv_matrix *const *hs, int k, const void *const *X,
+                         void *const *Y, spmv_dtype vdt, uint32_t acc, cudaStream_t s) {
+    if (count == 0) return SPMV_OK;
+    const int dt = hs[0]->dt;
+    for (int i = 0; i < count; ++i)
+        if (!hs[i]->has_merge || hs[i]->dt != dt) {
+            set_error("batch: every matrix needs merge tiles and one dtype");
+            return SPMV_ERR_UNSUPPORTED;
+        }
+    if (acc == SPMV_ACC_DEFAULT)
+        acc = (dt == SPMV_F64 || (dt == SPMV_PATTERN && vdt == SPMV_F64)) ? SPMV_ACC_F64 : SPMV_ACC_F32;
+    const int es = vdt == SPMV_F64 ? 8 : 4;
+    bool vec4 = (k % 4) == 0;
+    for (int i = 0; i < count && vec4; ++i)
+        vec4 = ((uintptr_t)X[i] % (size_t)(4 * es)) == 0 && ((uintptr_t)Y[i] % (size_t)es) == 0;
+    Plan *p = &b->plan;
+    p->hs.assign(hs, hs + count);
+    p->k = k;
+    p->vdt = vdt;
+    p->acc = acc;
+    p->dt = dt;
+    p->vec4 = vec4;
+    std::vector<int64_t> prefix(count + 1, 0);
+    for (int i = 0; i < count; ++i) prefix[i + 1] = prefix[i] + hs[i]->tiles;
+    p->total_tiles = prefix[count];
+    if (p->total_tiles == 0) return SPMV_OK;
+    auto grow = [&](void **ptr, int64_t &cap, int64_t need, size_t unit, const char *what) -> spmv_status {
+        if (need <= cap) return SPMV_OK;
+        if (*ptr) dev_free_async(*ptr, s);
+        *ptr = nullptr;
+        cap = 0;
+        SPMV_TRY(dev_alloc(ptr, (size_t)need * unit, what, s));
+        cap = need;
+        return SPMV_OK;
+    };
+    int64_t cap_prefix = b->cap_mats ? b->cap_mats + 1 : 0;
+    SPMV_TRY(grow((void **)&p->d_mats, b->cap_mats, count, sizeof(MatEntry), "batch table"));
+    SPMV_TRY(grow((void **)&p->d_prefix, cap_prefix, count + 1, 8, "batch prefix"));
+    SPMV_TRY(grow((void **)&p->d_carry, b->cap_carry, 2 * p->total_tiles * k, 8, "batch carries"));
+    SPMV_TRY(grow((void **)&p->d_crow, b->cap_tiles, p->total_tiles, 4, "batch carry rows"));
+    p->h_mats.resize(count);
+    for (int i = 0; i < count; ++i) {
+        MatEntry &e = p->h_mats[i];
+        spmv_matrix *h = hs[i];
+        e.desc = h->merge_desc;
+        e.col = h->col;
+        e.val = h->val;
+        e.part_row = h->part_row;
+        e.part_nz = h->part_nz;
+        e.x = X[i];
+        e.y = Y[i];
+        e.carry = p->d_carry + 2 * prefix[i] * k;
+        e.carry_row = p->d_crow + prefix[i];
+        e.err = h->status_dev + 3;
+        e.m = h->m;
+        e.tiles = h->tiles;
+    }
+    // pageable sources are staged before the calls return
+    SPMV_CUDA_TRY(cudaMemcpyAsync(p->d_prefix, prefix.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+    SPMV_CUDA_TRY(cudaMemcpyAsync(p->d_mats, p->h_mats.data(), sizeof(MatEntry) * count, cudaMemcpyHostToDevice, s));
+    return enqueue_plan(p, s);
+}
+
 spmv_status mul_batch(int count, spmv_matrix *const *hs, int k, const void *const *X, void *const *Y,
                       spmv_dtype vdt, uint32_t acc, cudaStream_t s) {
     if (count == 0) return SPMV_OK;

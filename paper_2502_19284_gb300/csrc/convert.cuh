@@ -65,5 +65,12 @@ spmv_status mul_csr_merge_noalloc(int64_t m, int64_t n, int64_t nnz, const int32
 spmv_status mul_batch(int count, spmv_matrix *const *hs, int k, const void *const *X, void *const *Y,
                       spmv_dtype vdt, uint32_t acc, cudaStream_t s);
 void forget_batch_plans(const spmv_matrix *h);
+// Uncaptured batch on caller-owned scratch (one BatchSlot per concurrent stream).
+struct BatchSlot;
+BatchSlot *batch_slot_new();
+void batch_slot_free(BatchSlot *b);
+int64_t batch_scratch_bytes(int count, spmv_matrix *const *hs, int k);
+spmv_status batch_direct(BatchSlot *b, int count, spmv_matrix *const *hs, int k, const void *const *X,
+                         void *const *Y, spmv_dtype vdt, uint32_t acc, cudaStream_t s);
 
 }  // namespace spmv

@@ -188,3 +188,18 @@ def round_bf16_bits(values: np.ndarray) -> np.ndarray:
 
 def bf16_bits_to_float64(bits: np.ndarray) -> np.ndarray:
     return (np.asarray(bits, np.uint16).astype(np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)
+
+
+def poisson_arrivals(rate: float, n: int, seed: int = 0) -> np.ndarray:
+    """n arrival times (seconds from 0) of a Poisson process of `rate` per second."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.cumsum(rng.exponential(1.0 / rate, size=n))
+
+
+def request_mix(n: int, n_matrices: int, pagerank_frac: float = 0.2, seed: int = 0):
+    """(kind, matrix) per request: kind 1 (PageRank) with probability pagerank_frac, else 0
+    (SpMV); matrices uniform over range(n_matrices)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    kind = (rng.random(n) < pagerank_frac).astype(np.int32)
+    mat = rng.integers(0, n_matrices, size=n).astype(np.int32)
+    return kind, mat

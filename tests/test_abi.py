@@ -50,6 +50,20 @@ def test_status_strings_and_argument_checks_without_gpu():
     assert lib.spmv_mul(None, None, None, 0, 0, None) == sp.SPMV_ERR_INVALID_ARG
     assert lib.spmv_mul_batch(1, None, 1, None, None, 0, 0, None) == sp.SPMV_ERR_INVALID_ARG
     assert lib.spmv_destroy(None) == sp.SPMV_OK
+    # serving: option limits are checked before any device call
+    out = ctypes.c_void_p()
+    for o in [(0, 4, 8), (1 << 30, 0, 8), (1 << 30, 65, 8), (1 << 30, 4, 0), (1 << 30, 4, 2000)]:
+        opts = sp.spmv_server_opts(*o)
+        assert lib.spmv_server_create(ctypes.byref(opts), ctypes.byref(out)) == sp.SPMV_ERR_INVALID_ARG
+    assert lib.spmv_server_add(None, None, None) == sp.SPMV_ERR_INVALID_ARG
+    assert lib.spmv_server_destroy(None) == sp.SPMV_OK
+
+
+def test_server_struct_layouts_match_header():
+    import paper_2502_19284_gb300 as sp
+    assert ctypes.sizeof(sp.spmv_request) == 48 and sp.spmv_request.damping.offset == 24
+    assert sp.spmv_request.x.offset == 32 and sp.spmv_request.y.offset == 40
+    assert ctypes.sizeof(sp.spmv_server_opts) == 16 and ctypes.sizeof(sp.spmv_server_stats_t) == 64
 
 
 def test_package_fails_loudly_without_library(tmp_path):

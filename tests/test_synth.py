@@ -54,3 +54,14 @@ def test_round_bf16_bits_matches_oracle_rounding():
     bits = synth.round_bf16_bits(v)
     ref = np.array([oracle.round_bf16_bits(x) for x in v], np.uint16)
     np.testing.assert_array_equal(bits, ref)
+
+
+def test_poisson_arrivals_and_mix():
+    t = synth.poisson_arrivals(1000.0, 20000, seed=3)
+    assert np.all(np.diff(t) >= 0)
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert abs(gaps.mean() - 1e-3) < 3e-5                    # mean inter-arrival 1/rate
+    assert abs(gaps.std() - 1e-3) < 5e-5                     # exponential: sd = mean
+    assert np.array_equal(t, synth.poisson_arrivals(1000.0, 20000, seed=3))
+    kind, mat = synth.request_mix(20000, 7, 0.2, seed=3)
+    assert abs(kind.mean() - 0.2) < 0.02 and set(np.unique(mat)) == set(range(7))
