@@ -194,6 +194,114 @@ def cpu_baseline(scale, rows, cols, vals, x, frac, reps=1):
     return total / best / 1e9, desc, best
 
 
+# ------------------------------------------------------------------ serving leg
+
+SERVE = dict(n_matrices=16, scales=(14, 20), edge_factor=16, budget=150 << 30, slots=8, max_batch=64,
+             rates=(2000.0, 10000.0), requests=2000, pagerank_frac=0.2, pagerank_iters=20, damping=0.85)
+
+
+def serving_leg(sp, torch, dev, synth, np):
+    """Poisson arrivals of SpMV (FP32 values and vectors) and 20-iteration PageRank requests
+    on a resident set of R-MAT matrices, through the serving loop, against the same trace on
+    the plain one-at-a-time FP64 path (FP64 copies of the matrices, one synchronous call per
+    request in arrival order).  Latency = completion - arrival."""
+    cfg = SERVE
+    rng = np.random.Generator(np.random.PCG64(77))
+    scales = rng.integers(cfg["scales"][0], cfg["scales"][1] + 1, size=cfg["n_matrices"])
+    h32, h64, xs, ys, prs, x64s, y64s, pr64s, ns = [], [], [], [], [], [], [], [], []
+    for i, sc in enumerate(scales):
+        n = 1 << int(sc)
+        r, c = synth.rmat(int(sc), cfg["edge_factor"], seed=1000 + i)
+        v = synth.values(r, c, seed=1000 + i)
+        rd, cd = torch.from_numpy(r).to(dev), torch.from_numpy(c).to(dev)
+        a = sp.spmv_create_coo(n, n, rd, cd, torch.from_numpy(v.astype(np.float32)).to(dev))
+        sp.spmv_convert(a, "merge")
+        b = sp.spmv_create_coo(n, n, rd, cd, torch.from_numpy(v).to(dev))
+        sp.spmv_convert(b, "auto")
+        h32.append(a)
+        h64.append(b)
+        x = synth.vector(n, seed=2000 + i)
+        xs.append(torch.from_numpy(x.astype(np.float32)).pin_memory())
+        ys.append(torch.empty(n, dtype=torch.float32).pin_memory())
+        prs.append(torch.empty(n, dtype=torch.float64).pin_memory())
+        x64s.append(torch.from_numpy(x).pin_memory())
+        y64s.append(torch.empty(n, dtype=torch.float64).pin_memory())
+        pr64s.append(torch.empty(n, dtype=torch.float64, device=dev))
+        ns.append(n)
+    torch.cuda.synchronize()
+    srv = sp.Server(cfg["budget"], slots=cfg["slots"], max_batch=cfg["max_batch"])
+    ids = [srv.add(h) for h in h32]
+    dx = [torch.empty(n, dtype=torch.float64, device=dev) for n in ns]
+    dy = [torch.empty(n, dtype=torch.float64, device=dev) for n in ns]
+    out = {"config": {"matrices": int(cfg["n_matrices"]), "scales": [int(v) for v in scales],
+                      "edge_factor": cfg["edge_factor"], "values": "f32 (served) / f64 (plain)",
+                      "mix": f"{1 - cfg['pagerank_frac']:.0%} SpMV / {cfg['pagerank_frac']:.0%} PageRank-"
+                             f"{cfg['pagerank_iters']}", "budget_bytes": cfg["budget"], "slots": cfg["slots"],
+                      "max_batch": cfg["max_batch"], "requests_per_rate": cfg["requests"],
+                      "resident_bytes": srv.stats()["resident_bytes"]},
+           "rates": []}
+    # accuracy of the served FP32 products against the FP64 path (largest matrix)
+    big = int(np.argmax(ns))
+    t = srv.submit(sp.Server.request(sp.SPMV_REQ_SPMV, ids[big], ys[big], x=xs[big]))
+    srv.wait(t)
+    dx[big].copy_(x64s[big])
+    sp.spmv_mul(h64[big], dx[big], dy[big])
+    a_ = ys[big].numpy().astype(np.float64)
+    b_ = dy[big].cpu().numpy()
+    absb = np.abs(b_)
+    out["accuracy"] = {"max_abs_err_vs_fp64": float(np.max(np.abs(a_ - b_))),
+                       "max_rel_err_vs_fp64_where_abs_gt_1e-3": float(np.max(np.abs(a_ - b_)[absb > 1e-3] / absb[absb > 1e-3]))
+                       if np.any(absb > 1e-3) else None,
+                       "matrix_scale": int(scales[big])}
+    for rate in cfg["rates"]:
+        N = cfg["requests"]
+        kind, mat = synth.request_mix(N, len(ns), cfg["pagerank_frac"], seed=int(rate))
+        arr = synth.poisson_arrivals(rate, N, seed=int(rate))
+        reqs = []
+        for k, m in zip(kind, mat):
+            if k == 1:
+                reqs.append(sp.Server.request(sp.SPMV_REQ_PAGERANK, ids[m], prs[m], iters=cfg["pagerank_iters"],
+                                              damping=cfg["damping"]))
+            else:
+                reqs.append(sp.Server.request(sp.SPMV_REQ_SPMV, ids[m], ys[m], x=xs[m]))
+        st0 = srv.stats()
+        t0 = time.perf_counter()
+        lat = srv.replay(reqs, arr)
+        wall = time.perf_counter() - t0
+        st1 = srv.stats()
+        served = {"p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                  "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
+                  "throughput_rps": round(N / float(np.max(arr + lat)), 1),
+                  "launches": st1["launches"] - st0["launches"],
+                  "batched_spmv": st1["batched_requests"] - st0["batched_requests"],
+                  "deferred": st1["deferred"] - st0["deferred"], "wall_s": round(wall, 3)}
+        # plain path: one request at a time, FP64, synchronous, in arrival order
+        plat = np.empty(N)
+        start = time.perf_counter() + 1e-3
+        stream = torch.cuda.current_stream()
+        for i, (k, m) in enumerate(zip(kind, mat)):
+            ta = start + arr[i]
+            while time.perf_counter() < ta:
+                pass
+            if k == 1:
+                sp.spmv_pagerank(h64[m], pr64s[m], cfg["damping"], cfg["pagerank_iters"])
+                prs[m].copy_(pr64s[m], non_blocking=True)
+            else:
+                dx[m].copy_(x64s[m], non_blocking=True)
+                sp.spmv_mul(h64[m], dx[m], dy[m])
+                y64s[m].copy_(dy[m], non_blocking=True)
+            stream.synchronize()
+            plat[i] = time.perf_counter() - ta
+        plain = {"p50_ms": round(float(np.percentile(plat, 50)) * 1e3, 3),
+                 "p99_ms": round(float(np.percentile(plat, 99)) * 1e3, 3),
+                 "throughput_rps": round(N / float(np.max(arr + plat)), 1)}
+        out["rates"].append({"rate_rps": rate, "served": served, "plain_fp64": plain})
+    srv.close()
+    for h in h32 + h64:
+        sp.spmv_destroy(h)
+    return out
+
+
 # ------------------------------------------------------------------ main
 
 def main():
@@ -206,6 +314,7 @@ def main():
     ap.add_argument("--cpu-frac", type=float, default=1.0 / 4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -400,6 +509,11 @@ def main():
                "h2d_bytes_per_step": nnz_in * 16 + n * 8, "d2h_bytes_per_step": 3 * m * 8,
                "ms_per_step": round(ms2, 3)}
 
+    # ---- serving leg (rank 0 of each replica runs its own)
+    serving = None
+    if not args.no_serving:
+        serving = serving_leg(sp, torch, dev, synth, np)
+
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -434,6 +548,7 @@ def main():
         "roofline_spmv_merge": roof_spmv,
         "kernel_shares": shares,
         "break_even": break_even,
+        "serving": serving,
         "cpu_baseline": cpu,
         "wall_s_timed": round(wall_s, 3),
     }
