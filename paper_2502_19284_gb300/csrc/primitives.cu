@@ -148,6 +148,10 @@ constexpr int RS_WARPS = RS_BLOCK / 32;
 constexpr int RADIX = 256;
 static_assert(RS_BLOCK == RADIX, "one thread per digit in the per-tile digit work");
 
+#ifndef RS_MATCH_ANY
+#define RS_MATCH_ANY 1   // rank with __match_any_sync (else with one ballot per digit bit)
+#endif
+#if !RS_MATCH_ANY
 // Lanes of the warp holding the same 8-bit digit as this lane (ballot per digit bit).
 __device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid) {
     uint32_t peers = __ballot_sync(0xffffffffu, valid);
@@ -158,6 +162,7 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid) {
     }
     return peers;
 }
+#endif
 
 // hist[d * ntiles + tile] = count of digit d in tile (same tiling as k_rs_scatter)
 __global__ __launch_bounds__(RS_BLOCK) void k_rs_count(const uint64_t *__restrict__ keys, int64_t n, int shift,
@@ -185,24 +190,44 @@ __global__ __launch_bounds__(RS_BLOCK) void k_rs_count(const uint64_t *__restric
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = t;
 }
 
-// Stable scatter of one tile at the offsets of the scanned digit-major counts.
+// Stable scatter of one tile at the offsets of the scanned digit-major counts.  The tile's
+// payloads are brought into shared memory by one bulk copy issued at the start (they are
+// not needed until the keys are ranked), the keys are loaded into registers and ranked per
+// warp in input order, keys and payloads are placed in digit order in shared memory, and
+// every digit run is written out contiguously.
+constexpr long long RS_SPIN_LIMIT = 1ll << 22;
+
+__device__ __forceinline__ uint32_t rs_smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
 __global__ __launch_bounds__(RS_BLOCK, 3) void k_rs_scatter(const uint64_t *__restrict__ keys_in,
                                                             const uint32_t *__restrict__ vals_in,
                                                             uint64_t *__restrict__ keys_out,
                                                             uint32_t *__restrict__ vals_out, int64_t n, int shift,
                                                             uint32_t mask, const uint32_t *__restrict__ offsets,
-                                                            int64_t ntiles) {
+                                                            int64_t ntiles, uint32_t *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *s_keys = (uint64_t *)smem_raw;
     uint32_t *s_vals = (uint32_t *)(s_keys + RS_TILE);
-    uint32_t *s_wcnt = s_vals + RS_TILE;
+    uint32_t *s_vin = s_vals + RS_TILE;
+    uint32_t *s_wcnt = s_vin + RS_TILE;
     uint32_t *s_dstart = s_wcnt + RS_WARPS * RADIX;
     uint32_t *s_gbase = s_dstart + RADIX;
+    uint64_t *s_bar = (uint64_t *)(s_gbase + RADIX);
     __shared__ uint32_t s_wt[RS_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
     const int64_t tile_base = (int64_t)blockIdx.x * RS_TILE;
     const int tile_n = (int)min((int64_t)RS_TILE, n - tile_base);
+    const bool bulk = tile_n == RS_TILE;   // a full tile: 16 KB of payloads, 16-byte aligned
+    if (threadIdx.x == 0 && bulk) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(rs_smem_u32(s_bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(rs_smem_u32(s_bar)),
+                     "r"((uint32_t)RS_TILE * 4u) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     :: "r"(rs_smem_u32(s_vin)), "l"(vals_in + tile_base), "r"((uint32_t)RS_TILE * 4u),
+                        "r"(rs_smem_u32(s_bar)) : "memory");
+    }
     const int64_t wbase = tile_base + (int64_t)warp * (32 * RS_IPT);
     for (int d = lane; d < RADIX; d += 32) s_wcnt[warp * RADIX + d] = 0;
     const uint32_t gofs = offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x];
@@ -218,7 +243,11 @@ __global__ __launch_bounds__(RS_BLOCK, 3) void k_rs_scatter(const uint64_t *__re
     for (int j = 0; j < RS_IPT; ++j) {
         const bool valid = wbase + j * 32 + lane < n;
         const uint32_t d = (uint32_t)(k[j] >> shift) & mask;
+#if RS_MATCH_ANY
+        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0x100u + (uint32_t)lane);
+#else
         const uint32_t peers = digit_peers(d, valid);
+#endif
         const uint32_t base = valid ? s_wcnt[warp * RADIX + d] : 0u;
         __syncwarp();
         if (valid && (peers & lt_mask) == 0) s_wcnt[warp * RADIX + d] = base + __popc(peers);
@@ -248,6 +277,16 @@ __global__ __launch_bounds__(RS_BLOCK, 3) void k_rs_scatter(const uint64_t *__re
     s_dstart[d] = dstart;
     s_gbase[d] = gofs - dstart;
     __syncthreads();
+    if (bulk) {   // the payloads have landed (bounded wait)
+        uint32_t done = 0;
+        for (long long it = 0; it < RS_SPIN_LIMIT && !done; ++it)
+            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                         : "=r"(done) : "r"(rs_smem_u32(s_bar)) : "memory");
+        if (!__syncthreads_and(done)) {
+            if (threadIdx.x == 0) atomicOr(err, 4u);
+            return;
+        }
+    }
 #pragma unroll
     for (int j = 0; j < RS_IPT; ++j) {
         const int64_t i = wbase + j * 32 + lane;
@@ -255,7 +294,7 @@ __global__ __launch_bounds__(RS_BLOCK, 3) void k_rs_scatter(const uint64_t *__re
             const uint32_t dj = dr[j] >> 16;
             const uint32_t p = s_dstart[dj] + s_wcnt[warp * RADIX + dj] + (dr[j] & 0xFFFFu);
             s_keys[p] = k[j];
-            s_vals[p] = vals_in[i];
+            s_vals[p] = bulk ? s_vin[i - tile_base] : vals_in[i];
         }
     }
     __syncthreads();
@@ -268,7 +307,7 @@ __global__ __launch_bounds__(RS_BLOCK, 3) void k_rs_scatter(const uint64_t *__re
     }
 }
 
-constexpr size_t RS_SMEM = (size_t)RS_TILE * 12 + (size_t)RS_WARPS * RADIX * 4 + 2 * RADIX * 4;
+constexpr size_t RS_SMEM = (size_t)RS_TILE * 16 + (size_t)RS_WARPS * RADIX * 4 + 2 * RADIX * 4 + 16;
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
@@ -276,11 +315,11 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 size_t radix_temp_bytes(int64_t n) {
     const int64_t ntiles = cdiv(std::max<int64_t>(n, 1), RS_TILE);
-    return align256((size_t)ntiles * RADIX * 4) + scan_temp_bytes((int64_t)ntiles * RADIX);
+    return align256((size_t)ntiles * RADIX * 4) + align256(scan_temp_bytes((int64_t)ntiles * RADIX)) + 256;
 }
 
 spmv_status radix_sort_pairs(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
-                             int begin_bit, int end_bit, void *temp, cudaStream_t s, bool *in_alt) {
+                             int begin_bit, int end_bit, void *temp, cudaStream_t s, bool *in_alt, uint32_t *err) {
     *in_alt = false;
     if (n <= 1 || end_bit <= begin_bit) return SPMV_OK;
     static bool attr_set = false;
@@ -291,6 +330,8 @@ spmv_status radix_sort_pairs(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals,
     const int64_t ntiles = cdiv(n, RS_TILE);
     uint32_t *cnt = (uint32_t *)temp;
     void *scan_tmp = (char *)temp + align256((size_t)ntiles * RADIX * 4);
+    if (!err)   // no status word of the caller: the last word of the scratch takes the flag
+        err = (uint32_t *)((char *)scan_tmp + align256(scan_temp_bytes((int64_t)ntiles * RADIX)));
     uint64_t *ka = keys, *kb = keys_alt;
     uint32_t *va = vals, *vb = vals_alt;
     for (int shift = begin_bit; shift < end_bit; shift += 8) {
@@ -299,7 +340,8 @@ spmv_status radix_sort_pairs(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals,
         SPMV_LAUNCH_CHECK("radix count");
         SPMV_TRY(exclusive_scan_u32(cnt, cnt, (int64_t)RADIX * ntiles, scan_tmp, s));
         SPMV_LAUNCH("k_rs_scatter", s,
-                    (k_rs_scatter<<<(unsigned)ntiles, RS_BLOCK, RS_SMEM, s>>>(ka, va, kb, vb, n, shift, mask, cnt, ntiles)));
+                    (k_rs_scatter<<<(unsigned)ntiles, RS_BLOCK, RS_SMEM, s>>>(ka, va, kb, vb, n, shift, mask, cnt, ntiles,
+                                                                               err)));
         SPMV_LAUNCH_CHECK("radix scatter");
         std::swap(ka, kb);
         std::swap(va, vb);
