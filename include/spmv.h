@@ -156,7 +156,9 @@ spmv_status spmv_mul(spmv_handle h, const void *x, void *y, spmv_dtype vec_dt, u
  * alignment of X/Y) is seen, and replayed after that; only the table of X/Y pointers is
  * copied per call.  Per column, the result is bitwise the one spmv_mul gives for the
  * same accumulation on the merge path (FP64 vectors accumulate in native FP64 here, so
- * SPMV_ACC_DEFAULT matches spmv_mul with SPMV_ACC_F64).  Calls with the same batch shape share scratch
+ * SPMV_ACC_DEFAULT matches spmv_mul with SPMV_ACC_F64).  With k = 1, a handle whose active
+ * format is row-split or blocked (spmv_convert, or chosen by spmv_tune) runs that format's
+ * product after the persistent launch instead, with spmv_mul's result.  Calls with the same batch shape share scratch
  * and must be ordered.  Not capturable into a caller's graph (the pointer table is
  * uploaded from pageable memory).  A handle's plans are dropped when it is converted
  * again or destroyed.
@@ -166,6 +168,30 @@ spmv_status spmv_mul_batch(int count, const spmv_handle *hs, int k, const void *
 
 /* spmv_destroy -- free every device buffer of the handle (synchronises with its stream). */
 spmv_status spmv_destroy(spmv_handle h);
+
+/*
+ * spmv_tune -- autotuner: time one product y = A x in each candidate storage format of the
+ * handle (Section 6.1 finds that the best method depends on the matrix; here it is
+ * measured), and make the fastest the active format.  Candidates: row-split CRS and
+ * merge-path CRS (built if missing, both cheap), and the Hilbert-blocked format if it is
+ * already built or flags has SPMV_TUNE_HB (its conversion costs far more than a product).
+ *   vec_dt, accum   the product to time (as in spmv_mul).
+ *   out             may be NULL; receives the chosen format and the median time of one
+ *                   product per format in milliseconds (-1 where not tried).
+ * Allocates scratch x and y of the handle's size, runs 2 + 2*reps products per candidate
+ * on `stream` and synchronises it.  spmv_mul then uses the chosen format; spmv_mul_batch
+ * with k = 1 runs a handle whose active format is row-split or blocked with that product,
+ * inside the same captured graph as the merge-path matrices of the batch.
+ */
+enum { SPMV_TUNE_HB = 0x1 };
+typedef struct {
+    int32_t chosen;     /* SPMV_FMT_CSR_ROWSPLIT, SPMV_FMT_CSR_MERGE or SPMV_FMT_HB */
+    int32_t reps;       /* timed products per candidate */
+    float ms[3];        /* median ms per product: [ROWSPLIT, MERGE, HB], -1 if not tried */
+    int32_t pad_;
+} spmv_tune_result;
+spmv_status spmv_tune(spmv_handle h, spmv_dtype vec_dt, uint32_t accum, uint32_t flags, spmv_tune_result *out,
+                      void *stream);
 
 /* ---------------------------------------------------------------- inspection */
 
@@ -245,9 +271,9 @@ spmv_status spmv_pagerank(spmv_handle h, double damping, int iters, double *x, v
  * them as one batched launch (the product of spmv_mul_batch, without capture); a PageRank
  * request runs alone, at most one per matrix at a time.  Slots run concurrently on their
  * own CUDA streams, so requests arriving while others run start as soon as a slot and
- * memory free up.  Every SpMV result is bitwise the spmv_mul_batch result (and so the
- * spmv_mul result with the same accumulation on the merge path; FP64 vectors accumulate in
- * native FP64), and every PageRank result the spmv_pagerank result, whatever else is in
+ * memory free up.  Every SpMV result is bitwise the spmv_mul result with the same
+ * accumulation on the merge path (FP64 vectors accumulate in native FP64, as with
+ * SPMV_ACC_F64), and every PageRank result the spmv_pagerank result, whatever else is in
  * flight.
  *
  * Memory: the budget covers the resident matrices (their spmv_info bytes at spmv_server_add,

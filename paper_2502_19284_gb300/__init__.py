@@ -48,6 +48,13 @@ class spmv_info_t(ctypes.Structure):
                 ("pad_", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
 
 
+class spmv_tune_result(ctypes.Structure):
+    _fields_ = [("chosen", ctypes.c_int32), ("reps", ctypes.c_int32), ("ms", ctypes.c_float * 3), ("pad_", ctypes.c_int32)]
+
+
+SPMV_TUNE_HB = 0x1
+
+
 class spmv_server_opts(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int32), ("max_batch", ctypes.c_int32)]
 
@@ -80,6 +87,7 @@ _SIG = {
     "spmv_hilbert_keys": [_i32, _i64, _p, _p, _p, _p],
     "spmv_mul_csr_merge_noalloc": [_i64, _i64, _i64, _p, _p, _p, _p, _p, _p],
     "spmv_pagerank": [_p, ctypes.c_double, _i32, _p, _p],
+    "spmv_tune": [_p, _i32, _u32, _u32, ctypes.POINTER(spmv_tune_result), _p],
     "spmv_server_create": [ctypes.POINTER(spmv_server_opts), ctypes.POINTER(_p)],
     "spmv_server_add": [_p, _p, ctypes.POINTER(ctypes.c_int32)],
     "spmv_server_submit": [_p, ctypes.POINTER(spmv_request), ctypes.POINTER(ctypes.c_int64)],
@@ -307,6 +315,15 @@ def _host_values(dt, nnz):
     if dt == SPMV_BF16:
         return np.empty(max(nnz, 1), np.uint16)
     return None
+
+
+def spmv_tune(h: Handle, vec_dtype="f64", accum=SPMV_ACC_DEFAULT, hb=False, stream=None) -> dict:
+    """Time one product per storage format and make the fastest the handle's active format."""
+    r = spmv_tune_result()
+    vdt = SPMV_F64 if vec_dtype in ("f64", SPMV_F64) else SPMV_F32
+    _check(_lib.spmv_tune(h.ptr, vdt, accum, SPMV_TUNE_HB if hb else 0, ctypes.byref(r), _stream(stream)), "spmv_tune")
+    names = {SPMV_FMT_CSR_ROWSPLIT: "rowsplit", SPMV_FMT_CSR_MERGE: "merge", SPMV_FMT_HB: "hb"}
+    return {"chosen": names[r.chosen], "ms": dict(zip(["rowsplit", "merge", "hb"], [float(v) for v in r.ms]))}
 
 
 class Server:

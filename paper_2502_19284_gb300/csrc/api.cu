@@ -393,6 +393,78 @@ spmv_status spmv_mul(spmv_handle h, const void *x, void *y, spmv_dtype vec_dt, u
     return SPMV_ERR_INVALID_ARG;
 }
 
+spmv_status spmv_tune(spmv_handle h, spmv_dtype vec_dt, uint32_t accum, uint32_t flags, spmv_tune_result *out,
+                      void *stream) {
+    g_err.clear();
+    SPMV_TRY(check_handle(h));
+    if ((vec_dt != SPMV_F64 && vec_dt != SPMV_F32) || accum > SPMV_ACC_COMPENSATED || (flags & ~SPMV_TUNE_HB)) {
+        set_error("spmv_tune: bad vector dtype, accumulation or flags");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    forget_batch_plans(h);
+    if (!h->has_csr) SPMV_TRY(build_csr(h, s));
+    if (!h->has_bins) SPMV_TRY(build_bins(h, s));
+    if (!h->has_merge) SPMV_TRY(build_merge(h, MERGE_WARP_ITEMS, s));
+    if (h->dt == SPMV_F64) SPMV_TRY(build_df(h, s));
+    if ((flags & SPMV_TUNE_HB) && !h->has_hb)
+        SPMV_TRY(build_hb(h, default_log2_beta(h->n, h->dt == SPMV_F64 ? 8 : 4), SPMV_INNER_HILBERT, s));
+    spmv_tune_result r;
+    r.reps = 5;
+    r.pad_ = 0;
+    for (float &v : r.ms) v = -1.f;
+    const int es = vec_dt == SPMV_F64 ? 8 : 4;
+    DevBuf x(s), y(s);
+    SPMV_TRY(x.alloc((size_t)std::max<int64_t>(h->n, 1) * es, "tune x"));
+    SPMV_TRY(y.alloc((size_t)std::max<int64_t>(h->m, 1) * es, "tune y"));
+    SPMV_CUDA_TRY(cudaMemsetAsync(x.p, 0, (size_t)std::max<int64_t>(h->n, 1) * es, s));
+    const int32_t fmts[3] = {SPMV_FMT_CSR_ROWSPLIT, SPMV_FMT_CSR_MERGE, SPMV_FMT_HB};
+    cudaEvent_t e0, e1;
+    SPMV_CUDA_TRY(cudaEventCreate(&e0));
+    SPMV_CUDA_TRY(cudaEventCreate(&e1));
+    const int32_t keep = h->format;
+    spmv_status st = SPMV_OK;
+    int best = -1;
+    for (int f = 0; f < 3 && st == SPMV_OK; ++f) {
+        if (fmts[f] == SPMV_FMT_HB && !h->has_hb) continue;
+        h->format = fmts[f];
+        std::vector<float> t;
+        for (int rep = 0; rep < 2 + 2 * r.reps && st == SPMV_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            st = spmv_mul(h, x.p, y.p, vec_dt, accum, s);
+            cudaEventRecord(e1, s);
+            if (st == SPMV_ERR_UNSUPPORTED) break;   // this format lacks the product: skip it
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = cuda_status(cudaGetLastError(), "spmv_tune");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep >= 2) t.push_back(ms);
+        }
+        if (st == SPMV_ERR_UNSUPPORTED) {
+            st = SPMV_OK;
+            g_err.clear();
+            continue;
+        }
+        if (st != SPMV_OK || t.empty()) break;
+        std::sort(t.begin(), t.end());
+        r.ms[f] = t[t.size() / 2];
+        if (best < 0 || r.ms[f] < r.ms[best]) best = f;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SPMV_OK || best < 0) {
+        h->format = keep;
+        if (st == SPMV_OK) {
+            set_error("spmv_tune: no format supports this product");
+            st = SPMV_ERR_UNSUPPORTED;
+        }
+        return st;
+    }
+    h->format = fmts[best];
+    r.chosen = fmts[best];
+    if (out) *out = r;
+    return SPMV_OK;
+}
+
 spmv_status spmv_mul_batch(int count, const spmv_handle *hs, int k, const void *const *X, void *const *Y,
                            spmv_dtype vec_dt, uint32_t accum, void *stream) {
     if (count < 0 || (count > 0 && (!hs || !X || !Y)) || k < 1 || k > 16) {
@@ -416,6 +488,33 @@ spmv_status spmv_mul_batch(int count, const spmv_handle *hs, int k, const void *
         // the batch runs on the merge-path tiles; build them for handles converted to
         // another format
         if (!hs[i]->has_merge) SPMV_TRY(build_merge(hs[i], MERGE_WARP_ITEMS, (cudaStream_t)stream));
+    }
+    // k = 1: a handle whose active format (spmv_convert or spmv_tune) is row-split or blocked
+    // runs its own product; the others share the persistent merge-path launch
+    if (k == 1) {
+        std::vector<spmv_matrix *> mh;
+        std::vector<const void *> mx;
+        std::vector<void *> my;
+        std::vector<int> own;
+        for (int i = 0; i < count; ++i) {
+            if (hs[i]->format == SPMV_FMT_CSR_ROWSPLIT || hs[i]->format == SPMV_FMT_HB) {
+                own.push_back(i);
+            } else {
+                mh.push_back(hs[i]);
+                mx.push_back(X[i]);
+                my.push_back(Y[i]);
+            }
+        }
+        if (!own.empty()) {
+            cudaStream_t s = (cudaStream_t)stream;
+            if (!mh.empty()) SPMV_TRY(mul_batch((int)mh.size(), mh.data(), 1, mx.data(), my.data(), vec_dt, accum, s));
+            for (int i : own) {
+                if (hs[i]->m == 0) continue;
+                if (hs[i]->format == SPMV_FMT_HB) SPMV_TRY(mul_hb(hs[i], X[i], Y[i], vec_dt, accum, s));
+                else SPMV_TRY(mul_rowsplit(hs[i], X[i], Y[i], vec_dt, accum, s));
+            }
+            return SPMV_OK;
+        }
     }
     return mul_batch(count, (spmv_matrix *const *)hs, k, X, Y, vec_dt, accum, (cudaStream_t)stream);
 }

@@ -206,3 +206,48 @@ def test_batch_errors(sp):
     sp.spmv_mul_batch([], [], [], k=2)                           # empty batch is a no-op
     for h in hs + [hp]:
         sp.spmv_destroy(h)
+
+
+def test_tune_picks_a_measured_format(sp):
+    scale = 14
+    n = 1 << scale
+    r, c = synth.rmat(scale, 16, seed=90)
+    v = synth.values(r, c, 91)
+    h = sp.spmv_create_coo(n, n, torch.from_numpy(r).to(DEV), torch.from_numpy(c).to(DEV), torch.from_numpy(v).to(DEV))
+    sp.spmv_convert(h, "rowsplit")
+    res = sp.spmv_tune(h, "f64", hb=True)
+    ms = res["ms"]
+    assert all(t > 0 for t in ms.values()), ms
+    assert res["chosen"] == min(ms, key=ms.get)
+    assert sp.spmv_info(h)["format"] == sp.FORMATS[res["chosen"]]
+    rp, co, vo = oracle.coo_to_csr(n, n, r, c, v)
+    x = synth.vector(n, 92)
+    y = torch.empty(n, dtype=torch.float64, device=DEV)
+    sp.spmv_mul(h, torch.from_numpy(x).to(DEV), y)
+    torch.cuda.synchronize()
+    assert (np.abs(y.cpu().numpy() - oracle.csr_spmv(rp, co, vo, x)) <= TOL * oracle.csr_absmul(rp, co, vo, x)).all()
+    sp.spmv_destroy(h)
+
+
+def test_batch_k1_runs_each_handles_active_format(sp):
+    """k = 1: row-split and blocked handles run their own product (result = spmv_mul), the
+    merge-path ones share the persistent launch."""
+    mats = build(sp)
+    sp.spmv_convert(mats[0][0], "rowsplit")
+    sp.spmv_convert(mats[1][0], "hb")
+    Xs = [rhs(n, 1, 60 + i) for i, (_, m, n, *_r) in enumerate(mats)]
+    Xd = [torch.from_numpy(X).to(DEV) for X in Xs]
+    Yd = [torch.full((m, 1), float("nan"), dtype=torch.float64, device=DEV) for (_, m, *_r) in mats]
+    sp.spmv_mul_batch([t[0] for t in mats], Xd, Yd, k=1, accum=sp.SPMV_ACC_F64)
+    torch.cuda.synchronize()
+    for i, ((h, m, n, rp, co, vo), X, Xt, Yt) in enumerate(zip(mats, Xs, Xd, Yd)):
+        y1 = torch.empty(m, dtype=torch.float64, device=DEV)
+        sp.spmv_mul(h, Xt[:, 0].contiguous(), y1, accum=sp.SPMV_ACC_F64)
+        torch.cuda.synchronize()
+        got = Yt.cpu().numpy()[:, 0]
+        if i != 1:   # the blocked product adds with atomics: equal within tolerance, not bitwise
+            assert np.array_equal(got, y1.cpu().numpy()), i
+        scale = oracle.csr_absmul(rp, co, vo, X[:, 0])
+        assert (np.abs(got - oracle.csr_spmv(rp, co, vo, X[:, 0])) <= TOL * scale).all(), i
+    for t in mats:
+        sp.spmv_destroy(t[0])
