@@ -172,6 +172,7 @@ struct spmv_matrix {
     uint32_t *hb_idx = nullptr;
     void *hb_val = nullptr;
     int32_t *blk_ptr = nullptr, *blk_row = nullptr, *blk_col = nullptr;
+    int32_t *hb_chunk_blk = nullptr;  // block of the first nonzero of every HB_CHUNK chunk (+ last block)
 
     // FP64 through double-float arithmetic (df64.cuh): set when every stored value lies in
     // the double-float window; x is split into float pairs per product (scratch below)

@@ -304,6 +304,26 @@ __global__ void k_fix_runs(const int32_t *__restrict__ part_row, int64_t tiles, 
     if (len > FIX_SHORT) fix_long[atomicAdd(nlong, 1ull)] = (int32_t)t;
 }
 
+// Block of the first nonzero of each chunk of HB_CHUNK (largest b with blk_ptr[b] <= e);
+// entry nchunks holds the last block.
+__global__ void k_hb_chunks(const int32_t *__restrict__ blk_ptr, int64_t nblk, int64_t nnz, int64_t nchunks,
+                            int32_t *__restrict__ chunk_blk) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > nchunks) return;
+    if (c == nchunks) {
+        chunk_blk[c] = (int32_t)(nblk - 1);
+        return;
+    }
+    const int64_t e = c * HB_CHUNK;
+    int64_t lo = 0, hi = nblk - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if ((int64_t)blk_ptr[mid] <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    chunk_blk[c] = (int32_t)lo;
+}
+
 // slot arrays from the CRS arrays through the slot -> CRS index map
 __global__ void k_slot_fill(const int32_t *__restrict__ src, int64_t n, const int32_t *__restrict__ col,
                             const double *__restrict__ val, int32_t *__restrict__ scol, float2 *__restrict__ sval2) {
@@ -795,11 +815,20 @@ spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s) {
         SPMV_TRY(bptr.alloc(4, "hb blk_ptr"));
         SPMV_CUDA_TRY(cudaMemsetAsync(bptr.p, 0, 4, s));
     }
+    const int64_t nchunks = (nnz + HB_CHUNK - 1) / HB_CHUNK;
+    DevBuf chk(s);
+    SPMV_TRY(chk.alloc((size_t)(nchunks + 1) * 4, "hb chunk blocks"));
+    if (nnz > 0) {
+        SPMV_LAUNCH("k_hb_chunks", s, (k_hb_chunks<<<grid_for(nchunks + 1), CB, 0, s>>>(bptr.as<int32_t>(), nblk, nnz,
+                                                                                     nchunks, chk.as<int32_t>())));
+        SPMV_LAUNCH_CHECK("hb chunks");
+    }
     if (h->has_hb) {
         dev_free_async(h->hb_idx, s); dev_free_async(h->hb_val, s); dev_free_async(h->blk_ptr, s);
-        dev_free_async(h->blk_row, s); dev_free_async(h->blk_col, s);
-        h->bytes -= h->nnz * (4 + es) + h->nblk * 12 + 4;
+        dev_free_async(h->blk_row, s); dev_free_async(h->blk_col, s); dev_free_async(h->hb_chunk_blk, s);
+        h->bytes -= h->nnz * (4 + es) + h->nblk * 12 + 4 + ((h->nnz + HB_CHUNK - 1) / HB_CHUNK + 1) * 4;
     }
+    h->hb_chunk_blk = (int32_t *)chk.release();
     h->hb_idx = (uint32_t *)idx.release();
     h->hb_val = val.release();
     h->blk_ptr = (int32_t *)bptr.release();
@@ -810,7 +839,7 @@ spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s) {
     h->grid_K = K;
     h->inner = inner;
     h->has_hb = true;
-    h->bytes += nnz * (4 + es) + nblk * 12 + 4;
+    h->bytes += nnz * (4 + es) + nblk * 12 + 4 + (nchunks + 1) * 4;
     return SPMV_OK;
 }
 

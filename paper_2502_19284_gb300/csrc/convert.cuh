@@ -21,6 +21,9 @@ constexpr int MERGE_WARP_ITEMS = 32 * MERGE_WARP_IPT;
 // Lane-slotted tile header: words 0..3 = first row, row count, continuation flag, 0;
 // words 4..35 = the 32 lane descriptors; words 36..39 = 0 (a tile's block is 160 bytes).
 constexpr int SLOT_DESC_WORDS = 40;
+// Blocked product: a CTA takes HB_CHUNK consecutive stored nonzeros; the conversion records
+// the block holding each chunk's first nonzero.
+constexpr int HB_CHUNK = 2048;
 // Carry runs up to FIX_SHORT tiles are summed by one thread, longer ones by a warp.
 constexpr int FIX_SHORT = 16;
 

@@ -1102,39 +1102,40 @@ spmv_status launch_rowsplit(const spmv_matrix *h, const void *x, void *y, cudaSt
 
 // ================================================================ Hilbert blocked
 constexpr int HB_BLOCK = 256;
-constexpr int HB_IPT = 8;
-constexpr int HB_TILE = HB_BLOCK * HB_IPT;
+constexpr int HB_IPT = HB_CHUNK / HB_BLOCK;
 
 __device__ __forceinline__ void atomic_add_out(double *p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void atomic_add_out(float *p, float v) { atomicAdd(p, v); }
 
+// Blocked product (Sections 3.1, 3.2): a CTA takes HB_CHUNK consecutive stored nonzeros (in
+// the stored Hilbert order) and copies the entries of the blocks they fall in (the first
+// block comes from the conversion's chunk table) into shared memory.  Thread t handles
+// nonzeros e0 + j * HB_BLOCK + t (j < 8), so that each warp instruction touches 32
+// consecutive nonzeros, whose rows and columns are close in Hilbert order: all index and
+// value loads are issued first, then the bisections (each starting at the previous block),
+// then the x gathers, then the additions to y (atomics; y is zeroed first).
 template <typename VT, typename XT, typename AT>
-__global__ __launch_bounds__(HB_BLOCK) void k_hb_spmv(int64_t nnz, int64_t nblk, int log2b,
+__global__ __launch_bounds__(HB_BLOCK) void k_hb_spmv(int64_t nnz, int log2b, const int32_t *__restrict__ chunk_blk,
                                                       const int32_t *__restrict__ blk_ptr,
                                                       const int32_t *__restrict__ blk_row,
                                                       const int32_t *__restrict__ blk_col,
                                                       const uint32_t *__restrict__ idx, const VT *__restrict__ val,
                                                       const XT *__restrict__ x, XT *__restrict__ y) {
-    __shared__ int32_t s_ptr[HB_TILE + 1];
-    __shared__ int32_t s_r0[HB_TILE];
-    __shared__ int32_t s_c0[HB_TILE];
-    __shared__ int64_t s_b[2];
-    const int64_t e0 = (int64_t)blockIdx.x * HB_TILE;
-    const int64_t e1 = min(e0 + HB_TILE, nnz);   // exclusive
-    if (threadIdx.x < 2) {
-        // first block with blk_ptr[b] <= e  (largest such b)
-        const int64_t e = threadIdx.x == 0 ? e0 : e1 - 1;
-        int64_t lo = 0, hi = nblk - 1;
-        while (lo < hi) {
-            int64_t mid = (lo + hi + 1) >> 1;
-            if ((int64_t)blk_ptr[mid] <= e) lo = mid;
-            else hi = mid - 1;
-        }
-        s_b[threadIdx.x] = lo;
+    __shared__ int32_t s_ptr[HB_CHUNK + 2];
+    __shared__ int32_t s_r0[HB_CHUNK + 1];
+    __shared__ int32_t s_c0[HB_CHUNK + 1];
+    const int64_t e0 = (int64_t)blockIdx.x * HB_CHUNK;
+    const int64_t e1 = min(e0 + (int64_t)HB_CHUNK, nnz);   // exclusive
+    const int32_t b0 = chunk_blk[blockIdx.x];
+    const int nb = chunk_blk[blockIdx.x + 1] - b0 + 1;     // blocks touching the chunk (maybe one more)
+    uint32_t p[HB_IPT];
+    AT v[HB_IPT];
+#pragma unroll
+    for (int j = 0; j < HB_IPT; ++j) {
+        const int64_t e = e0 + j * HB_BLOCK + threadIdx.x;
+        p[j] = e < e1 ? __ldg(idx + e) : 0u;
+        v[j] = e < e1 ? ld_val<VT, AT>(val, e) : AT(0);
     }
-    __syncthreads();
-    const int64_t b0 = s_b[0];
-    const int nb = (int)(s_b[1] - b0 + 1);   // <= HB_TILE blocks touch a tile
     for (int q = threadIdx.x; q < nb; q += HB_BLOCK) {
         s_ptr[q] = blk_ptr[b0 + q];
         s_r0[q] = blk_row[b0 + q] << log2b;
@@ -1142,30 +1143,34 @@ __global__ __launch_bounds__(HB_BLOCK) void k_hb_spmv(int64_t nnz, int64_t nblk,
     }
     if (threadIdx.x == 0) s_ptr[nb] = blk_ptr[b0 + nb];
     __syncthreads();
-#pragma unroll 2
-    for (int jj = 0; jj < HB_IPT; ++jj) {
-        const int64_t e = e0 + (int64_t)jj * HB_BLOCK + threadIdx.x;
-        if (e >= e1) break;
-        int lo = 0, hi = nb - 1;
+    int64_t rr[HB_IPT], cc[HB_IPT];
+    int lo = 0;
+#pragma unroll
+    for (int j = 0; j < HB_IPT; ++j) {
+        const int64_t e = e0 + j * HB_BLOCK + threadIdx.x;
+        int hi = nb - 1;   // largest b in [lo, nb) with s_ptr[b] <= e
         while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
+            const int mid = (lo + hi + 1) >> 1;
             if ((int64_t)s_ptr[mid] <= e) lo = mid;
             else hi = mid - 1;
         }
-        const uint32_t p = __ldg(idx + e);
-        const int64_t r = (int64_t)s_r0[lo] + (p >> 16);
-        const int64_t c = (int64_t)s_c0[lo] + (p & 0xFFFFu);
-        const AT v = ld_val<VT, AT>(val, e) * ld_x<XT, AT>(x, c);
-        atomic_add_out(y + r, XT(v));
+        rr[j] = (int64_t)s_r0[lo] + (p[j] >> 16);
+        cc[j] = (int64_t)s_c0[lo] + (p[j] & 0xFFFFu);
     }
+    AT xv[HB_IPT];
+#pragma unroll
+    for (int j = 0; j < HB_IPT; ++j) xv[j] = e0 + j * HB_BLOCK + threadIdx.x < e1 ? ld_x<XT, AT>(x, cc[j]) : AT(0);
+#pragma unroll
+    for (int j = 0; j < HB_IPT; ++j)
+        if (e0 + j * HB_BLOCK + threadIdx.x < e1) atomic_add_out(y + rr[j], XT(v[j] * xv[j]));
 }
 
 template <typename VT, typename XT, typename AT>
 spmv_status launch_hb(const spmv_matrix *h, const void *x, void *y, cudaStream_t s) {
     SPMV_CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)h->m * sizeof(XT), s));
     if (h->nnz == 0) return SPMV_OK;
-    SPMV_LAUNCH("k_hb_spmv", s, (k_hb_spmv<VT, XT, AT><<<cdivu(h->nnz, HB_TILE), HB_BLOCK, 0, s>>>(
-        h->nnz, h->nblk, h->log2beta, h->blk_ptr, h->blk_row, h->blk_col, h->hb_idx, (const VT *)h->hb_val,
+    SPMV_LAUNCH("k_hb_spmv", s, (k_hb_spmv<VT, XT, AT><<<cdivu(h->nnz, HB_CHUNK), HB_BLOCK, 0, s>>>(
+        h->nnz, h->log2beta, h->hb_chunk_blk, h->blk_ptr, h->blk_row, h->blk_col, h->hb_idx, (const VT *)h->hb_val,
         (const XT *)x, (XT *)y)));
     SPMV_LAUNCH_CHECK("hb spmv");
     return SPMV_OK;
