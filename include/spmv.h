@@ -88,13 +88,19 @@ typedef struct {
  *   SPMV_ACC_COMPENSATED  FP32 vectors and values: FP32 products and sums whose rounding
  *                     errors are collected in a second FP32 term (FMA product errors,
  *                     TwoSum addition errors); CSR_MERGE only.  The compensation runs on
- *                     every row: on GB300 its extra FP32 operations cost less than the
- *                     memory traffic they overlap, so no row-length threshold is applied.
+ *                     every row and every product.
+ *   SPMV_ACC_SEGMENT  FP32 vectors and values, CSR_MERGE only: FP32 products and sums
+ *                     inside each lane's share of a warp tile (at most 7 path items), the
+ *                     compensated (TwoSum) reduction only where partial sums of a row are
+ *                     joined across lanes and tiles -- i.e. only for rows longer than the
+ *                     in-lane threshold.  Error about 8u (|A||x|)_i + u |y_i| (u = 2^-24),
+ *                     independent of the row length, at close to plain FP32 cost.
  */
 #define SPMV_ACC_DEFAULT 0u
 #define SPMV_ACC_F32 1u
 #define SPMV_ACC_F64 2u
 #define SPMV_ACC_COMPENSATED 3u
+#define SPMV_ACC_SEGMENT 4u
 
 /*
  * spmv_create_coo -- ingest a matrix in triplet (coordinate) form (Section 2, Eq. 1).

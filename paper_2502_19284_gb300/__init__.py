@@ -31,7 +31,7 @@ SPMV_DEVICE_PTRS = 0x1
 SPMV_DUP_SUM = 0x0
 SPMV_DUP_ERROR = 0x2
 SPMV_INNER_HILBERT, SPMV_INNER_ROWMAJOR = 0, 1
-SPMV_ACC_DEFAULT, SPMV_ACC_F32, SPMV_ACC_F64, SPMV_ACC_COMPENSATED = range(4)
+SPMV_ACC_DEFAULT, SPMV_ACC_F32, SPMV_ACC_F64, SPMV_ACC_COMPENSATED, SPMV_ACC_SEGMENT = range(5)
 
 FORMATS = {"rowsplit": SPMV_FMT_CSR_ROWSPLIT, "merge": SPMV_FMT_CSR_MERGE, "hb": SPMV_FMT_HB, "auto": SPMV_FMT_AUTO}
 ELEM_SIZE = {SPMV_F64: 8, SPMV_F32: 4, SPMV_BF16: 2, SPMV_PATTERN: 0}

@@ -378,7 +378,7 @@ spmv_status spmv_mul(spmv_handle h, const void *x, void *y, spmv_dtype vec_dt, u
         set_error("spmv_mul: NULL vector");
         return SPMV_ERR_INVALID_ARG;
     }
-    if (accum > SPMV_ACC_COMPENSATED || (vec_dt != SPMV_F64 && vec_dt != SPMV_F32)) {
+    if (accum > SPMV_ACC_SEGMENT || (vec_dt != SPMV_F64 && vec_dt != SPMV_F32)) {
         set_error("spmv_mul: unknown vector dtype or accumulation mode");
         return SPMV_ERR_INVALID_ARG;
     }
@@ -397,7 +397,7 @@ spmv_status spmv_tune(spmv_handle h, spmv_dtype vec_dt, uint32_t accum, uint32_t
                       void *stream) {
     g_err.clear();
     SPMV_TRY(check_handle(h));
-    if ((vec_dt != SPMV_F64 && vec_dt != SPMV_F32) || accum > SPMV_ACC_COMPENSATED || (flags & ~SPMV_TUNE_HB)) {
+    if ((vec_dt != SPMV_F64 && vec_dt != SPMV_F32) || accum > SPMV_ACC_SEGMENT || (flags & ~SPMV_TUNE_HB)) {
         set_error("spmv_tune: bad vector dtype, accumulation or flags");
         return SPMV_ERR_INVALID_ARG;
     }

@@ -38,6 +38,7 @@ struct MatEntry {   // device table, one per matrix
     void *y;
     double *carry;    // tiles * k carries, then tiles * k head partials
     int32_t *carry_row;
+    const int32_t *fix_len, *fix_long;   // static carry runs of the handle (see build_fix_runs)
     uint32_t *err;    // the handle's status word for a timed-out wait
     int64_t m, tiles;
 };
@@ -60,6 +61,20 @@ struct CAcc {   // compensated FP32 (see SPMV_ACC_COMPENSATED)
     __device__ __forceinline__ void add(const CAcc &o) { df_add(s, c, o.s, o.c); }
     __device__ __forceinline__ CAcc shfl_up(int o) const {
         CAcc r;
+        r.s = __shfl_up_sync(0xffffffffu, s, o);
+        r.c = __shfl_up_sync(0xffffffffu, c, o);
+        return r;
+    }
+    __device__ __forceinline__ double dbl() const { return df_to_double(s, c); }
+    template <typename XT> __device__ __forceinline__ XT out() const { return XT(__fadd_rn(s, c)); }
+};
+struct SAcc {   // FP32 inside a lane, compensated across lanes and tiles (SPMV_ACC_SEGMENT)
+    float s, c;
+    __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
+    __device__ __forceinline__ void mad(float a, float x) { s = __fmaf_rn(a, x, s); }
+    __device__ __forceinline__ void add(const SAcc &o) { df_add(s, c, o.s, o.c); }
+    __device__ __forceinline__ SAcc shfl_up(int o) const {
+        SAcc r;
         r.s = __shfl_up_sync(0xffffffffu, s, o);
         r.c = __shfl_up_sync(0xffffffffu, c, o);
         return r;
@@ -267,8 +282,28 @@ __global__ __launch_bounds__(BW * 32) void k_batch(const MatEntry *__restrict__ 
     }
 }
 
-// Carry fix-up over the global tile space (see k_merge_fixup_tiles): one thread per
-// (tile, right-hand side).
+// Carry fix-up over the global tile space, as the single-vector product's (same run
+// structure, same summation order, so each column equals spmv_mul's result bitwise): one
+// thread per (tile, right-hand side) sums a short run in tile order; one warp per (long run,
+// right-hand side) sums a long one with lane-strided partials and a fixed shuffle tree.
+template <typename XT>
+__device__ __forceinline__ void batch_finish(const MatEntry &me, int64_t u, int32_t row, int k, int r, double sum) {
+    if (row >= me.m || u >= me.tiles) return;
+    XT *Y = (XT *)me.y;
+    if (me.desc[u * 32] >> 31) Y[(int64_t)row * k + r] = XT(sum + me.carry[(me.tiles + u) * k + r]);
+    else if (sum != 0.0) Y[(int64_t)row * k + r] = XT((double)Y[(int64_t)row * k + r] + sum);
+}
+
+__device__ __forceinline__ int find_entry(const int64_t *__restrict__ prefix, int count, int64_t g) {
+    int lo = 0, hi = count - 1;   // largest i with prefix[i] <= g
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 template <typename XT>
 __global__ void k_batch_fixup(const MatEntry *__restrict__ mats, const int64_t *__restrict__ prefix, int count,
                               int64_t total_tiles, int k) {
@@ -276,23 +311,33 @@ __global__ void k_batch_fixup(const MatEntry *__restrict__ mats, const int64_t *
     if (gid >= total_tiles * k) return;
     const int64_t g = gid / k;
     const int r = (int)(gid % k);
-    int lo = 0, hi = count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (prefix[mid] <= g) lo = mid;
-        else hi = mid - 1;
-    }
-    const MatEntry me = mats[lo];
-    const int64_t t = g - prefix[lo];
-    const int32_t row = me.carry_row[t];
-    if (t > 0 && me.carry_row[t - 1] == row) return;
+    const int i = find_entry(prefix, count, g);
+    const MatEntry &me = mats[i];
+    const int64_t t = g - prefix[i];
+    const int len = me.fix_len[t];
+    if (len == 0 || len > FIX_SHORT) return;
     double s = me.carry[t * k + r];
-    int64_t u = t + 1;
-    for (; u < me.tiles && me.carry_row[u] == row; ++u) s = s + me.carry[u * k + r];
-    if (row >= me.m || u >= me.tiles) return;
-    XT *Y = (XT *)me.y;
-    if (me.desc[u * 32] >> 31) Y[(int64_t)row * k + r] = XT(s + me.carry[(me.tiles + u) * k + r]);
-    else if (s != 0.0) Y[(int64_t)row * k + r] = XT((double)Y[(int64_t)row * k + r] + s);
+    for (int q = 1; q < len; ++q) s = s + me.carry[(t + q) * k + r];
+    batch_finish<XT>(me, t + len, me.carry_row[t], k, r, s);
+}
+
+template <typename XT>
+__global__ void k_batch_fixup_long(const MatEntry *__restrict__ mats, const int64_t *__restrict__ lprefix, int count,
+                                   int64_t total_long, int k) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= total_long * k) return;
+    const int64_t g = w / k;
+    const int r = (int)(w % k);
+    const int i = find_entry(lprefix, count, g);
+    const MatEntry &me = mats[i];
+    const int64_t t0 = me.fix_long[g - lprefix[i]];
+    const int len = me.fix_len[t0];
+    double s = 0.0;
+    for (int q = lane; q < len; q += 32) s = s + me.carry[(t0 + q) * k + r];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = s + __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) batch_finish<XT>(me, t0 + len, me.carry_row[t0], k, r, s);
 }
 
 // ---------------------------------------------------------------- plans
@@ -303,6 +348,8 @@ struct Plan {
     bool vec4 = false;
     MatEntry *d_mats = nullptr;
     int64_t *d_prefix = nullptr;
+    int64_t *d_lprefix = nullptr;   // prefix of the matrices' long carry runs
+    int64_t total_long = 0;
     double *d_carry = nullptr;
     int32_t *d_crow = nullptr;
     std::vector<MatEntry> h_mats;
@@ -318,6 +365,7 @@ void free_plan(Plan *p) {
     if (p->graph) cudaGraphExecDestroy(p->graph);
     dev_free(p->d_mats);
     dev_free(p->d_prefix);
+    dev_free(p->d_lprefix);
     dev_free(p->d_carry);
     dev_free(p->d_crow);
     delete p;
@@ -349,6 +397,12 @@ spmv_status enqueue_batch(Plan *p, cudaStream_t s) {
     SPMV_LAUNCH("k_batch_fixup", s, (k_batch_fixup<XT><<<(unsigned)((nfix + 255) / 256), 256, 0, s>>>(
                                         p->d_mats, p->d_prefix, (int)p->hs.size(), p->total_tiles, p->k)));
     SPMV_LAUNCH_CHECK("batch fixup");
+    if (p->total_long > 0) {
+        const int64_t threads = p->total_long * p->k * 32;
+        SPMV_LAUNCH("k_batch_fixup_long", s, (k_batch_fixup_long<XT><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+                                                 p->d_mats, p->d_lprefix, (int)p->hs.size(), p->total_long, p->k)));
+        SPMV_LAUNCH_CHECK("batch fixup long");
+    }
     return SPMV_OK;
 }
 
@@ -375,6 +429,10 @@ spmv_status enqueue_plan(Plan *p, cudaStream_t s) {
         if (dt == SPMV_F32) return enqueue_kb<float, float, float, CAcc>(p, v4, s);
         if (dt == SPMV_BF16) return enqueue_kb<__nv_bfloat16, float, float, CAcc>(p, v4, s);
         if (dt == SPMV_PATTERN) return enqueue_kb<PatternB, float, float, CAcc>(p, v4, s);
+    } else if (p->vdt == SPMV_F32 && p->acc == SPMV_ACC_SEGMENT) {
+        if (dt == SPMV_F32) return enqueue_kb<float, float, float, SAcc>(p, v4, s);
+        if (dt == SPMV_BF16) return enqueue_kb<__nv_bfloat16, float, float, SAcc>(p, v4, s);
+        if (dt == SPMV_PATTERN) return enqueue_kb<PatternB, float, float, SAcc>(p, v4, s);
     } else if (p->vdt == SPMV_F32 && p->acc == SPMV_ACC_F64) {
         if (dt == SPMV_F32) return enqueue_kb<float, float, double, DAcc>(p, v4, s);
         if (dt == SPMV_BF16) return enqueue_kb<__nv_bfloat16, float, double, DAcc>(p, v4, s);
@@ -399,6 +457,7 @@ void batch_slot_free(BatchSlot *b) {
     if (!b) return;
     dev_free(b->plan.d_mats);
     dev_free(b->plan.d_prefix);
+    dev_free(b->plan.d_lprefix);
     dev_free(b->plan.d_carry);
     dev_free(b->plan.d_crow);
     b->plan.d_mats = nullptr;
@@ -433,9 +492,13 @@ spmv_status batch_direct(BatchSlot *b, int count, spmv_matrix *const *hs, int k,
     p->acc = acc;
     p->dt = dt;
     p->vec4 = vec4;
-    std::vector<int64_t> prefix(count + 1, 0);
-    for (int i = 0; i < count; ++i) prefix[i + 1] = prefix[i] + hs[i]->tiles;
+    std::vector<int64_t> prefix(count + 1, 0), lprefix(count + 1, 0);
+    for (int i = 0; i < count; ++i) {
+        prefix[i + 1] = prefix[i] + hs[i]->tiles;
+        lprefix[i + 1] = lprefix[i] + hs[i]->fix_long_count;
+    }
     p->total_tiles = prefix[count];
+    p->total_long = lprefix[count];
     if (p->total_tiles == 0) return SPMV_OK;
     auto grow = [&](void **ptr, int64_t &cap, int64_t need, size_t unit, const char *what) -> spmv_status {
         if (need <= cap) return SPMV_OK;
@@ -446,9 +509,10 @@ spmv_status batch_direct(BatchSlot *b, int count, spmv_matrix *const *hs, int k,
         cap = need;
         return SPMV_OK;
     };
-    int64_t cap_prefix = b->cap_mats ? b->cap_mats + 1 : 0;
+    int64_t cap_prefix = b->cap_mats ? b->cap_mats + 1 : 0, cap_lprefix = cap_prefix;
     SPMV_TRY(grow((void **)&p->d_mats, b->cap_mats, count, sizeof(MatEntry), "batch table"));
     SPMV_TRY(grow((void **)&p->d_prefix, cap_prefix, count + 1, 8, "batch prefix"));
+    SPMV_TRY(grow((void **)&p->d_lprefix, cap_lprefix, count + 1, 8, "batch long-run prefix"));
     SPMV_TRY(grow((void **)&p->d_carry, b->cap_carry, 2 * p->total_tiles * k, 8, "batch carries"));
     SPMV_TRY(grow((void **)&p->d_crow, b->cap_tiles, p->total_tiles, 4, "batch carry rows"));
     p->h_mats.resize(count);
@@ -464,12 +528,15 @@ spmv_status batch_direct(BatchSlot *b, int count, spmv_matrix *const *hs, int k,
         e.y = Y[i];
         e.carry = p->d_carry + 2 * prefix[i] * k;
         e.carry_row = p->d_crow + prefix[i];
+        e.fix_len = h->fix_len;
+        e.fix_long = h->fix_long;
         e.err = h->status_dev + 3;
         e.m = h->m;
         e.tiles = h->tiles;
     }
     // pageable sources are staged before the calls return
     SPMV_CUDA_TRY(cudaMemcpyAsync(p->d_prefix, prefix.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+    SPMV_CUDA_TRY(cudaMemcpyAsync(p->d_lprefix, lprefix.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
     SPMV_CUDA_TRY(cudaMemcpyAsync(p->d_mats, p->h_mats.data(), sizeof(MatEntry) * count, cudaMemcpyHostToDevice, s));
     return enqueue_plan(p, s);
 }
@@ -509,13 +576,19 @@ spmv_status mul_batch(int count, spmv_matrix *const *hs, int k, const void *cons
         plan->acc = acc;
         plan->dt = dt;
         plan->vec4 = vec4;
-        std::vector<int64_t> prefix(count + 1, 0);
-        for (int i = 0; i < count; ++i) prefix[i + 1] = prefix[i] + hs[i]->tiles;
+        std::vector<int64_t> prefix(count + 1, 0), lprefix(count + 1, 0);
+        for (int i = 0; i < count; ++i) {
+            prefix[i + 1] = prefix[i] + hs[i]->tiles;
+            lprefix[i + 1] = lprefix[i] + hs[i]->fix_long_count;
+        }
         plan->total_tiles = prefix[count];
+        plan->total_long = lprefix[count];
         auto fail = [&](spmv_status st) { free_plan(plan); return st; };
         spmv_status st;
         if ((st = dev_alloc((void **)&plan->d_mats, sizeof(MatEntry) * count, "batch table", s)) != SPMV_OK ||
             (st = dev_alloc((void **)&plan->d_prefix, sizeof(int64_t) * (count + 1), "batch prefix", s)) != SPMV_OK ||
+            (st = dev_alloc((void **)&plan->d_lprefix, sizeof(int64_t) * (count + 1), "batch long-run prefix", s)) !=
+                SPMV_OK ||
             (st = dev_alloc((void **)&plan->d_carry, sizeof(double) * 2 * plan->total_tiles * k, "batch carries", s)) !=
                 SPMV_OK ||
             (st = dev_alloc((void **)&plan->d_crow, sizeof(int32_t) * plan->total_tiles, "batch carry rows", s)) !=
@@ -532,12 +605,16 @@ spmv_status mul_batch(int count, spmv_matrix *const *hs, int k, const void *cons
             e.part_nz = h->part_nz;
             e.carry = plan->d_carry + 2 * prefix[i] * k;
             e.carry_row = plan->d_crow + prefix[i];
+            e.fix_len = h->fix_len;
+            e.fix_long = h->fix_long;
             e.err = h->status_dev + 3;
             e.m = h->m;
             e.tiles = h->tiles;
         }
         cudaError_t e = cudaMemcpyAsync(plan->d_prefix, prefix.data(), sizeof(int64_t) * (count + 1),
                                         cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(plan->d_lprefix, lprefix.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return fail(cuda_status(e, "batch plan upload"));
         if (plan->total_tiles > 0) {   // capture the two launches once per batch shape
             cudaStream_t cs;

@@ -105,6 +105,21 @@ struct CompAcc {
     template <typename XT> __device__ __forceinline__ XT out() const { return XT(__fadd_rn(s, c)); }
 };
 
+// FP32 products and sums inside a lane (at most MERGE_WARP_IPT terms), compensated only in
+// the segmented reduction that joins lanes and tiles (SPMV_ACC_SEGMENT): a row contained in
+// one lane costs plain FP32; a longer row's lane partials are combined with TwoSum, so its
+// error stays at the short in-lane sums' ~7u instead of growing with the row length.
+struct SegAcc : CompAcc {
+    __device__ __forceinline__ void mad(float a, float x) { s = __fmaf_rn(a, x, s); }
+    __device__ __forceinline__ SegAcc shfl_up(int o) const {
+        SegAcc r;
+        r.s = __shfl_up_sync(0xffffffffu, s, o);
+        r.c = __shfl_up_sync(0xffffffffu, c, o);
+        return r;
+    }
+    __device__ __forceinline__ void add(const SegAcc &o) { df_add(s, c, o.s, o.c); }
+};
+
 // Operand loaders: native (value converted to AT) or split into double-float pairs.
 template <typename VT, typename AT>
 struct NativeLoad {
@@ -580,8 +595,9 @@ __global__ __launch_bounds__(MW_WARPS * 32) void k_merge_warp(const uint32_t *__
                                                                   smem_raw + (threadIdx.x >> 5) * 2 * WarpSlot<VT>::BYTES);
 }
 
-// FP32 or bfloat16 values with FP32 vectors, compensated FP32 accumulation.
-template <typename VT>
+// FP32 or bfloat16 values with FP32 vectors, compensated FP32 accumulation (Acc = CompAcc
+// everywhere, or SegAcc: compensated in the segmented reduction only).
+template <typename VT, typename Acc>
 __global__ __launch_bounds__(MW_WARPS * 32) void k_merge_warp_comp(const uint32_t *__restrict__ desc,
                                                                    const int32_t *__restrict__ col,
                                                                    const VT *__restrict__ val,
@@ -592,7 +608,7 @@ __global__ __launch_bounds__(MW_WARPS * 32) void k_merge_warp_comp(const uint32_
                                                                    double *__restrict__ carry_val, int64_t ntiles,
                                                                    uint32_t *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    merge_warp_run<CompAcc, NativeSLoad<VT, float>, VT, float, float>(ntiles, desc, col, val, x, y, part_row, part_nz,
+    merge_warp_run<Acc, NativeSLoad<VT, float>, VT, float, float>(ntiles, desc, col, val, x, y, part_row, part_nz,
                                                                      carry_row, carry_val, err,
                                                                      smem_raw + (threadIdx.x >> 5) * 2 * WarpSlot<VT>::BYTES);
 }
@@ -1181,16 +1197,16 @@ spmv_status launch_hb(const spmv_matrix *h, const void *x, void *y, cudaStream_t
 // BF16/F32/F32; BF16/F32/F64; PATTERN/F64/F64; PATTERN/F32/F32.
 enum Algo { MERGE, ROWSPLIT, HB };
 
-template <typename VT>
+template <typename VT, typename Acc>
 spmv_status launch_merge_comp(const spmv_matrix *h, const void *x, void *y, cudaStream_t s) {
     constexpr size_t smem = (size_t)MW_WARPS * 2 * WarpSlot<VT>::BYTES;
     static bool attr = false;
     if (!attr) {
-        SPMV_TRY(set_smem((const void *)k_merge_warp_comp<VT>, smem));
+        SPMV_TRY(set_smem((const void *)k_merge_warp_comp<VT, Acc>, smem));
         attr = true;
     }
-    const unsigned grid = persistent_grid((const void *)k_merge_warp_comp<VT>, MW_WARPS * 32, smem, h->tiles);
-    SPMV_LAUNCH("k_merge_spmv", s, (k_merge_warp_comp<VT><<<grid, MW_WARPS * 32, smem, s>>>(
+    const unsigned grid = persistent_grid((const void *)k_merge_warp_comp<VT, Acc>, MW_WARPS * 32, smem, h->tiles);
+    SPMV_LAUNCH("k_merge_spmv", s, (k_merge_warp_comp<VT, Acc><<<grid, MW_WARPS * 32, smem, s>>>(
                                        h->merge_desc, h->col, (const VT *)h->val, (const float *)x, (float *)y,
                                        h->part_row, h->part_nz, h->carry_row, h->carry_val, h->tiles,
                                        h->status_dev + 3)));
@@ -1219,9 +1235,14 @@ spmv_status dispatch(Algo a, const spmv_matrix *h, const void *x, void *y, spmv_
         goto unsupported;
     }
     if (vdt == SPMV_F32 && acc == SPMV_ACC_COMPENSATED && a == MERGE) {
-        if (dt == SPMV_F32) return launch_merge_comp<float>(h, x, y, s);
-        if (dt == SPMV_BF16) return launch_merge_comp<__nv_bfloat16>(h, x, y, s);
-        if (dt == SPMV_PATTERN) return launch_merge_comp<Pattern>(h, x, y, s);
+        if (dt == SPMV_F32) return launch_merge_comp<float, CompAcc>(h, x, y, s);
+        if (dt == SPMV_BF16) return launch_merge_comp<__nv_bfloat16, CompAcc>(h, x, y, s);
+        if (dt == SPMV_PATTERN) return launch_merge_comp<Pattern, CompAcc>(h, x, y, s);
+    }
+    if (vdt == SPMV_F32 && acc == SPMV_ACC_SEGMENT && a == MERGE) {
+        if (dt == SPMV_F32) return launch_merge_comp<float, SegAcc>(h, x, y, s);
+        if (dt == SPMV_BF16) return launch_merge_comp<__nv_bfloat16, SegAcc>(h, x, y, s);
+        if (dt == SPMV_PATTERN) return launch_merge_comp<Pattern, SegAcc>(h, x, y, s);
     }
     if (vdt == SPMV_F32) {
         if (acc == SPMV_ACC_F32) {

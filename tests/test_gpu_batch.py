@@ -100,8 +100,8 @@ def test_batch_integer_exact(sp):
         sp.spmv_destroy(h)
 
 
-@pytest.mark.parametrize("kind,acc", [("f32", "F32"), ("f32", "COMPENSATED"), ("f32", "F64"),
-                                      ("pattern", "F32"), ("pattern", "COMPENSATED")])
+@pytest.mark.parametrize("kind,acc", [("f32", "F32"), ("f32", "COMPENSATED"), ("f32", "SEGMENT"), ("f32", "F64"),
+                                      ("pattern", "F32"), ("pattern", "COMPENSATED"), ("pattern", "SEGMENT")])
 def test_batch_f32_bitwise_equal_to_single(sp, kind, acc):
     k = 4
     accv = getattr(sp, "SPMV_ACC_" + acc)
@@ -251,3 +251,32 @@ def test_batch_k1_runs_each_handles_active_format(sp):
         assert (np.abs(got - oracle.csr_spmv(rp, co, vo, X[:, 0])) <= TOL * scale).all(), i
     for t in mats:
         sp.spmv_destroy(t[0])
+
+
+@pytest.mark.parametrize("acc", ["F64", "SEGMENT"])
+def test_batch_long_carry_runs_bitwise_equal_to_single(sp, acc):
+    """Rows of up to 20,000 nonzeros span more than 16 warp tiles, so their carries are summed
+    by the warp-wide fix-up; the batch must reproduce spmv_mul bit for bit there too."""
+    n = 20000
+    r, c = synth.zipf_rows(n, 1.2, n, 0.05, seed=95)
+    perm = synth.shuffle_order(r.size, 6)
+    r, c = r[perm], c[perm]
+    v = synth.values(r, c, 96)
+    f32 = acc == "SEGMENT"
+    vd = torch.from_numpy(v.astype(np.float32) if f32 else v).to(DEV)
+    h = sp.spmv_create_coo(n, n, torch.from_numpy(r).to(DEV), torch.from_numpy(c).to(DEV), vd)
+    sp.spmv_convert(h, "merge")
+    accv = getattr(sp, "SPMV_ACC_" + acc)
+    dt = np.float32 if f32 else np.float64
+    for k in (1, 4):
+        X = rhs(n, k, 97, dtype=dt)
+        Xd = torch.from_numpy(X).to(DEV)
+        Y = torch.full((n, k), float("nan"), dtype=Xd.dtype, device=DEV)
+        sp.spmv_mul_batch([h], [Xd], [Y], k=k, accum=accv)
+        torch.cuda.synchronize()
+        for q in range(k):
+            y1 = torch.empty(n, dtype=Xd.dtype, device=DEV)
+            sp.spmv_mul(h, Xd[:, q].contiguous(), y1, accum=accv)
+            torch.cuda.synchronize()
+            assert np.array_equal(Y[:, q].cpu().numpy(), y1.cpu().numpy()), (k, q)
+    sp.spmv_destroy(h)

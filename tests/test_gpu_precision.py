@@ -7,6 +7,8 @@ values in double precision, so the comparison isolates the accumulation error.  
 with u = 2^-24 and L the row length:
   FP32 accumulation          |y - ref| <= gamma(L + 1) (|A||x|) + u |ref|
   compensated FP32           |y - ref| <= 8 L u^2 (|A||x|) + u |ref| + 2^-140
+  segmented compensation     |y - ref| <= (gamma(8) + 8 L u^2) (|A||x|) + u |ref| + 2^-140
+                             (FP32 inside a lane's <= 7 items, TwoSum where lanes and tiles join)
   FP64 accumulation          |y - ref| <= u |ref| + 1e-14 (|A||x|)     (output rounded to FP32)
 Integer-valued data with integer x is exact in every mode (all partial sums < 2^24).
 """
@@ -67,7 +69,8 @@ def test_precision_modes(sp, kind):
             h = sp.spmv_create_coo(m, n, torch.from_numpy(rows).to(DEV), torch.from_numpy(cols).to(DEV), vd,
                                    dtype=sp.SPMV_PATTERN if vd is None else None)
             xd = torch.from_numpy(x32).to(DEV)
-            for algo, modes in (("merge", (sp.SPMV_ACC_F32, sp.SPMV_ACC_COMPENSATED, sp.SPMV_ACC_F64)),
+            for algo, modes in (("merge", (sp.SPMV_ACC_F32, sp.SPMV_ACC_COMPENSATED, sp.SPMV_ACC_SEGMENT,
+                                           sp.SPMV_ACC_F64)),
                                 ("rowsplit", (sp.SPMV_ACC_F32, sp.SPMV_ACC_F64))):
                 sp.spmv_convert(h, algo)
                 for acc in modes:
@@ -86,6 +89,8 @@ def test_precision_modes(sp, kind):
                         bound = g * scale + U * np.abs(ref)
                     elif acc == sp.SPMV_ACC_COMPENSATED:
                         bound = 8 * L * U * U * scale + U * np.abs(ref) + 2.0 ** -140
+                    elif acc == sp.SPMV_ACC_SEGMENT:   # <= 7 FP32 terms per lane, TwoSum joins
+                        bound = (8 * U / (1 - 8 * U) + 8 * L * U * U) * scale + U * np.abs(ref) + 2.0 ** -140
                     else:
                         bound = U * np.abs(ref) + 1e-14 * scale
                     assert (err <= bound).all(), (name, algo, acc, float(np.max(err - bound)))
@@ -109,12 +114,12 @@ def test_compensation_reduces_error(sp):
     sp.spmv_convert(h, "merge")
     xd = torch.from_numpy(x32).to(DEV)
     errs = {}
-    for acc in (sp.SPMV_ACC_F32, sp.SPMV_ACC_COMPENSATED):
+    for acc in (sp.SPMV_ACC_F32, sp.SPMV_ACC_SEGMENT, sp.SPMV_ACC_COMPENSATED):
         y = torch.empty(n, dtype=torch.float32, device=DEV)
         sp.spmv_mul(h, xd, y, accum=acc)
         torch.cuda.synchronize()
         errs[acc] = np.abs(y.cpu().numpy().astype(np.float64) - ref).max()
-    assert errs[sp.SPMV_ACC_COMPENSATED] <= errs[sp.SPMV_ACC_F32]
+    assert errs[sp.SPMV_ACC_COMPENSATED] <= errs[sp.SPMV_ACC_SEGMENT] <= errs[sp.SPMV_ACC_F32]
 
 
 @pytest.mark.parametrize("scale", [10, 14])
