@@ -302,6 +302,159 @@ def serving_leg(sp, torch, dev, synth, np):
     return out
 
 
+# ------------------------------------------------------------------ batched leg
+
+BATCH = dict(n_matrices=64, scales=(10, 18), edge_factors=(8, 32), ks=(1, 4, 16), reps=5)
+BATCH_FULL = dict(n_matrices=512, scales=(10, 20), edge_factors=(8, 32), ks=(1, 4, 16), reps=3)
+
+
+def batched_leg(sp, torch, dev, synth, np, cfg):
+    """Many R-MAT matrices of uneven size (FP32 values) times k FP32 right-hand sides in one
+    captured batched launch (spmv_mul_batch), against the plain path: one FP64 spmv_mul per
+    matrix and right-hand side.  GFLOP/s = 2 nnz k / time (device events)."""
+    rng = np.random.Generator(np.random.PCG64(88))
+    scales = rng.integers(cfg["scales"][0], cfg["scales"][1] + 1, size=cfg["n_matrices"])
+    efs = rng.integers(cfg["edge_factors"][0], cfg["edge_factors"][1] + 1, size=cfg["n_matrices"])
+    h32, h64, ns, nnz_total = [], [], [], 0
+    for i, (sc, ef) in enumerate(zip(scales, efs)):
+        n = 1 << int(sc)
+        r, c = synth.rmat(int(sc), int(ef), seed=5000 + i)
+        v = synth.values(r, c, seed=5000 + i)
+        rd, cd = torch.from_numpy(r).to(dev), torch.from_numpy(c).to(dev)
+        a = sp.spmv_create_coo(n, n, rd, cd, torch.from_numpy(v.astype(np.float32)).to(dev))
+        sp.spmv_convert(a, "merge")
+        b = sp.spmv_create_coo(n, n, rd, cd, torch.from_numpy(v).to(dev))
+        sp.spmv_convert(b, "merge")
+        h32.append(a)
+        h64.append(b)
+        ns.append(n)
+        nnz_total += sp.spmv_info(a)["nnz"]
+    out = {"config": {"matrices": int(cfg["n_matrices"]), "scales": [int(cfg["scales"][0]), int(cfg["scales"][1])],
+                      "edge_factors": [int(cfg["edge_factors"][0]), int(cfg["edge_factors"][1])], "nnz": int(nnz_total),
+                      "values": "f32 batched / f64 plain", "rhs": "f32 batched / f64 plain"}, "k": []}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for k in cfg["ks"]:
+        X = [torch.randn(n, k, dtype=torch.float32, device=dev) for n in ns]
+        Y = [torch.empty(n, k, dtype=torch.float32, device=dev) for n in ns]
+        sp.spmv_mul_batch(h32, X, Y, k=k)          # plan + graph capture
+        torch.cuda.synchronize()
+        t0, t1 = ev(), ev()
+        t0.record()
+        for _ in range(cfg["reps"]):
+            sp.spmv_mul_batch(h32, X, Y, k=k)
+        t1.record()
+        torch.cuda.synchronize()
+        ms_b = t0.elapsed_time(t1) / cfg["reps"]
+        # plain: one FP64 product per matrix and column
+        X64 = [x.double() for x in X]
+        cols = [[x[:, q].contiguous() for q in range(k)] for x in X64]
+        y64 = [torch.empty(n, dtype=torch.float64, device=dev) for n in ns]
+        for h, cs, y in zip(h64, cols, y64):
+            sp.spmv_mul(h, cs[0], y)
+        torch.cuda.synchronize()
+        t0.record()
+        for h, cs, y in zip(h64, cols, y64):
+            for xc in cs:
+                sp.spmv_mul(h, xc, y)
+        t1.record()
+        torch.cuda.synchronize()
+        ms_p = t0.elapsed_time(t1)
+        flops = 2.0 * nnz_total * k
+        out["k"].append({"k": k, "batched_ms": round(ms_b, 4), "batched_gflops": round(flops / ms_b / 1e6, 1),
+                         "plain_fp64_ms": round(ms_p, 4), "plain_fp64_gflops": round(flops / ms_p / 1e6, 1)})
+        del X, Y, X64, cols, y64
+    for h in h32 + h64:
+        sp.spmv_destroy(h)
+    return out
+
+
+# ------------------------------------------------------------------ precision leg
+
+def precision_leg(sp, torch, dev, synth, np):
+    """Stored values FP64 / FP32 / BF16 / pattern times each accumulation mode on two matrices
+    (Erdos-Renyi n = 2^23 with 8 per row; Zipf(1.8) rows on n = 2^22, capped at 2^20, 5% empty).
+    Errors are normwise per row, max_i |y_i - ref_i| / (|A||x|)_i: 'accumulation' against the
+    FP64 product of the same rounded values, 'total' against the FP64 product of the original
+    values (FP64 native products match the oracle within 1e-13 (|A||x|), see the tests)."""
+    def mats():
+        n = 1 << 23
+        r, c = synth.erdos_renyi(n, 8, seed=11)
+        yield "erdos_renyi n=2^23 8/row", n, r, c
+        n = 1 << 22
+        r, c = synth.zipf_rows(n, 1.8, 1 << 20, 0.05, seed=12)
+        yield "zipf(1.8) rows n=2^22 cap 2^20 5% empty", n, r, c
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    out = []
+    for name, n, r, c in mats():
+        v64 = synth.values(r, c, seed=13)
+        x64 = synth.vector(n, seed=14)
+        rd, cd = torch.from_numpy(r).to(dev), torch.from_numpy(c).to(dev)
+        xd64 = torch.from_numpy(x64).to(dev)
+        xd32 = xd64.float()
+        xr64 = xd32.double()                       # the FP32 x as exact doubles
+
+        def fp64_product(vals, x, absval=False):
+            h = sp.spmv_create_coo(n, n, rd, cd, None if vals is None else (vals.abs() if absval else vals),
+                                   dtype=sp.SPMV_PATTERN if vals is None else None)
+            sp.spmv_convert(h, "merge")
+            y = torch.empty(n, dtype=torch.float64, device=dev)
+            sp.spmv_mul(h, x.abs() if absval else x, y, accum=sp.SPMV_ACC_F64)
+            torch.cuda.synchronize()
+            sp.spmv_destroy(h)
+            return y
+
+        v64d = torch.from_numpy(v64).to(dev)
+        y_exact = fp64_product(v64d, xd64)
+        s_exact = fp64_product(v64d, xd64, absval=True)
+        entry = {"matrix": name, "n": n, "nnz": int(r.size), "modes": []}
+        for kind in ("f64", "f32", "bf16", "pattern"):
+            if kind == "f64":
+                vstore, vr = v64d, v64d
+            elif kind == "f32":
+                vstore = v64d.float()
+                vr = vstore.double()
+            elif kind == "bf16":
+                bits = synth.round_bf16_bits(v64)
+                vstore = torch.from_numpy(bits.view(np.int16)).to(dev).view(torch.bfloat16)
+                vr = torch.from_numpy(synth.bf16_bits_to_float64(bits)).to(dev)
+            else:
+                vstore, vr = None, None
+            xin = xd64 if kind == "f64" else xd32
+            xref = xd64 if kind == "f64" else xr64
+            y_ref = fp64_product(vr, xref)
+            s_ref = fp64_product(vr, xref, absval=True)
+            h = sp.spmv_create_coo(n, n, rd, cd, vstore, dtype=sp.SPMV_PATTERN if vstore is None else None)
+            sp.spmv_convert(h, "merge")
+            modes = ([("default (double-float)", sp.SPMV_ACC_DEFAULT), ("f64", sp.SPMV_ACC_F64)] if kind == "f64" else
+                     [("f32", sp.SPMV_ACC_F32), ("segment", sp.SPMV_ACC_SEGMENT),
+                      ("compensated", sp.SPMV_ACC_COMPENSATED)] + ([("f64", sp.SPMV_ACC_F64)] if kind != "pattern" else []))
+            y = torch.empty(n, dtype=xin.dtype, device=dev)
+            for mname, acc in modes:
+                sp.spmv_mul(h, xin, y, accum=acc)
+                torch.cuda.synchronize()
+                t0, t1 = ev(), ev()
+                t0.record()
+                for _ in range(5):
+                    sp.spmv_mul(h, xin, y, accum=acc)
+                t1.record()
+                torch.cuda.synchronize()
+                ms = t0.elapsed_time(t1) / 5
+                yd = y.double()
+                ok_r, ok_e = s_ref > 0, s_exact > 0
+                acc_err = float(((yd - y_ref).abs()[ok_r] / s_ref[ok_r]).max()) if bool(ok_r.any()) else 0.0
+                tot_err = float(((yd - y_exact).abs()[ok_e] / s_exact[ok_e]).max()) if bool(ok_e.any()) else 0.0
+                es = {"f64": 8, "f32": 4, "bf16": 2, "pattern": 0}[kind]
+                xs = 8 if kind == "f64" else 4
+                nbytes = r.size * (4 + es) + (n + 1) * 4 + 2 * n * xs
+                entry["modes"].append({"values": kind, "accumulation": mname, "ms": round(ms, 4),
+                                       "gbs": round(nbytes / ms / 1e6, 1), "gflops": round(2 * r.size / ms / 1e6, 1),
+                                       "max_accumulation_err": acc_err,
+                                       "max_total_err": None if kind == "pattern" else tot_err})
+            sp.spmv_destroy(h)
+        out.append(entry)
+    return out
+
+
 # ------------------------------------------------------------------ main
 
 def main():
@@ -315,6 +468,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--batched-full", action="store_true", help="512 matrices, scales 10-20")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -514,6 +670,14 @@ def main():
     if not args.no_serving:
         serving = serving_leg(sp, torch, dev, synth, np)
 
+    batched = None
+    if not args.no_batched:
+        batched = batched_leg(sp, torch, dev, synth, np, BATCH_FULL if args.batched_full else BATCH)
+
+    precision = None
+    if not args.no_precision:
+        precision = precision_leg(sp, torch, dev, synth, np)
+
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -549,6 +713,8 @@ def main():
         "kernel_shares": shares,
         "break_even": break_even,
         "serving": serving,
+        "batched": batched,
+        "precision": precision,
         "cpu_baseline": cpu,
         "wall_s_timed": round(wall_s, 3),
     }

@@ -377,7 +377,7 @@ spmv_status enqueue_batch(Plan *p, cudaStream_t s) {
     const size_t smem = (size_t)BW * Slot::BYTES;
     static bool attr = false;
     if (!attr) {
-        SPMV_TRY(set_smem((const void *)k_batch<VT, XT, T, Acc, KB>, smem));
+        SPMV_TRY(set_smem_ctas((const void *)k_batch<VT, XT, T, Acc, KB>, smem, 5));
         attr = true;
     }
     int dev = 0, sms = 1, per_sm = 1;

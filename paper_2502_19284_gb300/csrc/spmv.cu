@@ -999,7 +999,7 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
     }
     static bool attr = false;
     if (!attr) {
-        SPMV_TRY(set_smem((const void *)k_merge_warp<VT, XT, AT>, smem));
+        SPMV_TRY(set_smem_ctas((const void *)k_merge_warp<VT, XT, AT>, smem, 5));
         attr = true;
     }
     const unsigned grid = persistent_grid((const void *)k_merge_warp<VT, XT, AT>, MW_WARPS * 32, smem, h->tiles);
@@ -1202,7 +1202,7 @@ spmv_status launch_merge_comp(const spmv_matrix *h, const void *x, void *y, cuda
     constexpr size_t smem = (size_t)MW_WARPS * 2 * WarpSlot<VT>::BYTES;
     static bool attr = false;
     if (!attr) {
-        SPMV_TRY(set_smem((const void *)k_merge_warp_comp<VT, Acc>, smem));
+        SPMV_TRY(set_smem_ctas((const void *)k_merge_warp_comp<VT, Acc>, smem, 5));
         attr = true;
     }
     const unsigned grid = persistent_grid((const void *)k_merge_warp_comp<VT, Acc>, MW_WARPS * 32, smem, h->tiles);
@@ -1360,7 +1360,7 @@ spmv_status mul_merge_pattern_split(const spmv_matrix *h, const double *x, const
     constexpr size_t smem = (size_t)MW_WARPS * 2 * WarpSlot<Pattern>::BYTES;
     static bool attr = false;
     if (!attr) {
-        SPMV_TRY(set_smem((const void *)k_merge_warp_pat_df, smem));
+        SPMV_TRY(set_smem_ctas((const void *)k_merge_warp_pat_df, smem, 5));
         attr = true;
     }
     const unsigned grid = persistent_grid((const void *)k_merge_warp_pat_df, MW_WARPS * 32, smem, h->tiles);
