@@ -142,7 +142,13 @@ spmv_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, voi
 namespace {
 
 constexpr int RS_BLOCK = 256;
-constexpr int RS_IPT = 16;
+#ifndef RS_IPT_CFG
+#define RS_IPT_CFG 8
+#endif
+#ifndef RS_MINB_CFG
+#define RS_MINB_CFG 5
+#endif
+constexpr int RS_IPT = RS_IPT_CFG;   // keys per thread in a radix tile
 constexpr int RS_TILE = RS_BLOCK * RS_IPT;
 constexpr int RS_WARPS = RS_BLOCK / 32;
 constexpr int RADIX = 256;
@@ -199,7 +205,7 @@ constexpr long long RS_SPIN_LIMIT = 1ll << 22;
 
 __device__ __forceinline__ uint32_t rs_smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__global__ __launch_bounds__(RS_BLOCK, 3) void k_rs_scatter(const uint64_t *__restrict__ keys_in,
+__global__ __launch_bounds__(RS_BLOCK, RS_MINB_CFG) void k_rs_scatter(const uint64_t *__restrict__ keys_in,
                                                             const uint32_t *__restrict__ vals_in,
                                                             uint64_t *__restrict__ keys_out,
                                                             uint32_t *__restrict__ vals_out, int64_t n, int shift,

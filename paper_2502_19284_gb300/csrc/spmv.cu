@@ -1032,7 +1032,21 @@ __device__ __forceinline__ void rowsplit_group(const int32_t *__restrict__ row_p
     if (ridx < count) {
         row = rows[ridx];
         const int32_t k0 = __ldg(row_ptr + row), k1 = __ldg(row_ptr + row + 1);
-        for (int32_t k = k0 + lane; k < k1; k += G) acc = acc + ld_val<VT, AT>(val, k) * ld_x<XT, AT>(x, __ldg(col + k));
+        // U independent loads in flight per lane (long rows of the class take several rounds)
+        constexpr int U = G >= 8 ? 4 : 1;
+        int32_t k = k0 + lane;
+        for (; k + (U - 1) * G < k1; k += U * G) {
+            int32_t c[U];
+            AT a[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                c[u] = __ldg(col + k + u * G);
+                a[u] = ld_val<VT, AT>(val, k + u * G);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) acc = acc + a[u] * ld_x<XT, AT>(x, c[u]);
+        }
+        for (; k < k1; k += G) acc = acc + ld_val<VT, AT>(val, k) * ld_x<XT, AT>(x, __ldg(col + k));
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc = acc + __shfl_xor_sync(0xffffffffu, acc, o, G);
