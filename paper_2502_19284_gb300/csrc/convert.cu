@@ -364,20 +364,24 @@ __device__ __forceinline__ int64_t row_of(const int32_t *__restrict__ row_ptr, i
 
 constexpr int HB_KEY_ROWS = 2048;   // row_ptr slice kept in shared memory per block
 
+// Row of the first CRS entry of every key tile (and of the last entry, at index ntiles), one
+// bisection per thread, so that no key tile starts with a serial search.
+__global__ void k_tile_rows(const int32_t *__restrict__ row_ptr, int64_t m, int64_t nnz, int64_t ntiles,
+                            int64_t *__restrict__ tile_row) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > ntiles) return;
+    tile_row[c] = row_of(row_ptr, 0, m - 1, min(c * (int64_t)HB_KEY_TILE, nnz - 1));
+}
+
 __global__ void k_hb_keys(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int64_t m, int64_t nnz,
-                          int K, int log2b, int inner, uint64_t *__restrict__ keys, uint32_t *__restrict__ perm) {
-    __shared__ int64_t br[2];
+                          const int64_t *__restrict__ tile_row, int K, int log2b, int inner,
+                          uint64_t *__restrict__ keys, uint32_t *__restrict__ perm) {
     __shared__ int32_t s_rp[HB_KEY_ROWS + 1];
     __shared__ uint8_t s_fwd2[64], s_inv2[64];
     if (threadIdx.x < 64) hilbert_tables2(s_fwd2, s_inv2, threadIdx.x);
     const int64_t e0 = (int64_t)blockIdx.x * HB_KEY_TILE;
     const int64_t e1 = min(e0 + (int64_t)HB_KEY_TILE, nnz) - 1;
-    if (threadIdx.x < 2) {
-        int64_t e = threadIdx.x == 0 ? e0 : e1;
-        br[threadIdx.x] = row_of(row_ptr, 0, m - 1, e);
-    }
-    __syncthreads();
-    const int64_t rlo = br[0], rhi = br[1];
+    const int64_t rlo = tile_row[blockIdx.x], rhi = tile_row[blockIdx.x + 1];   // rows of e0 and (at least) e1
     const bool in_smem = rhi - rlo + 1 <= HB_KEY_ROWS;
     if (in_smem)
         for (int64_t r = rlo + threadIdx.x; r <= rhi + 1 && r <= m; r += blockDim.x) s_rp[r - rlo] = row_ptr[r];
@@ -785,8 +789,14 @@ spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s) {
         SPMV_TRY(idx.alloc((size_t)nnz * 4, "hb idx"));
         if (es) SPMV_TRY(val.alloc((size_t)nnz * es, "hb values"));
         const int64_t ktiles = (nnz + HB_KEY_TILE - 1) / HB_KEY_TILE;
-        SPMV_LAUNCH("k_hb_keys", s, (k_hb_keys<<<(unsigned)ktiles, CB, 0, s>>>(h->row_ptr, h->col, m, nnz, K, log2b, inner, keys.as<uint64_t>(),
-                                                  perm.as<uint32_t>())));
+        DevBuf trow(s);
+        SPMV_TRY(trow.alloc((size_t)(ktiles + 1) * 8, "hb key tile rows"));
+        SPMV_LAUNCH("k_tile_rows", s, (k_tile_rows<<<grid_for(ktiles + 1), CB, 0, s>>>(h->row_ptr, m, nnz, ktiles,
+                                                                                     trow.as<int64_t>())));
+        SPMV_LAUNCH_CHECK("hb key tile rows");
+        SPMV_LAUNCH("k_hb_keys", s, (k_hb_keys<<<(unsigned)ktiles, CB, 0, s>>>(h->row_ptr, h->col, m, nnz,
+                                                                             trow.as<int64_t>(), K, log2b, inner,
+                                                                             keys.as<uint64_t>(), perm.as<uint32_t>())));
         SPMV_LAUNCH_CHECK("hb keys");
         bool alt = false;
         SPMV_TRY(radix_sort_pairs(keys.as<uint64_t>(), keys_alt.as<uint64_t>(), perm.as<uint32_t>(),
