@@ -100,7 +100,7 @@ def kernel_units(name, m, n, nnz):
     cbits = max(1, (n - 1).bit_length()) if n > 1 else 1
     rbits = max(1, (m - 1).bit_length()) if m > 1 else 1
     return {"k_rs_scatter": (sort_passes(cbits + rbits) + sort_passes(2 * K)) * nnz + m,
-            "k_merge_spmv": nnz}.get(name)
+            "k_merge_spmv": nnz, "k_hb_spmv": nnz}.get(name)
 
 
 # ------------------------------------------------------------------ clocks
@@ -633,7 +633,7 @@ def main():
         traffic = None
         t = traffic_db.get(kname)
         units = kernel_units(kname, m, n, nnz)
-        if t and units and t.get("source_sha") == source_sha(t.get("source")):
+        if t and units and t.get("source_sha") == source_sha(t.get("source"), t.get("from"), t.get("to")):
             traffic = int(t["bytes_per_unit"] * units * args.steps / cnt)   # ncu DRAM bytes, scaled per launch
         return {"kernel": kname, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "peak_note": peak_src, "traffic": traffic,
@@ -722,13 +722,21 @@ def main():
     return 0
 
 
-def source_sha(rel):
+def source_sha(rel, start=None, end=None):
+    """Hash of a kernel's source: the file, or the text between two marker lines of it."""
     if not rel:
         return None
     try:
-        return hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()[:16]
+        text = open(os.path.join(ROOT, rel), "rb").read()
     except OSError:
         return None
+    if start:
+        i = text.find(start.encode())
+        j = text.find(end.encode(), i + 1) if end and i >= 0 else -1
+        if i < 0 or j < 0:
+            return None
+        text = text[i:j]
+    return hashlib.sha256(text).hexdigest()[:16]
 
 
 def run_reference(args, rank, world):
