@@ -254,10 +254,12 @@ __global__ __launch_bounds__(RS_BLOCK, RS_MINB_CFG) void k_rs_scatter(const uint
 #else
         const uint32_t peers = digit_peers(d, valid);
 #endif
-        const uint32_t base = valid ? s_wcnt[warp * RADIX + d] : 0u;
-        __syncwarp();
-        if (valid && (peers & lt_mask) == 0) s_wcnt[warp * RADIX + d] = base + __popc(peers);
-        __syncwarp();
+        // the first lane of each peer group reserves the group's ranks with one shared-memory
+        // atomic (issued in item order, so earlier items rank first) and hands out the base
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0u;
+        if (valid && lane == leader) base = atomicAdd(&s_wcnt[warp * RADIX + d], (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader < 0 ? lane : leader);
         dr[j] = (d << 16) | (base + __popc(peers & lt_mask));
     }
     __syncthreads();
