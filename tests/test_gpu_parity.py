@@ -95,6 +95,10 @@ CASES = [
     (4097, 4097, 50000, 5, 0.0),    # ragged tails
     (3000, 3000, 20000, 6, 0.3),    # duplicates
     (70000, 70000, 30000, 7, 0.0),  # mostly empty rows
+    (1, 200000, 150000, 8, 0.0),    # one row far longer than a shared-memory sort (per-row radix)
+    (50, 100000, 200000, 9, 0.2),   # long rows with duplicates (ties kept in input order)
+    (20000, 20000, 100000, 10, 0.3),  # short rows with duplicates
+    (3, 5000, 6000, 11, 0.5),       # rows near the short/long boundary, many duplicates
 ]
 
 
