@@ -103,6 +103,24 @@ def kernel_units(name, m, n, nnz):
             "k_merge_spmv": nnz, "k_hb_spmv": nnz}.get(name)
 
 
+# ------------------------------------------------------------------ ranks
+
+def max_over_ranks(value, world, dist, device):
+    """The largest per-rank step time (every rank gets it); the job is as slow as its slowest
+    rank.  `device` is the rank's CUDA device (NCCL) or "cpu" (gloo)."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(step_bytes, ms_max, world):
+    """Whole-job GB/s: every rank processes its own instance of the workload (weak scaling)."""
+    return world * step_bytes / (ms_max * 1e-3) / 1e9
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -580,12 +598,8 @@ def main():
     rb = row_bytes(m, n, nnz, nblk)
     step_bytes = sum(rb.values())
     ms_step = total_ms / args.steps
-    ms_max = ms_step
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * step_bytes / (ms_max * 1e-3) / 1e9
+    ms_max = max_over_ranks(ms_step, world, dist, dev)
+    value = job_value(step_bytes, ms_max, world)
 
     rows_out = {}
     flops = row_flops(nnz)
@@ -656,12 +670,8 @@ def main():
         hy = [torch.empty(m, dtype=torch.float64).pin_memory() for _ in range(3)]
         K2 = max(2, args.steps // 2)
         tot2, wall2, _ = timed(K2, 1, src=(hr, hc, hv), host_x=hx, host_y=hy)
-        ms2 = tot2 / K2
-        if world > 1:
-            t = torch.tensor([ms2], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms2 = float(t.item())
-        e2e = {"value": round(world * step_bytes / (ms2 * 1e-3) / 1e9, 2), "unit": "GB/s",
+        ms2 = max_over_ranks(tot2 / K2, world, dist, dev)
+        e2e = {"value": round(job_value(step_bytes, ms2, world), 2), "unit": "GB/s",
                "h2d_bytes_per_step": nnz_in * 16 + n * 8, "d2h_bytes_per_step": 3 * m * 8,
                "ms_per_step": round(ms2, 3)}
 
