@@ -426,20 +426,37 @@ __device__ __forceinline__ void hb_cell(uint64_t key, int K, int log2b, int inne
     }
 }
 
-// Populate: packed in-block index, block-start flags.
+// Populate: packed in-block index, block-start flags.  Each thread decodes HB_FILL_U keys
+// (elements i, i + T, ... for T threads) with their table chains interleaved.
+constexpr int HB_FILL_U = 4;
 __global__ void k_hb_fill(const uint64_t *__restrict__ keys, int64_t nnz, int K, int log2b, int inner,
                           uint32_t *__restrict__ idx, uint32_t *__restrict__ head) {
     __shared__ uint8_t s_fwd2[64], s_inv2[64];
     if (threadIdx.x < 64) hilbert_tables2(s_fwd2, s_inv2, threadIdx.x);
     __syncthreads();
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nnz) return;
-    uint64_t key = keys[t];
-    uint32_t r, c;
-    hb_cell(key, K, log2b, inner, &r, &c, s_inv2);
-    uint32_t mask = (1u << log2b) - 1u;
-    idx[t] = ((r & mask) << 16) | (c & mask);
-    head[t] = (t == 0 || (keys[t - 1] >> (2 * log2b)) != (key >> (2 * log2b))) ? 1u : 0u;
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t mask = (1u << log2b) - 1u;
+    uint64_t key[HB_FILL_U];
+    uint32_t r[HB_FILL_U], c[HB_FILL_U];
+#pragma unroll
+    for (int u = 0; u < HB_FILL_U; ++u) {
+        const int64_t t = t0 + u * T;
+        key[u] = t < nnz ? keys[t] : 0ull;
+    }
+    if (inner == SPMV_INNER_ROWMAJOR) {
+#pragma unroll
+        for (int u = 0; u < HB_FILL_U; ++u) hb_cell(key[u], K, log2b, inner, &r[u], &c[u], s_inv2);
+    } else {
+        hilbert_cell2_n<HB_FILL_U>(K, key, r, c, s_inv2);
+    }
+#pragma unroll
+    for (int u = 0; u < HB_FILL_U; ++u) {
+        const int64_t t = t0 + u * T;
+        if (t >= nnz) continue;
+        idx[t] = ((r[u] & mask) << 16) | (c[u] & mask);
+        head[t] = (t == 0 || (keys[t - 1] >> (2 * log2b)) != (key[u] >> (2 * log2b))) ? 1u : 0u;
+    }
 }
 
 __global__ void k_hb_blocks(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ head,
@@ -803,7 +820,7 @@ spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s) {
                                   perm_alt.as<uint32_t>(), nnz, 0, 2 * K, tmp.p, s, &alt));
         uint64_t *Ks = alt ? keys_alt.as<uint64_t>() : keys.as<uint64_t>();
         uint32_t *Ps = alt ? perm_alt.as<uint32_t>() : perm.as<uint32_t>();
-        SPMV_LAUNCH("k_hb_fill", s, (k_hb_fill<<<grid_for(nnz), CB, 0, s>>>(Ks, nnz, K, log2b, inner, idx.as<uint32_t>(), head.as<uint32_t>())));
+        SPMV_LAUNCH("k_hb_fill", s, (k_hb_fill<<<grid_for((nnz + HB_FILL_U - 1) / HB_FILL_U), CB, 0, s>>>(Ks, nnz, K, log2b, inner, idx.as<uint32_t>(), head.as<uint32_t>())));
         SPMV_LAUNCH_CHECK("hb fill");
         if (es) SPMV_TRY(gather_values(h->val, h->dt, Ps, nnz, val.p, s));
         SPMV_TRY(exclusive_scan_u32(head.as<uint32_t>(), bid.as<uint32_t>(), nnz, tmp.p, s));

@@ -137,4 +137,42 @@ __device__ __forceinline__ void hilbert_cell2(int K, uint64_t d, uint32_t *r, ui
     *c = cc;
 }
 
+// U independent cells at once: the dependent table lookups of the U chains are
+// interleaved, so one thread keeps U of them in flight.
+template <int U>
+__device__ __forceinline__ void hilbert_cell2_n(int K, const uint64_t *d, uint32_t *r, uint32_t *c,
+                                                const uint8_t *inv2) {
+    uint32_t st[U];
+    int lev = K;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        r[u] = 0;
+        c[u] = 0;
+        st[u] = 0;
+    }
+    if (lev & 1) {
+        --lev;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t dig = (uint32_t)(d[u] >> (2 * lev)) & 3u;
+            const uint32_t e = (uint32_t)(HILBERT_INV >> (4 * dig)) & 0xFu;   // state 0
+            r[u] = (e >> 3) & 1u;
+            c[u] = (e >> 2) & 1u;
+            st[u] = e & 3u;
+        }
+    }
+    while (lev > 0) {
+        lev -= 2;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t dd = (uint32_t)(d[u] >> (2 * lev)) & 15u;
+            const uint32_t e = inv2[(st[u] << 4) | dd];
+            const uint32_t bits = e >> 2;   // r1 c1 r0 c0
+            r[u] = (r[u] << 2) | ((bits >> 3) << 1) | ((bits >> 1) & 1u);
+            c[u] = (c[u] << 2) | (((bits >> 2) & 1u) << 1) | (bits & 1u);
+            st[u] = e & 3u;
+        }
+    }
+}
+
 }  // namespace spmv

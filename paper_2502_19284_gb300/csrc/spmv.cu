@@ -618,15 +618,19 @@ __global__ __launch_bounds__(MW_WARPS * 32) void k_merge_warp_comp(const uint32_
 // sits in slot k * 32 + l, so every operand of a lane is at a fixed offset and the shared
 // memory accesses of a warp are contiguous.  A row end or tail slot holds value 0 and is
 // neither gathered nor accumulated.  Values are split into float pairs at the conversion.
+// The gathers of x go straight into registers; once a lane holds its values in registers
+// the value area takes the tile's finished rows.
+#ifndef SLOT_CTAS_CFG
+#define SLOT_CTAS_CFG 6
+#endif
 struct SlotTile {
     static constexpr int OFF_HDR = 16;                                   // after the mbarrier
     static constexpr int OFF_COL = OFF_HDR + SLOT_DESC_WORDS * 4;
-    static constexpr int OFF_VAL = OFF_COL + MW_ITEMS * 4;
-    static constexpr int OFF_XB = OFF_VAL + MW_ITEMS * 8;                // gathered x, then finished rows
-    static constexpr int BYTES = OFF_XB + MW_ITEMS * 8;
+    static constexpr int OFF_VAL = OFF_COL + MW_ITEMS * 4;               // values, then finished rows
+    static constexpr int BYTES = OFF_VAL + MW_ITEMS * 8;
     static constexpr uint32_t TX = SLOT_DESC_WORDS * 4 + MW_ITEMS * 12;   // bytes brought by TMA
 };
-static_assert(SlotTile::BYTES % 16 == 0 && SlotTile::OFF_VAL % 16 == 0 && SlotTile::OFF_XB % 16 == 0, "16-byte slots");
+static_assert(SlotTile::BYTES % 16 == 0 && SlotTile::OFF_VAL % 16 == 0 && SlotTile::OFF_COL % 16 == 0, "16-byte slots");
 
 // Operand forms: double-float (values and x as float pairs), or native FP64 with the value
 // rebuilt from its pair (|a - hi - lo| <= 2^-48 |a|) when x is outside the double-float window.
@@ -637,6 +641,19 @@ template <> struct SlotOps<DfAcc, float2> {
 template <> struct SlotOps<NativeAcc<double>, double> {
     __device__ __forceinline__ static double a(float2 v) { return (double)v.x + (double)v.y; }
 };
+static_assert(sizeof(DfAcc) <= 8 && sizeof(NativeAcc<double>) <= 8, "finished rows fit the value area");
+
+// read-only gather with an L2 policy
+__device__ __forceinline__ float2 ldg_hint(const float2 *p, uint64_t pol) {
+    float2 v;
+    asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ldg_hint(const double *p, uint64_t pol) {
+    double v;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
 
 __device__ __forceinline__ void slot_issue(const uint32_t *__restrict__ sdesc, const int32_t *__restrict__ scol,
                                            const float2 *__restrict__ sval, int64_t t, unsigned char *slot,
@@ -653,21 +670,22 @@ __device__ __forceinline__ void slot_issue(const uint32_t *__restrict__ sdesc, c
 __device__ __forceinline__ uint32_t slot_nz(uint32_t d) { return ~(d >> 16) & ((1u << ((d >> 24) & 7u)) - 1u); }
 
 template <typename XG>
-__device__ __forceinline__ void slot_gather(unsigned char *slot, const XG *__restrict__ xg, uint64_t pol) {
+__device__ __forceinline__ void slot_gather(const unsigned char *slot, const XG *__restrict__ xg, uint64_t pol,
+                                            XG (&xr)[MW_IPT]) {
     const int lane = threadIdx.x & 31;
     const uint32_t nz = slot_nz(((const uint32_t *)(slot + SlotTile::OFF_HDR))[4 + lane]);
     const int32_t *sc = (const int32_t *)(slot + SlotTile::OFF_COL) + lane;
-    XG *xb = (XG *)(slot + SlotTile::OFF_XB) + lane;
 #pragma unroll
-    for (int k = 0; k < MW_IPT; ++k)
-        if ((nz >> k) & 1u) cp_async_gather(xb + k * 32, xg + sc[k * 32], pol, 8);
-    cp_async_commit();
+    for (int k = 0; k < MW_IPT; ++k) {
+        xr[k] = XG{};
+        if ((nz >> k) & 1u) xr[k] = ldg_hint(xg + sc[k * 32], pol);
+    }
 }
 
 template <typename Acc, typename XG>
-__device__ __forceinline__ void slot_compute(int64_t t, unsigned char *slot, double *__restrict__ y,
-                                             int32_t *__restrict__ carry_row, double *__restrict__ carry_val,
-                                             double *__restrict__ head_val) {
+__device__ __forceinline__ void slot_compute(int64_t t, unsigned char *slot, const XG (&xr)[MW_IPT],
+                                             double *__restrict__ y, int32_t *__restrict__ carry_row,
+                                             double *__restrict__ carry_val, double *__restrict__ head_val) {
     using Op = typename Acc::Op;
     const int lane = threadIdx.x & 31;
     const uint32_t *hd = (const uint32_t *)(slot + SlotTile::OFF_HDR);
@@ -678,22 +696,18 @@ __device__ __forceinline__ void slot_compute(int64_t t, unsigned char *slot, dou
     const int istart = (int)(d & 0xFFu);
     const uint32_t bits = (d >> 16) & 0x7Fu, nz = slot_nz(d);
     const float2 *sv = (const float2 *)(slot + SlotTile::OFF_VAL) + lane;
-    const XG *xb = (const XG *)(slot + SlotTile::OFF_XB) + lane;
-    Op a[MW_IPT], xv[MW_IPT];
+    Op a[MW_IPT];
 #pragma unroll
-    for (int k = 0; k < MW_IPT; ++k) {
-        a[k] = SlotOps<Acc, XG>::a(sv[k * 32]);
-        xv[k] = xb[k * 32];
-    }
-    __syncwarp();   // the x buffer becomes the finished-row buffer
-    Acc *s_rows = (Acc *)(slot + SlotTile::OFF_XB);
+    for (int k = 0; k < MW_IPT; ++k) a[k] = SlotOps<Acc, XG>::a(sv[k * 32]);
+    __syncwarp();   // the value area becomes the finished-row buffer
+    Acc *s_rows = (Acc *)(slot + SlotTile::OFF_VAL);
     Acc acc;
     acc.zero();
     int i = istart;
 #pragma unroll
     for (int k = 0; k < MW_IPT; ++k) {
         if ((nz >> k) & 1u) {
-            acc.mad(a[k], xv[k]);
+            acc.mad(a[k], xr[k]);
         } else if ((bits >> k) & 1u) {   // row i ends here: stash it
             s_rows[i] = acc;
             acc.zero();
@@ -742,10 +756,39 @@ __device__ __forceinline__ void slot_compute(int64_t t, unsigned char *slot, dou
     for (int r = (cont ? 1 : 0) + lane; r < nrows; r += 32) y[i0 + r] = s_rows[r].template out<double>();
 }
 
-// Persistent warp over tiles w, w + W, ... with SLOT_STAGES slots: while tile k is computed,
-// the gathers of x for tile k+1 and the bulk copies of tiles k+2 .. k+SLOT_STAGES-1 are in
-// flight.
+// Persistent warp over tiles w, w + W, ... with two slots and two register sets: while tile
+// k is computed from slot k % 2 and register set k % 2, the gathers of tile k+1 are in
+// flight into the other register set and the bulk copies of tile k+2 are issued into slot
+// k % 2 as soon as it is free.
 constexpr int SLOT_STAGES = 2;
+
+template <int NW, typename Acc, typename XG>
+__device__ __forceinline__ bool slot_step(int64_t t, int64_t W, int64_t ntiles, int cs, uint32_t &parity,
+                                          unsigned char *wslots, const uint32_t *__restrict__ sdesc,
+                                          const int32_t *__restrict__ scol, const float2 *__restrict__ sval,
+                                          const XG *__restrict__ xg, double *__restrict__ y,
+                                          int32_t *__restrict__ carry_row, double *__restrict__ carry_val,
+                                          uint32_t *__restrict__ err, const XG (&xcur)[MW_IPT], XG (&xnext)[MW_IPT],
+                                          uint64_t stream_pol, uint64_t keep_pol) {
+    const int lane = threadIdx.x & 31;
+    const int ns = cs ^ 1;
+    unsigned char *cur = wslots + cs * SlotTile::BYTES, *nxt = wslots + ns * SlotTile::BYTES;
+    if (t + W < ntiles) {   // the next tile's copies have landed: start its gathers
+        if (!mbar_wait((uint64_t *)nxt, (parity >> ns) & 1u)) {
+            if (lane == 0) atomicOr(err, ST_TIMEOUT);
+            return false;
+        }
+        parity ^= 1u << ns;
+        slot_gather<XG>(nxt, xg, keep_pol, xnext);
+    }
+    slot_compute<Acc, XG>(t, cur, xcur, y, carry_row, carry_val, carry_val + ntiles);
+    // the finished rows were written through the generic proxy: order them before the
+    // bulk copy that refills the slot
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0 && t + SLOT_STAGES * W < ntiles) slot_issue(sdesc, scol, sval, t + SLOT_STAGES * W, cur, stream_pol);
+    return true;
+}
 
 template <int NW, typename Acc, typename XG>
 __device__ __forceinline__ void slot_run(int64_t ntiles, const uint32_t *__restrict__ sdesc,
@@ -776,38 +819,30 @@ __device__ __forceinline__ void slot_run(int64_t ntiles, const uint32_t *__restr
         return;
     }
     parity ^= 1u;
-    slot_gather<XG>(slot(0), xg, keep_pol);
-    int cs = 0;
-    for (; t < ntiles; t += W) {
-        const int ns = cs + 1 == SLOT_STAGES ? 0 : cs + 1;
-        if (t + W < ntiles) {   // the next tile's copies have landed: start its gathers
-            if (!mbar_wait(bar(ns), (parity >> ns) & 1u)) {
-                if (lane == 0) atomicOr(err, ST_TIMEOUT);
-                cp_async_wait<0>();
-                return;
-            }
-            parity ^= 1u << ns;
-            slot_gather<XG>(slot(ns), xg, keep_pol);
-            cp_async_wait<1>();   // this lane's gathers of tile t are complete
-        } else {
-            cp_async_wait<0>();
-        }
-        slot_compute<Acc, XG>(t, slot(cs), y, carry_row, carry_val, carry_val + ntiles);
-        __syncwarp();   // slot cs is free
-        if (lane == 0 && t + SLOT_STAGES * W < ntiles)
-            slot_issue(sdesc, scol, sval, t + SLOT_STAGES * W, slot(cs), stream_pol);
-        cs = ns;
+    XG xa[MW_IPT], xb[MW_IPT];
+    slot_gather<XG>(slot(0), xg, keep_pol, xa);
+    for (;;) {
+        if (!slot_step<NW, Acc, XG>(t, W, ntiles, 0, parity, wslots, sdesc, scol, sval, xg, y, carry_row, carry_val,
+                                    err, xa, xb, stream_pol, keep_pol))
+            return;
+        t += W;
+        if (t >= ntiles) return;
+        if (!slot_step<NW, Acc, XG>(t, W, ntiles, 1, parity, wslots, sdesc, scol, sval, xg, y, carry_row, carry_val,
+                                    err, xb, xa, stream_pol, keep_pol))
+            return;
+        t += W;
+        if (t >= ntiles) return;
     }
 }
 
 // SLOT_WARPS warps per CTA, SLOT_CTAS CTAs per SM: enough warps to cover the latencies,
-// and a carveout that leaves ~60 KB of the SM's on-chip memory to the L1 cache, where the
-// gathers of frequently used x entries hit (measured on R-MAT scale 22: 381 us with 60-92 KB
-// of L1 against 524 us with 28 KB).
+// and a carveout that leaves the rest of the SM's on-chip memory to the L1 cache, which
+// holds the gathers in flight and the frequently used x entries (measured on R-MAT scale
+// 22: 381 us with 60-92 KB of L1 against 524 us with 28 KB).
 // x2 holds x split per product; *xflag non-zero (some x outside the window) switches to
 // native FP64 on x with the values rebuilt from their pairs.
 constexpr int SLOT_WARPS = 4;
-constexpr int SLOT_CTAS = 5;
+constexpr int SLOT_CTAS = SLOT_CTAS_CFG;
 constexpr size_t SLOT_SMEM = (size_t)SLOT_WARPS * SLOT_STAGES * SlotTile::BYTES;
 
 __global__ __launch_bounds__(SLOT_WARPS * 32) void k_merge_slot_df(const uint32_t *__restrict__ sdesc,
