@@ -175,7 +175,7 @@ bool is_device_ptr(const void *p) {
 void free_all(spmv_matrix *h) {
     void *ptrs[] = {h->coo_row, h->coo_col, h->coo_val, h->row_ptr, h->col, h->val, h->bin_rows,
                     h->part_row, h->part_nz, h->carry_row, h->carry_val, h->merge_desc, h->hb_idx, h->hb_val,
-                    h->blk_ptr, h->blk_row, h->blk_col, h->hb_chunk_blk, h->xsplit, h->xsplit_flag, h->slot_desc, h->slot_col, h->slot_val2, h->fix_len, h->fix_long,
+                    h->blk_ptr, h->blk_row, h->blk_col, h->hb_chunk_blk, h->xsplit, h->xsplit_flag, h->slot_desc, h->slot_col, h->slot_val2, h->slot_val, h->fix_len, h->fix_long,
                     h->pr_inv, h->pr_z, h->pr_z2, h->pr_y, h->pr_part, h->status_dev};
     if (h->pr_graph) cudaGraphExecDestroy((cudaGraphExec_t)h->pr_graph);
     for (void *p : ptrs) dev_free(p);

@@ -164,6 +164,7 @@ struct spmv_matrix {
     uint32_t *slot_desc = nullptr;
     int32_t *slot_col = nullptr;
     float2 *slot_val2 = nullptr;      // FP64 values split into float pairs (when df_ok)
+    void *slot_val = nullptr;         // FP32 or bfloat16 values as stored
 
     // Hilbert-ordered blocked format
     bool has_hb = false;

@@ -338,6 +338,16 @@ __global__ void k_slot_fill(const int32_t *__restrict__ src, int64_t n, const in
     }
 }
 
+// FP32 / bfloat16 values in slot order (0 in row-end and tail slots)
+template <typename V>
+__global__ void k_slot_vals(const int32_t *__restrict__ src, int64_t n, const V *__restrict__ val,
+                            V *__restrict__ sval) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t j = src[i];
+    sval[i] = j >= 0 ? val[j] : V(0.f);
+}
+
 __global__ void k_merge_partition(const int32_t *__restrict__ row_ptr, int64_t m, int64_t nnz, int64_t tiles,
                                   int64_t tile_items, int32_t *__restrict__ part_row, int32_t *__restrict__ part_nz) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -694,31 +704,43 @@ spmv_status build_bins(spmv_matrix *h, cudaStream_t s) {
     return SPMV_OK;
 }
 
-// Lane-slotted copy of the merge tiles (column indices, and for FP64 matrices inside the
-// double-float window the split values).
+// Lane-slotted copy of the merge tiles: column indices, and the values (FP64 matrices inside
+// the double-float window: split into float pairs; FP32 and bfloat16: as stored).
 spmv_status build_slots(spmv_matrix *h, cudaStream_t s) {
     const int64_t tiles = h->tiles, slots = tiles * MERGE_WARP_ITEMS;
     if (h->dt == SPMV_F64) SPMV_TRY(build_df(h, s));
-    const bool vals = h->dt == SPMV_F64 && h->df_ok;
-    DevBuf sd(s), sc(s), sv(s), src(s);
+    const bool vals2 = h->dt == SPMV_F64 && h->df_ok;
+    const size_t vbytes = h->dt == SPMV_F32 ? 4 : h->dt == SPMV_BF16 ? 2 : 0;
+    DevBuf sd(s), sc(s), sv(s), sw(s), src(s);
     SPMV_TRY(sd.alloc((size_t)tiles * SLOT_DESC_WORDS * 4, "slot descriptors"));
     SPMV_TRY(sc.alloc((size_t)slots * 4, "slot columns"));
-    if (vals) SPMV_TRY(sv.alloc((size_t)slots * sizeof(float2), "slot values"));
+    if (vals2) SPMV_TRY(sv.alloc((size_t)slots * sizeof(float2), "slot values"));
+    if (vbytes) SPMV_TRY(sw.alloc((size_t)slots * vbytes, "slot values"));
     SPMV_TRY(src.alloc((size_t)slots * 4, "slot map"));
     SPMV_LAUNCH("k_merge_slots", s, (k_merge_slots<<<(unsigned)((tiles + 7) / 8), 256, 0, s>>>(
                                         h->row_ptr, h->part_row, h->part_nz, tiles, sd.as<uint32_t>(), src.as<int32_t>())));
     SPMV_LAUNCH_CHECK("merge slots");
     SPMV_LAUNCH("k_slot_fill", s, (k_slot_fill<<<grid_for(slots), CB, 0, s>>>(src.as<int32_t>(), slots, h->col,
-                                      (const double *)h->val, sc.as<int32_t>(), vals ? sv.as<float2>() : nullptr)));
+                                      (const double *)h->val, sc.as<int32_t>(), vals2 ? sv.as<float2>() : nullptr)));
     SPMV_LAUNCH_CHECK("slot fill");
+    if (h->dt == SPMV_F32)
+        SPMV_LAUNCH("k_slot_vals", s, (k_slot_vals<float><<<grid_for(slots), CB, 0, s>>>(
+                                          src.as<int32_t>(), slots, (const float *)h->val, sw.as<float>())));
+    else if (h->dt == SPMV_BF16)
+        SPMV_LAUNCH("k_slot_vals", s, (k_slot_vals<__nv_bfloat16><<<grid_for(slots), CB, 0, s>>>(
+                                          src.as<int32_t>(), slots, (const __nv_bfloat16 *)h->val,
+                                          sw.as<__nv_bfloat16>())));
+    SPMV_LAUNCH_CHECK("slot values");
     if (h->slot_desc) {
         dev_free_async(h->slot_desc, s); dev_free_async(h->slot_col, s);
         if (h->slot_val2) dev_free_async(h->slot_val2, s);
+        if (h->slot_val) dev_free_async(h->slot_val, s);
     }
     h->slot_desc = (uint32_t *)sd.release();
     h->slot_col = (int32_t *)sc.release();
-    h->slot_val2 = vals ? (float2 *)sv.release() : nullptr;
-    h->bytes += tiles * SLOT_DESC_WORDS * 4 + slots * (vals ? 12 : 4);
+    h->slot_val2 = vals2 ? (float2 *)sv.release() : nullptr;
+    h->slot_val = vbytes ? sw.release() : nullptr;
+    h->bytes += tiles * SLOT_DESC_WORDS * 4 + slots * (4 + (vals2 ? 8 : 0) + (int64_t)vbytes);
     return SPMV_OK;
 }
 

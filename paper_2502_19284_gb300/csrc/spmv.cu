@@ -614,36 +614,50 @@ __global__ __launch_bounds__(MW_WARPS * 32) void k_merge_warp_comp(const uint32_
 }
 
 // ---------------------------------------------------------------- lane-slotted warp tiles
-// FP64 product on the lane-slotted copy of the tiles (build_slots): path item k of lane l
-// sits in slot k * 32 + l, so every operand of a lane is at a fixed offset and the shared
-// memory accesses of a warp are contiguous.  A row end or tail slot holds value 0 and is
-// neither gathered nor accumulated.  Values are split into float pairs at the conversion.
-// The gathers of x go straight into registers; once a lane holds its values in registers
-// the value area takes the tile's finished rows.
+// Merge-path product on the lane-slotted copy of the tiles (build_slots): path item k of
+// lane l sits in slot k * 32 + l, so every operand of a lane is at a fixed offset and the
+// shared memory accesses of a warp are contiguous.  A row end or tail slot holds value 0 and
+// is neither gathered nor accumulated.  Stored values SV: FP64 split into float pairs at the
+// conversion (float2), FP32, bfloat16, or none (pattern).  The gathers of x go straight into
+// registers; once a lane holds its values in registers, the value area (grown to the row
+// buffer's size where that is larger) takes the tile's finished rows.
 #ifndef SLOT_CTAS_CFG
 #define SLOT_CTAS_CFG 6
 #endif
-struct SlotTile {
+template <typename SV, typename Acc>
+struct SlotT {
     static constexpr int OFF_HDR = 16;                                   // after the mbarrier
     static constexpr int OFF_COL = OFF_HDR + SLOT_DESC_WORDS * 4;
     static constexpr int OFF_VAL = OFF_COL + MW_ITEMS * 4;               // values, then finished rows
-    static constexpr int BYTES = OFF_VAL + MW_ITEMS * 8;
-    static constexpr uint32_t TX = SLOT_DESC_WORDS * 4 + MW_ITEMS * 12;   // bytes brought by TMA
+    static constexpr int VAL_BYTES = std::is_same<SV, Pattern>::value ? 0 : MW_ITEMS * (int)sizeof(SV);
+    static constexpr int ROW_BYTES = MW_ITEMS * (int)sizeof(Acc);
+    static constexpr int BYTES = OFF_VAL + ((VAL_BYTES > ROW_BYTES ? VAL_BYTES : ROW_BYTES) + 15) / 16 * 16;
+    static constexpr uint32_t TX = SLOT_DESC_WORDS * 4 + MW_ITEMS * 4 + VAL_BYTES;   // bytes brought by TMA
+    static_assert(OFF_VAL % 16 == 0 && OFF_COL % 16 == 0 && VAL_BYTES % 16 == 0, "16-byte bulk copies");
 };
-static_assert(SlotTile::BYTES % 16 == 0 && SlotTile::OFF_VAL % 16 == 0 && SlotTile::OFF_COL % 16 == 0, "16-byte slots");
 
-// Operand forms: double-float (values and x as float pairs), or native FP64 with the value
-// rebuilt from its pair (|a - hi - lo| <= 2^-48 |a|) when x is outside the double-float window.
-template <typename Acc, typename XG> struct SlotOps;
-template <> struct SlotOps<DfAcc, float2> {
-    __device__ __forceinline__ static float2 a(float2 v) { return v; }
-};
-template <> struct SlotOps<NativeAcc<double>, double> {
-    __device__ __forceinline__ static double a(float2 v) { return (double)v.x + (double)v.y; }
-};
-static_assert(sizeof(DfAcc) <= 8 && sizeof(NativeAcc<double>) <= 8, "finished rows fit the value area");
+// Operand from a stored value: double-float pairs as they are, or rebuilt as an FP64 value
+// (|a - hi - lo| <= 2^-48 |a|) when x is outside the double-float window; other types
+// converted to the accumulator's operand type.
+template <typename Acc, typename SV>
+__device__ __forceinline__ typename Acc::Op slot_a(const SV *sv, int k) {
+    using Op = typename Acc::Op;
+    if constexpr (std::is_same<SV, float2>::value) {
+        if constexpr (std::is_same<Op, float2>::value) return sv[k];
+        else return (double)sv[k].x + (double)sv[k].y;
+    } else if constexpr (std::is_same<Op, float2>::value) {   // pattern through double-float
+        return make_float2(1.f, 0.f);
+    } else {
+        return sval<SV, Op>(sv, k);
+    }
+}
 
-// read-only gather with an L2 policy
+// read-only gathers with an L2 policy
+__device__ __forceinline__ float ldg_hint(const float *p, uint64_t pol) {
+    float v;
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
 __device__ __forceinline__ float2 ldg_hint(const float2 *p, uint64_t pol) {
     float2 v;
     asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
@@ -655,26 +669,26 @@ __device__ __forceinline__ double ldg_hint(const double *p, uint64_t pol) {
     return v;
 }
 
+template <typename Slot, typename SV>
 __device__ __forceinline__ void slot_issue(const uint32_t *__restrict__ sdesc, const int32_t *__restrict__ scol,
-                                           const float2 *__restrict__ sval, int64_t t, unsigned char *slot,
-                                           uint64_t pol) {
+                                           const SV *__restrict__ sval, int64_t t, unsigned char *slot, uint64_t pol) {
     uint64_t *bar = (uint64_t *)slot;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(SlotTile::TX)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(Slot::TX)
                  : "memory");
-    tma_load_1d(slot + SlotTile::OFF_HDR, sdesc + t * SLOT_DESC_WORDS, SLOT_DESC_WORDS * 4, bar, pol);
-    tma_load_1d(slot + SlotTile::OFF_COL, scol + t * MW_ITEMS, MW_ITEMS * 4, bar, pol);
-    tma_load_1d(slot + SlotTile::OFF_VAL, sval + t * MW_ITEMS, MW_ITEMS * 8, bar, pol);
+    tma_load_1d(slot + Slot::OFF_HDR, sdesc + t * SLOT_DESC_WORDS, SLOT_DESC_WORDS * 4, bar, pol);
+    tma_load_1d(slot + Slot::OFF_COL, scol + t * MW_ITEMS, MW_ITEMS * 4, bar, pol);
+    if constexpr (Slot::VAL_BYTES > 0) tma_load_1d(slot + Slot::OFF_VAL, sval + t * MW_ITEMS, Slot::VAL_BYTES, bar, pol);
 }
 
 // nonzero items of a lane descriptor: not a row end and inside the lane's item count
 __device__ __forceinline__ uint32_t slot_nz(uint32_t d) { return ~(d >> 16) & ((1u << ((d >> 24) & 7u)) - 1u); }
 
-template <typename XG>
+template <typename Slot, typename XG>
 __device__ __forceinline__ void slot_gather(const unsigned char *slot, const XG *__restrict__ xg, uint64_t pol,
                                             XG (&xr)[MW_IPT]) {
     const int lane = threadIdx.x & 31;
-    const uint32_t nz = slot_nz(((const uint32_t *)(slot + SlotTile::OFF_HDR))[4 + lane]);
-    const int32_t *sc = (const int32_t *)(slot + SlotTile::OFF_COL) + lane;
+    const uint32_t nz = slot_nz(((const uint32_t *)(slot + Slot::OFF_HDR))[4 + lane]);
+    const int32_t *sc = (const int32_t *)(slot + Slot::OFF_COL) + lane;
 #pragma unroll
     for (int k = 0; k < MW_IPT; ++k) {
         xr[k] = XG{};
@@ -682,32 +696,32 @@ __device__ __forceinline__ void slot_gather(const unsigned char *slot, const XG 
     }
 }
 
-template <typename Acc, typename XG>
+template <typename Slot, typename Acc, typename SV, typename XG, typename YT>
 __device__ __forceinline__ void slot_compute(int64_t t, unsigned char *slot, const XG (&xr)[MW_IPT],
-                                             double *__restrict__ y, int32_t *__restrict__ carry_row,
+                                             YT *__restrict__ y, int32_t *__restrict__ carry_row,
                                              double *__restrict__ carry_val, double *__restrict__ head_val) {
     using Op = typename Acc::Op;
     const int lane = threadIdx.x & 31;
-    const uint32_t *hd = (const uint32_t *)(slot + SlotTile::OFF_HDR);
+    const uint32_t *hd = (const uint32_t *)(slot + Slot::OFF_HDR);
     const uint32_t d = hd[4 + lane];
     const int64_t i0 = (int32_t)hd[0];
     const int nrows = (int)hd[1];
     const bool cont = hd[2] != 0u;
     const int istart = (int)(d & 0xFFu);
     const uint32_t bits = (d >> 16) & 0x7Fu, nz = slot_nz(d);
-    const float2 *sv = (const float2 *)(slot + SlotTile::OFF_VAL) + lane;
+    const SV *sv = (const SV *)(slot + Slot::OFF_VAL) + lane;
     Op a[MW_IPT];
 #pragma unroll
-    for (int k = 0; k < MW_IPT; ++k) a[k] = SlotOps<Acc, XG>::a(sv[k * 32]);
+    for (int k = 0; k < MW_IPT; ++k) a[k] = slot_a<Acc, SV>(sv, k * 32);
     __syncwarp();   // the value area becomes the finished-row buffer
-    Acc *s_rows = (Acc *)(slot + SlotTile::OFF_VAL);
+    Acc *s_rows = (Acc *)(slot + Slot::OFF_VAL);
     Acc acc;
     acc.zero();
     int i = istart;
 #pragma unroll
     for (int k = 0; k < MW_IPT; ++k) {
         if ((nz >> k) & 1u) {
-            acc.mad(a[k], xr[k]);
+            acc.mad(a[k], Op(xr[k]));
         } else if ((bits >> k) & 1u) {   // row i ends here: stash it
             s_rows[i] = acc;
             acc.zero();
@@ -753,7 +767,7 @@ __device__ __forceinline__ void slot_compute(int64_t t, unsigned char *slot, con
             head_val[t] = dv;
         }
     }
-    for (int r = (cont ? 1 : 0) + lane; r < nrows; r += 32) y[i0 + r] = s_rows[r].template out<double>();
+    for (int r = (cont ? 1 : 0) + lane; r < nrows; r += 32) y[i0 + r] = s_rows[r].template out<YT>();
 }
 
 // Persistent warp over tiles w, w + W, ... with two slots and two register sets: while tile
@@ -762,46 +776,47 @@ __device__ __forceinline__ void slot_compute(int64_t t, unsigned char *slot, con
 // k % 2 as soon as it is free.
 constexpr int SLOT_STAGES = 2;
 
-template <int NW, typename Acc, typename XG>
+template <typename Slot, typename Acc, typename SV, typename XG, typename YT>
 __device__ __forceinline__ bool slot_step(int64_t t, int64_t W, int64_t ntiles, int cs, uint32_t &parity,
                                           unsigned char *wslots, const uint32_t *__restrict__ sdesc,
-                                          const int32_t *__restrict__ scol, const float2 *__restrict__ sval,
-                                          const XG *__restrict__ xg, double *__restrict__ y,
+                                          const int32_t *__restrict__ scol, const SV *__restrict__ sval,
+                                          const XG *__restrict__ xg, YT *__restrict__ y,
                                           int32_t *__restrict__ carry_row, double *__restrict__ carry_val,
                                           uint32_t *__restrict__ err, const XG (&xcur)[MW_IPT], XG (&xnext)[MW_IPT],
                                           uint64_t stream_pol, uint64_t keep_pol) {
     const int lane = threadIdx.x & 31;
     const int ns = cs ^ 1;
-    unsigned char *cur = wslots + cs * SlotTile::BYTES, *nxt = wslots + ns * SlotTile::BYTES;
+    unsigned char *cur = wslots + cs * Slot::BYTES, *nxt = wslots + ns * Slot::BYTES;
     if (t + W < ntiles) {   // the next tile's copies have landed: start its gathers
         if (!mbar_wait((uint64_t *)nxt, (parity >> ns) & 1u)) {
             if (lane == 0) atomicOr(err, ST_TIMEOUT);
             return false;
         }
         parity ^= 1u << ns;
-        slot_gather<XG>(nxt, xg, keep_pol, xnext);
+        slot_gather<Slot, XG>(nxt, xg, keep_pol, xnext);
     }
-    slot_compute<Acc, XG>(t, cur, xcur, y, carry_row, carry_val, carry_val + ntiles);
+    slot_compute<Slot, Acc, SV, XG, YT>(t, cur, xcur, y, carry_row, carry_val, carry_val + ntiles);
     // the finished rows were written through the generic proxy: order them before the
     // bulk copy that refills the slot
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncwarp();
-    if (lane == 0 && t + SLOT_STAGES * W < ntiles) slot_issue(sdesc, scol, sval, t + SLOT_STAGES * W, cur, stream_pol);
+    if (lane == 0 && t + SLOT_STAGES * W < ntiles) slot_issue<Slot, SV>(sdesc, scol, sval, t + SLOT_STAGES * W, cur, stream_pol);
     return true;
 }
 
-template <int NW, typename Acc, typename XG>
+template <int NW, typename Acc, typename SV, typename XG, typename YT>
 __device__ __forceinline__ void slot_run(int64_t ntiles, const uint32_t *__restrict__ sdesc,
-                                         const int32_t *__restrict__ scol, const float2 *__restrict__ sval,
-                                         const XG *__restrict__ xg, double *__restrict__ y,
+                                         const int32_t *__restrict__ scol, const SV *__restrict__ sval,
+                                         const XG *__restrict__ xg, YT *__restrict__ y,
                                          int32_t *__restrict__ carry_row, double *__restrict__ carry_val,
                                          uint32_t *__restrict__ err, unsigned char *wslots) {
+    using Slot = SlotT<SV, Acc>;
     const int lane = threadIdx.x & 31;
     const int64_t W = (int64_t)gridDim.x * NW;
     int64_t t = (int64_t)blockIdx.x * NW + (threadIdx.x >> 5);
     if (t >= ntiles) return;
-    auto slot = [&](int i) { return wslots + i * SlotTile::BYTES; };
-    auto bar = [&](int i) { return (uint64_t *)(wslots + i * SlotTile::BYTES); };
+    auto slot = [&](int i) { return wslots + i * Slot::BYTES; };
+    auto bar = [&](int i) { return (uint64_t *)(wslots + i * Slot::BYTES); };
     const uint64_t stream_pol = l2_policy_evict_first(), keep_pol = l2_policy_evict_last();
     if (lane == 0) {
 #pragma unroll
@@ -810,7 +825,7 @@ __device__ __forceinline__ void slot_run(int64_t ntiles, const uint32_t *__restr
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 #pragma unroll
         for (int i = 0; i < SLOT_STAGES; ++i)
-            if (t + i * W < ntiles) slot_issue(sdesc, scol, sval, t + i * W, slot(i), stream_pol);
+            if (t + i * W < ntiles) slot_issue<Slot, SV>(sdesc, scol, sval, t + i * W, slot(i), stream_pol);
     }
     __syncwarp();
     uint32_t parity = 0;   // bit i: phase parity of the next completion of slot i
@@ -820,15 +835,15 @@ __device__ __forceinline__ void slot_run(int64_t ntiles, const uint32_t *__restr
     }
     parity ^= 1u;
     XG xa[MW_IPT], xb[MW_IPT];
-    slot_gather<XG>(slot(0), xg, keep_pol, xa);
+    slot_gather<Slot, XG>(slot(0), xg, keep_pol, xa);
     for (;;) {
-        if (!slot_step<NW, Acc, XG>(t, W, ntiles, 0, parity, wslots, sdesc, scol, sval, xg, y, carry_row, carry_val,
-                                    err, xa, xb, stream_pol, keep_pol))
+        if (!slot_step<Slot, Acc, SV, XG, YT>(t, W, ntiles, 0, parity, wslots, sdesc, scol, sval, xg, y, carry_row,
+                                              carry_val, err, xa, xb, stream_pol, keep_pol))
             return;
         t += W;
         if (t >= ntiles) return;
-        if (!slot_step<NW, Acc, XG>(t, W, ntiles, 1, parity, wslots, sdesc, scol, sval, xg, y, carry_row, carry_val,
-                                    err, xb, xa, stream_pol, keep_pol))
+        if (!slot_step<Slot, Acc, SV, XG, YT>(t, W, ntiles, 1, parity, wslots, sdesc, scol, sval, xg, y, carry_row,
+                                              carry_val, err, xb, xa, stream_pol, keep_pol))
             return;
         t += W;
         if (t >= ntiles) return;
@@ -839,15 +854,18 @@ __device__ __forceinline__ void slot_run(int64_t ntiles, const uint32_t *__restr
 // and a carveout that leaves the rest of the SM's on-chip memory to the L1 cache, which
 // holds the gathers in flight and the frequently used x entries (measured on R-MAT scale
 // 22: 381 us with 60-92 KB of L1 against 524 us with 28 KB).
-// x2 holds x split per product; *xflag non-zero (some x outside the window) switches to
-// native FP64 on x with the values rebuilt from their pairs.
 constexpr int SLOT_WARPS = 4;
 constexpr int SLOT_CTAS = SLOT_CTAS_CFG;
-constexpr size_t SLOT_SMEM = (size_t)SLOT_WARPS * SLOT_STAGES * SlotTile::BYTES;
+template <typename SV, typename Acc>
+constexpr size_t slot_smem() { return (size_t)SLOT_WARPS * SLOT_STAGES * SlotT<SV, Acc>::BYTES; }
 
+// FP64 vector through double-float: x2 holds x split per product; *xflag non-zero (some x
+// outside the window) switches to native FP64 on x with the values rebuilt from their pairs.
+// SV = float2 (split FP64 values) or Pattern.
+template <typename SV>
 __global__ __launch_bounds__(SLOT_WARPS * 32) void k_merge_slot_df(const uint32_t *__restrict__ sdesc,
                                                                    const int32_t *__restrict__ scol,
-                                                                   const float2 *__restrict__ sval2,
+                                                                   const SV *__restrict__ sval2,
                                                                    const double *__restrict__ x,
                                                                    const float2 *__restrict__ x2,
                                                                    const uint32_t *__restrict__ xflag,
@@ -856,12 +874,29 @@ __global__ __launch_bounds__(SLOT_WARPS * 32) void k_merge_slot_df(const uint32_
                                                                    double *__restrict__ carry_val, int64_t ntiles,
                                                                    uint32_t *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned char *ws = smem_raw + (threadIdx.x >> 5) * SLOT_STAGES * SlotTile::BYTES;
+    static_assert(SlotT<SV, DfAcc>::BYTES == SlotT<SV, NativeAcc<double>>::BYTES, "one slot size for both forms");
+    unsigned char *ws = smem_raw + (threadIdx.x >> 5) * SLOT_STAGES * SlotT<SV, DfAcc>::BYTES;
     if (*xflag == 0u)
-        slot_run<SLOT_WARPS, DfAcc, float2>(ntiles, sdesc, scol, sval2, x2, y, carry_row, carry_val, err, ws);
+        slot_run<SLOT_WARPS, DfAcc, SV, float2, double>(ntiles, sdesc, scol, sval2, x2, y, carry_row, carry_val, err,
+                                                        ws);
     else
-        slot_run<SLOT_WARPS, NativeAcc<double>, double>(ntiles, sdesc, scol, sval2, x, y, carry_row, carry_val,
-                                                        err, ws);
+        slot_run<SLOT_WARPS, NativeAcc<double>, SV, double, double>(ntiles, sdesc, scol, sval2, x, y, carry_row,
+                                                                    carry_val, err, ws);
+}
+
+// FP32 vectors: FP32, bfloat16 or pattern values with any accumulator (FP32, compensated,
+// compensated in the segmented reduction only, or FP64).
+template <typename SV, typename Acc>
+__global__ __launch_bounds__(SLOT_WARPS * 32) void k_merge_slot(const uint32_t *__restrict__ sdesc,
+                                                                const int32_t *__restrict__ scol,
+                                                                const SV *__restrict__ sval,
+                                                                const float *__restrict__ x, float *__restrict__ y,
+                                                                int32_t *__restrict__ carry_row,
+                                                                double *__restrict__ carry_val, int64_t ntiles,
+                                                                uint32_t *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *ws = smem_raw + (threadIdx.x >> 5) * SLOT_STAGES * SlotT<SV, Acc>::BYTES;
+    slot_run<SLOT_WARPS, Acc, SV, float, float>(ntiles, sdesc, scol, sval, x, y, carry_row, carry_val, err, ws);
 }
 
 // Pattern matrix (every stored value 1) with an FP64 vector through double-float: the value
@@ -1003,6 +1038,30 @@ constexpr size_t merge_smem(int ipt) {
     return (size_t)MP_BLOCK * ipt * (sizeof(Acc) + 4) + (MP_BLOCK + 32) * 4 + (MP_BLOCK + 32) * sizeof(Acc);
 }
 
+// Slotted product for FP32 vectors (values FP32, bfloat16 or pattern).
+template <typename SV, typename Acc>
+spmv_status launch_slot(const spmv_matrix *h, const void *x, void *y, cudaStream_t s) {
+    constexpr size_t smem = slot_smem<SV, Acc>();
+    static bool attr = false;
+    if (!attr) {
+        SPMV_TRY(set_smem_ctas((const void *)k_merge_slot<SV, Acc>, smem, SLOT_CTAS));
+        attr = true;
+    }
+    const unsigned grid = persistent_grid((const void *)k_merge_slot<SV, Acc>, SLOT_WARPS * 32, smem, h->tiles);
+    SPMV_LAUNCH("k_merge_spmv", s, (k_merge_slot<SV, Acc><<<grid, SLOT_WARPS * 32, smem, s>>>(
+                                       h->slot_desc, h->slot_col, (const SV *)h->slot_val, (const float *)x, (float *)y,
+                                       h->carry_row, h->carry_val, h->tiles, h->status_dev + 3)));
+    SPMV_LAUNCH_CHECK("merge spmv");
+    SPMV_TRY(launch_fixup<float>(h, (float *)y, s));
+    return SPMV_OK;
+}
+
+// the slotted copy holds this matrix's values (or it needs none)
+template <typename VT>
+bool has_slot_vals(const spmv_matrix *h) {
+    return h->slot_desc && (std::is_same<VT, Pattern>::value || h->slot_val);
+}
+
 template <typename VT, typename XT, typename AT, int IPT>
 spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allow_df, cudaStream_t s) {
     constexpr bool FP64 = std::is_same<VT, double>::value && std::is_same<XT, double>::value &&
@@ -1010,12 +1069,13 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
     constexpr size_t smem = (size_t)MW_WARPS * 2 * WarpSlot<VT>::BYTES;
     if constexpr (FP64) {
         if (allow_df && h->df_ok && h->xsplit && h->slot_val2) {
+            constexpr size_t ssmem = slot_smem<float2, DfAcc>();
             static bool attr = false;
             if (!attr) {
-                SPMV_TRY(set_smem_ctas((const void *)k_merge_slot_df, SLOT_SMEM, SLOT_CTAS));
+                SPMV_TRY(set_smem_ctas((const void *)k_merge_slot_df<float2>, ssmem, SLOT_CTAS));
                 attr = true;
             }
-            const unsigned grid = persistent_grid((const void *)k_merge_slot_df, SLOT_WARPS * 32, SLOT_SMEM, h->tiles);
+            const unsigned grid = persistent_grid((const void *)k_merge_slot_df<float2>, SLOT_WARPS * 32, ssmem, h->tiles);
             SPMV_CUDA_TRY(cudaMemsetAsync(h->xsplit_flag, 0, 4, s));
             if (h->n > 0) {
                 SPMV_LAUNCH("k_df_split_x", s,
@@ -1024,7 +1084,7 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
                 SPMV_LAUNCH_CHECK("x split");
             }
             SPMV_LAUNCH("k_merge_spmv", s,
-                        (k_merge_slot_df<<<grid, SLOT_WARPS * 32, SLOT_SMEM, s>>>(
+                        (k_merge_slot_df<float2><<<grid, SLOT_WARPS * 32, ssmem, s>>>(
                             h->slot_desc, h->slot_col, h->slot_val2, (const double *)x, h->xsplit, h->xsplit_flag,
                             (double *)y, h->carry_row, h->carry_val, h->tiles, h->status_dev + 3)));
             SPMV_LAUNCH_CHECK("merge spmv");
@@ -1032,6 +1092,8 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
             return SPMV_OK;
         }
     }
+    if constexpr (std::is_same<XT, float>::value && !std::is_same<VT, double>::value)
+        if (has_slot_vals<VT>(h)) return launch_slot<VT, NativeAcc<AT>>(h, x, y, s);
     static bool attr = false;
     if (!attr) {
         SPMV_TRY(set_smem_ctas((const void *)k_merge_warp<VT, XT, AT>, smem, 5));
@@ -1248,6 +1310,7 @@ enum Algo { MERGE, ROWSPLIT, HB };
 
 template <typename VT, typename Acc>
 spmv_status launch_merge_comp(const spmv_matrix *h, const void *x, void *y, cudaStream_t s) {
+    if (has_slot_vals<VT>(h)) return launch_slot<VT, Acc>(h, x, y, s);
     constexpr size_t smem = (size_t)MW_WARPS * 2 * WarpSlot<VT>::BYTES;
     static bool attr = false;
     if (!attr) {
@@ -1406,6 +1469,21 @@ spmv_status mul_csr_merge_noalloc(int64_t m, int64_t n, int64_t nnz, const int32
 
 spmv_status mul_merge_pattern_split(const spmv_matrix *h, const double *x, const float2 *x2, const uint32_t *xflag,
                                     double *y, cudaStream_t s) {
+    if (h->slot_desc) {
+        constexpr size_t ssmem = slot_smem<Pattern, DfAcc>();
+        static bool sattr = false;
+        if (!sattr) {
+            SPMV_TRY(set_smem_ctas((const void *)k_merge_slot_df<Pattern>, ssmem, SLOT_CTAS));
+            sattr = true;
+        }
+        const unsigned grid = persistent_grid((const void *)k_merge_slot_df<Pattern>, SLOT_WARPS * 32, ssmem, h->tiles);
+        SPMV_LAUNCH("k_merge_spmv", s, (k_merge_slot_df<Pattern><<<grid, SLOT_WARPS * 32, ssmem, s>>>(
+                                           h->slot_desc, h->slot_col, (const Pattern *)nullptr, x, x2, xflag, y,
+                                           h->carry_row, h->carry_val, h->tiles, h->status_dev + 3)));
+        SPMV_LAUNCH_CHECK("pattern merge spmv");
+        SPMV_TRY(launch_fixup<double>(h, y, s));
+        return SPMV_OK;
+    }
     constexpr size_t smem = (size_t)MW_WARPS * 2 * WarpSlot<Pattern>::BYTES;
     static bool attr = false;
     if (!attr) {
