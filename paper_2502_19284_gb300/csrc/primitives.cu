@@ -67,16 +67,20 @@ __global__ __launch_bounds__(SCAN_BLOCK) void k_scan_reduce(const uint32_t *__re
     }
 }
 
-// Exclusive scan of one tile, plus the tile's offset from the scanned partials.
+// Exclusive scan of one tile, plus the tile's offset from the scanned partials.  The tile is
+// staged in shared memory with one padding word per 32 (thread-contiguous runs of SCAN_IPT
+// words then fall on distinct banks).
+__device__ __forceinline__ int scan_pad(int i) { return i + (i >> 5); }
+
 __global__ __launch_bounds__(SCAN_BLOCK) void k_scan_down(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
                                                           int64_t n, const uint32_t *__restrict__ offsets) {
-    __shared__ uint32_t tile[SCAN_TILE];
+    __shared__ uint32_t tile[SCAN_TILE + SCAN_TILE / 32];
     __shared__ uint32_t tot;
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
 #pragma unroll
     for (int j = 0; j < SCAN_IPT; ++j) {
         int64_t i = base + (int64_t)j * SCAN_BLOCK + threadIdx.x;
-        tile[j * SCAN_BLOCK + threadIdx.x] = i < n ? in[i] : 0u;
+        tile[scan_pad(j * SCAN_BLOCK + threadIdx.x)] = i < n ? in[i] : 0u;
     }
     __syncthreads();
     uint32_t loc[SCAN_IPT];
@@ -84,16 +88,16 @@ __global__ __launch_bounds__(SCAN_BLOCK) void k_scan_down(const uint32_t *__rest
 #pragma unroll
     for (int j = 0; j < SCAN_IPT; ++j) {
         loc[j] = s;
-        s += tile[threadIdx.x * SCAN_IPT + j];
+        s += tile[scan_pad(threadIdx.x * SCAN_IPT + j)];
     }
     uint32_t off = block_exclusive_scan(s, &tot) + (offsets ? offsets[blockIdx.x] : 0u);
 #pragma unroll
-    for (int j = 0; j < SCAN_IPT; ++j) tile[threadIdx.x * SCAN_IPT + j] = loc[j] + off;
+    for (int j = 0; j < SCAN_IPT; ++j) tile[scan_pad(threadIdx.x * SCAN_IPT + j)] = loc[j] + off;
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < SCAN_IPT; ++j) {
         int64_t i = base + (int64_t)j * SCAN_BLOCK + threadIdx.x;
-        if (i < n) out[i] = tile[j * SCAN_BLOCK + threadIdx.x];
+        if (i < n) out[i] = tile[scan_pad(j * SCAN_BLOCK + threadIdx.x)];
     }
 }
 
