@@ -111,7 +111,8 @@ spmv_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, voi
 size_t radix_temp_bytes(int64_t n);
 spmv_status radix_sort_pairs(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
                              int begin_bit, int end_bit, void *temp, cudaStream_t s, bool *in_alt,
-                             uint32_t *err = nullptr);   // err: status word for a timed-out wait
+                             uint32_t *err = nullptr);   // err: a zeroed status word; a timed-out wait
+                                                         // sets ST_TIMEOUT in it
 
 // Hilbert index of (r, c) on the 2^K grid (device function lives in hilbert.cuh).
 spmv_status launch_hilbert_keys(int K, int64_t n, const int32_t *rows, const int32_t *cols, uint64_t *keys,

@@ -514,10 +514,27 @@ __global__ void k_df_window(const double *__restrict__ v, int64_t n, uint32_t *_
 
 // ---------------------------------------------------------------- helpers
 spmv_status read_status(spmv_matrix *h, cudaStream_t s, uint32_t *out) {
-    SPMV_CUDA_TRY(cudaMemcpyAsync(h->status_host, h->status_dev, 4, cudaMemcpyDeviceToHost, s));
+    SPMV_CUDA_TRY(cudaMemcpyAsync(h->status_host, h->status_dev, 8, cudaMemcpyDeviceToHost, s));   // words 0 and 1
     SPMV_CUDA_TRY(cudaStreamSynchronize(s));
     *out = *h->status_host;
     return SPMV_OK;
+}
+
+// Word 1 of the handle's status: set (ST_TIMEOUT) by a radix sort whose bounded waits gave
+// up.  sort_begin zeroes it before a sort; sort_failed reads the host copy that the next
+// synchronising read brought back.
+spmv_status sort_begin(spmv_matrix *h, cudaStream_t s) {
+    SPMV_CUDA_TRY(cudaMemsetAsync(h->status_dev + 1, 0, 4, s));
+    return SPMV_OK;
+}
+spmv_status sort_fetch(spmv_matrix *h, cudaStream_t s) {
+    SPMV_CUDA_TRY(cudaMemcpyAsync(h->status_host + 1, h->status_dev + 1, 4, cudaMemcpyDeviceToHost, s));
+    return SPMV_OK;
+}
+bool sort_failed(const spmv_matrix *h) {
+    if (!(h->status_host[1] & ST_TIMEOUT)) return false;
+    set_error("spmv_convert: a bounded wait of the radix sort gave up");
+    return true;
 }
 
 template <typename T>
@@ -589,8 +606,9 @@ spmv_status build_csr(spmv_matrix *h, cudaStream_t s) {
                                                 perm.as<uint32_t>())));
         SPMV_LAUNCH_CHECK("coo keys");
         bool alt = false;
+        SPMV_TRY(sort_begin(h, s));
         SPMV_TRY(radix_sort_pairs(keys.as<uint64_t>(), keys_alt.as<uint64_t>(), perm.as<uint32_t>(),
-                                  perm_alt.as<uint32_t>(), nnz, 0, cbits + rbits, tmp.p, s, &alt));
+                                  perm_alt.as<uint32_t>(), nnz, 0, cbits + rbits, tmp.p, s, &alt, h->status_dev + 1));
         uint64_t *K = alt ? keys_alt.as<uint64_t>() : keys.as<uint64_t>();
         uint32_t *P = alt ? perm_alt.as<uint32_t>() : perm.as<uint32_t>();
         uint64_t *Kspare = alt ? keys.as<uint64_t>() : keys_alt.as<uint64_t>();
@@ -600,6 +618,7 @@ spmv_status build_csr(spmv_matrix *h, cudaStream_t s) {
         SPMV_LAUNCH_CHECK("heads");
         uint32_t stw = 0;
         SPMV_TRY(read_status(h, s, &stw));
+        if (sort_failed(h)) return SPMV_ERR_TIMEOUT;
         uint64_t *rowkeys = K;
         if (stw & ST_DUPLICATE) {
             if (h->flags & SPMV_DUP_ERROR) {
@@ -689,12 +708,15 @@ spmv_status build_bins(spmv_matrix *h, cudaStream_t s) {
                                            counts.as<unsigned long long>(), counts.as<unsigned long long>() + 8)));
     SPMV_LAUNCH_CHECK("row class");
     bool alt = false;
+    SPMV_TRY(sort_begin(h, s));
     SPMV_TRY(radix_sort_pairs(cls.as<uint64_t>(), cls_alt.as<uint64_t>(), rows.as<uint32_t>(), rows_alt.as<uint32_t>(),
-                              m, 0, 3, tmp.p, s, &alt));
+                              m, 0, 3, tmp.p, s, &alt, h->status_dev + 1));
     SPMV_CUDA_TRY(cudaMemcpyAsync(bin_rows.p, alt ? rows_alt.p : rows.p, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
     unsigned long long hc[16];
     SPMV_CUDA_TRY(cudaMemcpyAsync(hc, counts.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    SPMV_TRY(sort_fetch(h, s));
     SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+    if (sort_failed(h)) return SPMV_ERR_TIMEOUT;
     for (int c = 0; c < 8; ++c) h->bin_count[c] = (int64_t)hc[c];
     h->max_row_len = (int64_t)hc[8];
     if (h->bin_rows) dev_free_async(h->bin_rows, s);
@@ -838,8 +860,9 @@ spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s) {
                                                                              keys.as<uint64_t>(), perm.as<uint32_t>())));
         SPMV_LAUNCH_CHECK("hb keys");
         bool alt = false;
+        SPMV_TRY(sort_begin(h, s));
         SPMV_TRY(radix_sort_pairs(keys.as<uint64_t>(), keys_alt.as<uint64_t>(), perm.as<uint32_t>(),
-                                  perm_alt.as<uint32_t>(), nnz, 0, 2 * K, tmp.p, s, &alt));
+                                  perm_alt.as<uint32_t>(), nnz, 0, 2 * K, tmp.p, s, &alt, h->status_dev + 1));
         uint64_t *Ks = alt ? keys_alt.as<uint64_t>() : keys.as<uint64_t>();
         uint32_t *Ps = alt ? perm_alt.as<uint32_t>() : perm.as<uint32_t>();
         SPMV_LAUNCH("k_hb_fill", s, (k_hb_fill<<<grid_for((nnz + HB_FILL_U - 1) / HB_FILL_U), CB, 0, s>>>(Ks, nnz, K, log2b, inner, idx.as<uint32_t>(), head.as<uint32_t>())));
@@ -849,7 +872,9 @@ spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s) {
         uint32_t last[2] = {0, 0};
         SPMV_CUDA_TRY(cudaMemcpyAsync(&last[0], bid.as<uint32_t>() + nnz - 1, 4, cudaMemcpyDeviceToHost, s));
         SPMV_CUDA_TRY(cudaMemcpyAsync(&last[1], head.as<uint32_t>() + nnz - 1, 4, cudaMemcpyDeviceToHost, s));
+        SPMV_TRY(sort_fetch(h, s));
         SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+        if (sort_failed(h)) return SPMV_ERR_TIMEOUT;
         nblk = (int64_t)last[0] + last[1];
         SPMV_TRY(bptr.alloc((size_t)(nblk + 1) * 4, "hb blk_ptr"));
         SPMV_TRY(brow.alloc((size_t)nblk * 4, "hb blk_row"));
