@@ -76,6 +76,10 @@ struct DevBuf {
     spmv_status alloc(size_t bytes, const char *what) { return dev_alloc(&p, bytes < 16 ? 16 : bytes, what, s); }
     template <typename T> T *as() const { return (T *)p; }
     void *release() { void *q = p; p = nullptr; return q; }
+    void reset() {
+        if (p) dev_free_async(p, s);
+        p = nullptr;
+    }
 };
 
 // Device status word bits (written by kernels with atomicOr).

@@ -91,11 +91,6 @@ __global__ void k_gather(const T *__restrict__ src, const uint32_t *__restrict__
     }
 }
 
-__global__ void k_key_cols(const uint64_t *__restrict__ keys, int64_t n, int cbits, int32_t *__restrict__ col) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) col[i] = (int32_t)(keys[i] & ((1ull << cbits) - 1ull));
-}
-
 __device__ __forceinline__ double load_as_double(const void *v, int dt, int64_t i) {
     if (dt == SPMV_F64) return ((const double *)v)[i];
     if (dt == SPMV_F32) return (double)((const float *)v)[i];
@@ -131,21 +126,35 @@ __global__ void k_dup_compact(const uint64_t *__restrict__ keys, const uint32_t 
 // Gaps longer than GAP_INLINE rows are queued for k_fill_gaps.
 constexpr int GAP_INLINE = 64;
 
+// row_ptr from sorted keys: entry i (0 <= i <= nnz) gives value i to the rows between the
+// row of key i-1 (exclusive) and the row of key i; runs longer than GAP_INLINE rows (empty
+// rows) are recorded for k_fill_gaps.  With col != nullptr it also writes the column of
+// every key and flags equal neighbouring keys (ST_DUPLICATE), the whole finish of a
+// conversion without duplicates in one read of the keys.
 __global__ void k_row_ptr_fill(const uint64_t *__restrict__ keys, int64_t nnz, int cbits, int64_t m,
                                int32_t *__restrict__ row_ptr, int64_t *__restrict__ gaps,
-                               unsigned long long *__restrict__ ngaps) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i > nnz) return;
-    int64_t hi = i < nnz ? (int64_t)(keys[i] >> cbits) : m;
-    int64_t lo = i > 0 ? (int64_t)(keys[i - 1] >> cbits) + 1 : 0;   // rows lo..hi get value i
-    if (hi - lo + 1 <= GAP_INLINE) {
-        for (int64_t r = lo; r <= hi; ++r) row_ptr[r] = (int32_t)i;
-    } else {
-        unsigned long long g = atomicAdd(ngaps, 1ull);
-        gaps[3 * g + 0] = lo;
-        gaps[3 * g + 1] = hi;
-        gaps[3 * g + 2] = i;
+                               unsigned long long *__restrict__ ngaps, int32_t *__restrict__ col,
+                               uint32_t *__restrict__ status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool dup = false;
+    if (i <= nnz) {
+        const uint64_t kc = i < nnz ? keys[i] : 0ull, kp = i > 0 ? keys[i - 1] : 0ull;
+        if (col && i < nnz) {
+            col[i] = (int32_t)(kc & ((1ull << cbits) - 1ull));
+            dup = i > 0 && kc == kp;
+        }
+        const int64_t hi = i < nnz ? (int64_t)(kc >> cbits) : m;
+        const int64_t lo = i > 0 ? (int64_t)(kp >> cbits) + 1 : 0;   // rows lo..hi get value i
+        if (hi - lo + 1 <= GAP_INLINE) {
+            for (int64_t r = lo; r <= hi; ++r) row_ptr[r] = (int32_t)i;
+        } else {
+            const unsigned long long g = atomicAdd(ngaps, 1ull);
+            gaps[3 * g + 0] = lo;
+            gaps[3 * g + 1] = hi;
+            gaps[3 * g + 2] = i;
+        }
     }
+    if (col && __any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) atomicOr(status, ST_DUPLICATE);
 }
 
 __global__ void k_fill_gaps(const int64_t *__restrict__ gaps, const unsigned long long *__restrict__ ngaps,
@@ -159,27 +168,42 @@ __global__ void k_fill_gaps(const int64_t *__restrict__ gaps, const unsigned lon
 }
 
 // ---------------------------------------------------------------- row-length bins
+// Row-length class of every row (key) with the row id (payload), the rows per class and the
+// longest row.  Grid-stride with per-warp ballots and per-block totals, so that only a few
+// thousand global atomics meet on the nine counters.
+constexpr int ROW_CLASS_GRID = 1024;
 __global__ void k_row_class(const int32_t *__restrict__ row_ptr, int64_t m, uint64_t *__restrict__ cls,
                             uint32_t *__restrict__ rows, unsigned long long *__restrict__ counts,
                             unsigned long long *__restrict__ maxlen) {
-    __shared__ unsigned long long sc[NUM_ROW_CLASSES];
-    if (threadIdx.x < NUM_ROW_CLASSES) sc[threadIdx.x] = 0;
+    __shared__ uint32_t sc[NUM_ROW_CLASSES];
+    __shared__ unsigned long long smax;
+    if (threadIdx.x < NUM_ROW_CLASSES) sc[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) smax = 0ull;
     __syncthreads();
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long len = 0;
-    if (i < m) {
-        len = (unsigned long long)(row_ptr[i + 1] - row_ptr[i]);
-        int c = row_class(len);
-        cls[i] = (uint64_t)c;
-        rows[i] = (uint32_t)i;
-        atomicAdd(&sc[c], 1ull);
+    const int lane = threadIdx.x & 31;
+    unsigned long long mx = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < m; i0 += stride) {   // warp-uniform trip count
+        const int64_t i = i0 + threadIdx.x;
+        int c = -1;
+        if (i < m) {
+            const unsigned long long len = (unsigned long long)(row_ptr[i + 1] - row_ptr[i]);
+            c = row_class(len);
+            cls[i] = (uint64_t)c;
+            rows[i] = (uint32_t)i;
+            mx = max(mx, len);
+        }
+#pragma unroll
+        for (int q = 0; q < NUM_ROW_CLASSES; ++q) {
+            const uint32_t bq = __ballot_sync(0xffffffffu, c == q);
+            if (lane == 0 && bq) atomicAdd(&sc[q], (uint32_t)__popc(bq));
+        }
     }
-    // block max of the row length
-    unsigned long long mx = len;
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0 && mx) atomicMax(maxlen, mx);
+    if (lane == 0 && mx) atomicMax(&smax, mx);
     __syncthreads();
-    if (threadIdx.x < NUM_ROW_CLASSES && sc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sc[threadIdx.x]);
+    if (threadIdx.x < NUM_ROW_CLASSES && sc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], (unsigned long long)sc[threadIdx.x]);
+    if (threadIdx.x == 0 && smax) atomicMax(maxlen, smax);
 }
 
 // ---------------------------------------------------------------- merge partition
@@ -237,9 +261,14 @@ __global__ void k_merge_desc(const int32_t *__restrict__ row_ptr, const int32_t 
 // Lane-slotted layout of the warp tiles: one warp per tile writes the tile's header and
 // lane descriptors (same fields as k_merge_desc) and, for every slot k * 32 + lane, the CRS
 // index of the nonzero at path item k of the lane, or -1 for a row end or a tail slot.
+// Slot values: none (pattern, or FP64 outside the double-float window), FP64 split into
+// float pairs, FP32 or bfloat16 as stored.
+enum SlotVals { SLOT_NONE = 0, SLOT_DF = 1, SLOT_F32 = 2, SLOT_BF16 = 3 };
+
 __global__ void k_merge_slots(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ part_row,
                               const int32_t *__restrict__ part_nz, int64_t tiles, uint32_t *__restrict__ sdesc,
-                              int32_t *__restrict__ src) {
+                              const int32_t *__restrict__ col, const void *__restrict__ val, int vals,
+                              int32_t *__restrict__ scol, void *__restrict__ sval) {
     __shared__ uint32_t s_bits[8][8];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t t = (int64_t)blockIdx.x * 8 + w;
@@ -269,14 +298,27 @@ __global__ void k_merge_slots(const int32_t *__restrict__ row_ptr, const int32_t
         hd[lane] = lane == 0 ? (uint32_t)i0 : lane == 1 ? (uint32_t)nrows : lane == 2 ? cont : 0u;
         hd[36 + lane] = 0u;
     }
-    // nonzero index of path item d0 + k: j0 + (d0 + k) - (row ends before it)
+    // nonzero index of path item d0 + k: j0 + (d0 + k) - (row ends before it); a row end or a
+    // tail slot holds column 0 and value 0
     int ends = before;
-    int32_t *out = src + t * MERGE_WARP_ITEMS + lane;
+    const int64_t o = t * MERGE_WARP_ITEMS + lane;
 #pragma unroll
     for (int k = 0; k < MERGE_WARP_IPT; ++k) {
         const bool in = k < d1 - d0;
         const bool end = in && ((bits >> k) & 1u);
-        out[k * 32] = (in && !end) ? (int32_t)(j0 + d0 + k - ends) : -1;
+        const bool nzk = in && !end;
+        const int64_t j = j0 + d0 + k - ends;
+        const int64_t q = o + k * 32;
+        scol[q] = nzk ? col[j] : 0;
+        if (vals == SLOT_DF) {
+            float2 r = make_float2(0.f, 0.f);
+            if (nzk) df_split(((const double *)val)[j], &r.x, &r.y);
+            ((float2 *)sval)[q] = r;
+        } else if (vals == SLOT_F32) {
+            ((float *)sval)[q] = nzk ? ((const float *)val)[j] : 0.f;
+        } else if (vals == SLOT_BF16) {
+            ((__nv_bfloat16 *)sval)[q] = nzk ? ((const __nv_bfloat16 *)val)[j] : __float2bfloat16(0.f);
+        }
         ends += end ? 1 : 0;
     }
 }
@@ -322,30 +364,6 @@ __global__ void k_hb_chunks(const int32_t *__restrict__ blk_ptr, int64_t nblk, i
         else hi = mid - 1;
     }
     chunk_blk[c] = (int32_t)lo;
-}
-
-// slot arrays from the CRS arrays through the slot -> CRS index map
-__global__ void k_slot_fill(const int32_t *__restrict__ src, int64_t n, const int32_t *__restrict__ col,
-                            const double *__restrict__ val, int32_t *__restrict__ scol, float2 *__restrict__ sval2) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int32_t j = src[i];
-    scol[i] = j >= 0 ? col[j] : 0;
-    if (sval2) {
-        float2 r = make_float2(0.f, 0.f);
-        if (j >= 0) df_split(val[j], &r.x, &r.y);
-        sval2[i] = r;
-    }
-}
-
-// FP32 / bfloat16 values in slot order (0 in row-end and tail slots)
-template <typename V>
-__global__ void k_slot_vals(const int32_t *__restrict__ src, int64_t n, const V *__restrict__ val,
-                            V *__restrict__ sval) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int32_t j = src[i];
-    sval[i] = j >= 0 ? val[j] : V(0.f);
 }
 
 __global__ void k_merge_partition(const int32_t *__restrict__ row_ptr, int64_t m, int64_t nnz, int64_t tiles,
@@ -553,14 +571,15 @@ spmv_status gather_values(const void *src, spmv_dtype dt, const uint32_t *perm, 
     return SPMV_OK;
 }
 
-spmv_status fill_row_ptr(const uint64_t *keys, int64_t nnz, int cbits, int64_t m, int32_t *row_ptr, cudaStream_t s) {
+spmv_status fill_row_ptr(const uint64_t *keys, int64_t nnz, int cbits, int64_t m, int32_t *row_ptr, cudaStream_t s,
+                         int32_t *col = nullptr, uint32_t *status = nullptr) {
     DevBuf gaps(s), ngaps(s);
     int64_t cap = (m + 1) / GAP_INLINE + 2;
     SPMV_TRY(gaps.alloc((size_t)cap * 3 * sizeof(int64_t), "row_ptr gaps"));
     SPMV_TRY(ngaps.alloc(sizeof(unsigned long long), "row_ptr gap count"));
     SPMV_CUDA_TRY(cudaMemsetAsync(ngaps.p, 0, sizeof(unsigned long long), s));
     SPMV_LAUNCH("k_row_ptr_fill", s, (k_row_ptr_fill<<<grid_for(nnz + 1), CB, 0, s>>>(keys, nnz, cbits, m, row_ptr, gaps.as<int64_t>(),
-                                                    ngaps.as<unsigned long long>())));
+                                                    ngaps.as<unsigned long long>(), col, status)));
     SPMV_LAUNCH_CHECK("row_ptr fill");
     SPMV_LAUNCH("k_fill_gaps", s, (k_fill_gaps<<<1184, CB, 0, s>>>(gaps.as<int64_t>(), ngaps.as<unsigned long long>(), row_ptr)));
     SPMV_LAUNCH_CHECK("row_ptr gaps");
@@ -600,7 +619,6 @@ spmv_status build_csr(spmv_matrix *h, cudaStream_t s) {
         SPMV_TRY(keys_alt.alloc((size_t)nnz * 8, "sort keys"));
         SPMV_TRY(perm.alloc((size_t)nnz * 4, "sort perm"));
         SPMV_TRY(perm_alt.alloc((size_t)nnz * 4, "sort perm"));
-        SPMV_TRY(head.alloc((size_t)nnz * 4, "heads"));
         SPMV_TRY(tmp.alloc(std::max(radix_temp_bytes(nnz), scan_temp_bytes(nnz)), "sort temp"));
         SPMV_LAUNCH("k_coo_keys", s, (k_coo_keys<<<grid_for(nnz), CB, 0, s>>>(h->coo_row, h->coo_col, nnz, cbits, keys.as<uint64_t>(),
                                                 perm.as<uint32_t>())));
@@ -613,18 +631,21 @@ spmv_status build_csr(spmv_matrix *h, cudaStream_t s) {
         uint32_t *P = alt ? perm_alt.as<uint32_t>() : perm.as<uint32_t>();
         uint64_t *Kspare = alt ? keys.as<uint64_t>() : keys_alt.as<uint64_t>();
         uint32_t *Pspare = alt ? perm.as<uint32_t>() : perm_alt.as<uint32_t>();
+        // finish assuming no duplicate keys: columns, row_ptr and the duplicate check in one pass
         SPMV_CUDA_TRY(cudaMemsetAsync(h->status_dev, 0, 4, s));
-        SPMV_LAUNCH("k_heads", s, (k_heads<<<grid_for(nnz), CB, 0, s>>>(K, nnz, head.as<uint32_t>(), h->status_dev)));
-        SPMV_LAUNCH_CHECK("heads");
+        SPMV_TRY(col.alloc((size_t)nnz * 4 + TMA_PAD, "col_ind"));
+        SPMV_TRY(fill_row_ptr(K, nnz, cbits, m, row_ptr.as<int32_t>(), s, col.as<int32_t>(), h->status_dev));
         uint32_t stw = 0;
         SPMV_TRY(read_status(h, s, &stw));
         if (sort_failed(h)) return SPMV_ERR_TIMEOUT;
-        uint64_t *rowkeys = K;
         if (stw & ST_DUPLICATE) {
             if (h->flags & SPMV_DUP_ERROR) {
                 set_error("spmv_convert: duplicate (row, col) entries with SPMV_DUP_ERROR");
                 return SPMV_ERR_DUPLICATE;
             }
+            SPMV_TRY(head.alloc((size_t)nnz * 4, "heads"));
+            SPMV_LAUNCH("k_heads", s, (k_heads<<<grid_for(nnz), CB, 0, s>>>(K, nnz, head.as<uint32_t>(), h->status_dev)));
+            SPMV_LAUNCH_CHECK("heads");
             uint32_t *pos = Pspare;
             SPMV_TRY(exclusive_scan_u32(head.as<uint32_t>(), pos, nnz, tmp.p, s));
             uint32_t last[2] = {0, 0};
@@ -632,22 +653,19 @@ spmv_status build_csr(spmv_matrix *h, cudaStream_t s) {
             SPMV_CUDA_TRY(cudaMemcpyAsync(&last[1], head.as<uint32_t>() + nnz - 1, 4, cudaMemcpyDeviceToHost, s));
             SPMV_CUDA_TRY(cudaStreamSynchronize(s));
             nout = (int64_t)last[0] + last[1];
+            col.reset();
             SPMV_TRY(col.alloc((size_t)nout * 4 + TMA_PAD, "col_ind"));
             if (es) SPMV_TRY(val.alloc((size_t)nout * es + TMA_PAD, "values"));
             SPMV_LAUNCH("k_dup_compact", s, (k_dup_compact<<<grid_for(nnz), CB, 0, s>>>(K, P, head.as<uint32_t>(), pos, nnz, cbits,
                                                        es ? h->coo_val : nullptr, h->dt, Kspare,
                                                        col.as<int32_t>(), val.p)));
             SPMV_LAUNCH_CHECK("dup compact");
-            rowkeys = Kspare;
+            SPMV_TRY(fill_row_ptr(Kspare, nout, cbits, m, row_ptr.as<int32_t>(), s));
         } else {
             nout = nnz;
-            SPMV_TRY(col.alloc((size_t)nnz * 4 + TMA_PAD, "col_ind"));
             if (es) SPMV_TRY(val.alloc((size_t)nnz * es + TMA_PAD, "values"));
-            SPMV_LAUNCH("k_key_cols", s, (k_key_cols<<<grid_for(nnz), CB, 0, s>>>(K, nnz, cbits, col.as<int32_t>())));
-            SPMV_LAUNCH_CHECK("key cols");
             if (es) SPMV_TRY(gather_values(h->coo_val, h->dt, P, nnz, val.p, s));
         }
-        SPMV_TRY(fill_row_ptr(rowkeys, nout, cbits, m, row_ptr.as<int32_t>(), s));
     }
     h->row_ptr = (int32_t *)row_ptr.release();
     h->col = (int32_t *)col.release();
@@ -704,7 +722,7 @@ spmv_status build_bins(spmv_matrix *h, cudaStream_t s) {
     SPMV_TRY(tmp.alloc(radix_temp_bytes(m), "sort temp"));
     SPMV_TRY(bin_rows.alloc((size_t)m * 4, "bin rows"));
     SPMV_CUDA_TRY(cudaMemsetAsync(counts.p, 0, 16 * sizeof(unsigned long long), s));
-    SPMV_LAUNCH("k_row_class", s, (k_row_class<<<grid_for(m), CB, 0, s>>>(h->row_ptr, m, cls.as<uint64_t>(), rows.as<uint32_t>(),
+    SPMV_LAUNCH("k_row_class", s, (k_row_class<<<(unsigned)std::min<int64_t>(grid_for(m), ROW_CLASS_GRID), CB, 0, s>>>(h->row_ptr, m, cls.as<uint64_t>(), rows.as<uint32_t>(),
                                            counts.as<unsigned long long>(), counts.as<unsigned long long>() + 8)));
     SPMV_LAUNCH_CHECK("row class");
     bool alt = false;
@@ -733,26 +751,16 @@ spmv_status build_slots(spmv_matrix *h, cudaStream_t s) {
     if (h->dt == SPMV_F64) SPMV_TRY(build_df(h, s));
     const bool vals2 = h->dt == SPMV_F64 && h->df_ok;
     const size_t vbytes = h->dt == SPMV_F32 ? 4 : h->dt == SPMV_BF16 ? 2 : 0;
-    DevBuf sd(s), sc(s), sv(s), sw(s), src(s);
+    const int mode = vals2 ? SLOT_DF : h->dt == SPMV_F32 ? SLOT_F32 : h->dt == SPMV_BF16 ? SLOT_BF16 : SLOT_NONE;
+    DevBuf sd(s), sc(s), sv(s);
     SPMV_TRY(sd.alloc((size_t)tiles * SLOT_DESC_WORDS * 4, "slot descriptors"));
     SPMV_TRY(sc.alloc((size_t)slots * 4, "slot columns"));
     if (vals2) SPMV_TRY(sv.alloc((size_t)slots * sizeof(float2), "slot values"));
-    if (vbytes) SPMV_TRY(sw.alloc((size_t)slots * vbytes, "slot values"));
-    SPMV_TRY(src.alloc((size_t)slots * 4, "slot map"));
+    else if (vbytes) SPMV_TRY(sv.alloc((size_t)slots * vbytes, "slot values"));
     SPMV_LAUNCH("k_merge_slots", s, (k_merge_slots<<<(unsigned)((tiles + 7) / 8), 256, 0, s>>>(
-                                        h->row_ptr, h->part_row, h->part_nz, tiles, sd.as<uint32_t>(), src.as<int32_t>())));
+                                        h->row_ptr, h->part_row, h->part_nz, tiles, sd.as<uint32_t>(), h->col, h->val,
+                                        mode, sc.as<int32_t>(), sv.p)));
     SPMV_LAUNCH_CHECK("merge slots");
-    SPMV_LAUNCH("k_slot_fill", s, (k_slot_fill<<<grid_for(slots), CB, 0, s>>>(src.as<int32_t>(), slots, h->col,
-                                      (const double *)h->val, sc.as<int32_t>(), vals2 ? sv.as<float2>() : nullptr)));
-    SPMV_LAUNCH_CHECK("slot fill");
-    if (h->dt == SPMV_F32)
-        SPMV_LAUNCH("k_slot_vals", s, (k_slot_vals<float><<<grid_for(slots), CB, 0, s>>>(
-                                          src.as<int32_t>(), slots, (const float *)h->val, sw.as<float>())));
-    else if (h->dt == SPMV_BF16)
-        SPMV_LAUNCH("k_slot_vals", s, (k_slot_vals<__nv_bfloat16><<<grid_for(slots), CB, 0, s>>>(
-                                          src.as<int32_t>(), slots, (const __nv_bfloat16 *)h->val,
-                                          sw.as<__nv_bfloat16>())));
-    SPMV_LAUNCH_CHECK("slot values");
     if (h->slot_desc) {
         dev_free_async(h->slot_desc, s); dev_free_async(h->slot_col, s);
         if (h->slot_val2) dev_free_async(h->slot_val2, s);
@@ -761,7 +769,7 @@ spmv_status build_slots(spmv_matrix *h, cudaStream_t s) {
     h->slot_desc = (uint32_t *)sd.release();
     h->slot_col = (int32_t *)sc.release();
     h->slot_val2 = vals2 ? (float2 *)sv.release() : nullptr;
-    h->slot_val = vbytes ? sw.release() : nullptr;
+    h->slot_val = vbytes ? sv.release() : nullptr;
     h->bytes += tiles * SLOT_DESC_WORDS * 4 + slots * (4 + (vals2 ? 8 : 0) + (int64_t)vbytes);
     return SPMV_OK;
 }
