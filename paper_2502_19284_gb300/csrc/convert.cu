@@ -401,12 +401,26 @@ __global__ void k_tile_rows(const int32_t *__restrict__ row_ptr, int64_t m, int6
     tile_row[c] = row_of(row_ptr, 0, m - 1, min(c * (int64_t)HB_KEY_TILE, nnz - 1));
 }
 
+// Hilbert key of every CRS entry (and its CRS position as the sort payload).  A thread takes
+// HB_KEY_U consecutive entries: one bisection for the first one's row (over the tile's row_ptr
+// slice in shared memory when it fits), then a forward walk for the others.
+constexpr int HB_KEY_U = HB_KEY_TILE / CB;
+
+__device__ __forceinline__ uint64_t hb_key(uint32_t r, uint32_t c, int K, int log2b, int inner, const uint16_t *fwd4) {
+    if (inner == SPMV_INNER_ROWMAJOR) {
+        const uint64_t blk = hilbert_key4(K - log2b, r >> log2b, c >> log2b, fwd4);
+        const uint32_t mask = (1u << log2b) - 1u;
+        return (blk << (2 * log2b)) | ((uint64_t)(r & mask) << log2b) | (uint64_t)(c & mask);
+    }
+    return hilbert_key4(K, r, c, fwd4);
+}
+
 __global__ void k_hb_keys(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int64_t m, int64_t nnz,
                           const int64_t *__restrict__ tile_row, int K, int log2b, int inner,
                           uint64_t *__restrict__ keys, uint32_t *__restrict__ perm) {
     __shared__ int32_t s_rp[HB_KEY_ROWS + 1];
-    __shared__ uint8_t s_fwd2[64], s_inv2[64];
-    if (threadIdx.x < 64) hilbert_tables2(s_fwd2, s_inv2, threadIdx.x);
+    __shared__ __align__(16) uint16_t s_fwd4[1024];
+    hilbert_stage(s_fwd4, g_hilbert4.fwd);
     const int64_t e0 = (int64_t)blockIdx.x * HB_KEY_TILE;
     const int64_t e1 = min(e0 + (int64_t)HB_KEY_TILE, nnz) - 1;
     const int64_t rlo = tile_row[blockIdx.x], rhi = tile_row[blockIdx.x + 1];   // rows of e0 and (at least) e1
@@ -414,53 +428,77 @@ __global__ void k_hb_keys(const int32_t *__restrict__ row_ptr, const int32_t *__
     if (in_smem)
         for (int64_t r = rlo + threadIdx.x; r <= rhi + 1 && r <= m; r += blockDim.x) s_rp[r - rlo] = row_ptr[r];
     __syncthreads();
-    for (int64_t k = e0 + threadIdx.x; k <= e1; k += blockDim.x) {
-        uint32_t r;
-        if (in_smem) {   // largest r in [rlo, rhi] with row_ptr[r] <= k, searched in shared memory
-            int lo = 0, hi = (int)(rhi - rlo);
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if ((int64_t)s_rp[mid] <= k) lo = mid;
-                else hi = mid - 1;
+    const int64_t k0 = e0 + (int64_t)threadIdx.x * HB_KEY_U;
+    if (k0 > e1) return;
+    // row of entry k0: largest r in [rlo, rhi] with row_ptr[r] <= k0
+    int64_t r;
+    if (in_smem) {
+        int lo = 0, hi = (int)(rhi - rlo);
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((int64_t)s_rp[mid] <= k0) lo = mid;
+            else hi = mid - 1;
+        }
+        r = rlo + lo;
+    } else {
+        r = row_of(row_ptr, rlo, rhi, k0);
+    }
+    auto next_start = [&](int64_t rr) -> int64_t {   // row_ptr[rr + 1]
+        return in_smem ? (int64_t)s_rp[rr + 1 - rlo] : (int64_t)row_ptr[rr + 1];
+    };
+    int64_t rend = next_start(r);
+    if (k0 + HB_KEY_U - 1 <= e1) {   // a full run: vector loads and stores
+        const int4 cv0 = *(const int4 *)(col + k0), cv1 = *(const int4 *)(col + k0 + 4);
+        const int32_t cc[HB_KEY_U] = {cv0.x, cv0.y, cv0.z, cv0.w, cv1.x, cv1.y, cv1.z, cv1.w};
+        uint64_t h[HB_KEY_U];
+#pragma unroll
+        for (int u = 0; u < HB_KEY_U; ++u) {
+            const int64_t k = k0 + u;
+            while (k >= rend) {   // entries of empty rows do not exist: walk to the row holding k
+                ++r;
+                rend = next_start(r);
             }
-            r = (uint32_t)(rlo + lo);
-        } else {
-            r = (uint32_t)row_of(row_ptr, rlo, rhi, k);
+            h[u] = hb_key((uint32_t)r, (uint32_t)cc[u], K, log2b, inner, s_fwd4);
         }
-        uint32_t c = (uint32_t)col[k];
-        uint64_t h;
-        if (inner == SPMV_INNER_ROWMAJOR) {
-            uint64_t blk = hilbert_key2(K - log2b, r >> log2b, c >> log2b, s_fwd2);
-            uint32_t mask = (1u << log2b) - 1u;
-            h = (blk << (2 * log2b)) | ((uint64_t)(r & mask) << log2b) | (uint64_t)(c & mask);
-        } else {
-            h = hilbert_key2(K, r, c, s_fwd2);
+        ulonglong2 *kd = (ulonglong2 *)(keys + k0);
+#pragma unroll
+        for (int u = 0; u < HB_KEY_U / 2; ++u) kd[u] = make_ulonglong2(h[2 * u], h[2 * u + 1]);
+        const uint32_t p0 = (uint32_t)k0;
+        ((uint4 *)(perm + k0))[0] = make_uint4(p0, p0 + 1, p0 + 2, p0 + 3);
+        ((uint4 *)(perm + k0))[1] = make_uint4(p0 + 4, p0 + 5, p0 + 6, p0 + 7);
+    } else {
+        for (int64_t k = k0; k <= e1; ++k) {
+            while (k >= rend) {
+                ++r;
+                rend = next_start(r);
+            }
+            keys[k] = hb_key((uint32_t)r, (uint32_t)col[k], K, log2b, inner, s_fwd4);
+            perm[k] = (uint32_t)k;
         }
-        keys[k] = h;
-        perm[k] = (uint32_t)k;
     }
 }
+static_assert(HB_KEY_U == 8, "two int4 column loads per run");
 
 __device__ __forceinline__ void hb_cell(uint64_t key, int K, int log2b, int inner, uint32_t *r, uint32_t *c,
-                                        const uint8_t *inv2) {
+                                        const uint16_t *inv4) {
     if (inner == SPMV_INNER_ROWMAJOR) {
         uint32_t br, bc;
-        hilbert_cell2(K - log2b, key >> (2 * log2b), &br, &bc, inv2);
+        hilbert_cell4(K - log2b, key >> (2 * log2b), &br, &bc, inv4);
         uint32_t mask = (1u << log2b) - 1u;
         *r = (br << log2b) | (uint32_t)((key >> log2b) & mask);
         *c = (bc << log2b) | (uint32_t)(key & mask);
     } else {
-        hilbert_cell2(K, key, r, c, inv2);
+        hilbert_cell4(K, key, r, c, inv4);
     }
 }
 
 // Populate: packed in-block index, block-start flags.  Each thread decodes HB_FILL_U keys
-// (elements i, i + T, ... for T threads) with their table chains interleaved.
+// (elements i, i + T, ... for T threads).
 constexpr int HB_FILL_U = 4;
 __global__ void k_hb_fill(const uint64_t *__restrict__ keys, int64_t nnz, int K, int log2b, int inner,
                           uint32_t *__restrict__ idx, uint32_t *__restrict__ head) {
-    __shared__ uint8_t s_fwd2[64], s_inv2[64];
-    if (threadIdx.x < 64) hilbert_tables2(s_fwd2, s_inv2, threadIdx.x);
+    __shared__ __align__(16) uint16_t s_inv4[1024];
+    hilbert_stage(s_inv4, g_hilbert4.inv);
     __syncthreads();
     const int64_t T = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -472,12 +510,8 @@ __global__ void k_hb_fill(const uint64_t *__restrict__ keys, int64_t nnz, int K,
         const int64_t t = t0 + u * T;
         key[u] = t < nnz ? keys[t] : 0ull;
     }
-    if (inner == SPMV_INNER_ROWMAJOR) {
 #pragma unroll
-        for (int u = 0; u < HB_FILL_U; ++u) hb_cell(key[u], K, log2b, inner, &r[u], &c[u], s_inv2);
-    } else {
-        hilbert_cell2_n<HB_FILL_U>(K, key, r, c, s_inv2);
-    }
+    for (int u = 0; u < HB_FILL_U; ++u) hb_cell(key[u], K, log2b, inner, &r[u], &c[u], s_inv4);
 #pragma unroll
     for (int u = 0; u < HB_FILL_U; ++u) {
         const int64_t t = t0 + u * T;
@@ -487,33 +521,47 @@ __global__ void k_hb_fill(const uint64_t *__restrict__ keys, int64_t nnz, int K,
     }
 }
 
+// Block table from the block-start entries (one per block; the cells are decoded with the
+// one-level machine, no table staged).
 __global__ void k_hb_blocks(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ head,
                             const uint32_t *__restrict__ bid, int64_t nnz, int K, int log2b, int inner,
                             int32_t *__restrict__ blk_ptr, int32_t *__restrict__ blk_row,
                             int32_t *__restrict__ blk_col) {
-    __shared__ uint8_t s_fwd2[64], s_inv2[64];
-    if (threadIdx.x < 64) hilbert_tables2(s_fwd2, s_inv2, threadIdx.x);
-    __syncthreads();
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nnz || !head[t]) return;
-    uint32_t r, c;
-    hb_cell(keys[t], K, log2b, inner, &r, &c, s_inv2);
-    uint32_t b = bid[t];
-    blk_ptr[b] = (int32_t)t;
-    blk_row[b] = (int32_t)(r >> log2b);
-    blk_col[b] = (int32_t)(c >> log2b);
+    (void)inner;
+    const int64_t t0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;   // four flags per thread
+    if (t0 >= nnz) return;
+    uint32_t f[4];
+    if (t0 + 3 < nnz) {
+        const uint4 h4 = *(const uint4 *)(head + t0);
+        f[0] = h4.x; f[1] = h4.y; f[2] = h4.z; f[3] = h4.w;
+    } else {
+        for (int u = 0; u < 4; ++u) f[u] = t0 + u < nnz ? head[t0 + u] : 0u;
+    }
+    for (int u = 0; u < 4; ++u) {
+        if (!f[u]) continue;
+        const int64_t t = t0 + u;
+        // block coordinates: the top K - log2b levels of the key in either inner order (the
+        // curve is hierarchical, so they are the block's own Hilbert index)
+        uint32_t br, bc;
+        hilbert_cell1(K - log2b, keys[t] >> (2 * log2b), &br, &bc);
+        const uint32_t b = bid[t];
+        blk_ptr[b] = (int32_t)t;
+        blk_row[b] = (int32_t)br;
+        blk_col[b] = (int32_t)bc;
+    }
 }
 
 __global__ void k_hilbert_keys(int K, int64_t n, const int32_t *__restrict__ rows, const int32_t *__restrict__ cols,
                                uint64_t *__restrict__ keys) {
-    __shared__ uint8_t s_fwd2[64], s_inv2[64];
-    if (threadIdx.x < 64) hilbert_tables2(s_fwd2, s_inv2, threadIdx.x);
+    __shared__ __align__(16) uint16_t s_fwd4[1024], s_inv4[1024];
+    hilbert_stage(s_fwd4, g_hilbert4.fwd);
+    hilbert_stage(s_inv4, g_hilbert4.inv);
     __syncthreads();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        const uint64_t h = hilbert_key2(K, (uint32_t)rows[i], (uint32_t)cols[i], s_fwd2);
+        const uint64_t h = hilbert_key4(K, (uint32_t)rows[i], (uint32_t)cols[i], s_fwd4);
         uint32_t r, c;
-        hilbert_cell2(K, h, &r, &c, s_inv2);   // the inverse must return the cell
+        hilbert_cell4(K, h, &r, &c, s_inv4);   // the inverse must return the cell
         keys[i] = (r == (uint32_t)rows[i] && c == (uint32_t)cols[i]) ? h : ~0ull;
     }
 }
@@ -887,7 +935,7 @@ spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s) {
         SPMV_TRY(bptr.alloc((size_t)(nblk + 1) * 4, "hb blk_ptr"));
         SPMV_TRY(brow.alloc((size_t)nblk * 4, "hb blk_row"));
         SPMV_TRY(bcol.alloc((size_t)nblk * 4, "hb blk_col"));
-        SPMV_LAUNCH("k_hb_blocks", s, (k_hb_blocks<<<grid_for(nnz), CB, 0, s>>>(Ks, head.as<uint32_t>(), bid.as<uint32_t>(), nnz, K, log2b, inner,
+        SPMV_LAUNCH("k_hb_blocks", s, (k_hb_blocks<<<grid_for((nnz + 3) / 4), CB, 0, s>>>(Ks, head.as<uint32_t>(), bid.as<uint32_t>(), nnz, K, log2b, inner,
                                                  bptr.as<int32_t>(), brow.as<int32_t>(), bcol.as<int32_t>())));
         SPMV_LAUNCH_CHECK("hb blocks");
         *h->status_host = (uint32_t)nnz;   // pinned staging slot for the tail entry

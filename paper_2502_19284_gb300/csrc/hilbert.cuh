@@ -43,136 +43,103 @@ constexpr uint64_t HILBERT_INV =
     ((uint64_t)((3 << 2) | 2) << 48) | ((uint64_t)((1 << 2) | 3) << 52) | ((uint64_t)((0 << 2) | 3) << 56) |
     ((uint64_t)((2 << 2) | 1) << 60);
 
-__host__ __device__ __forceinline__ uint64_t hilbert_key(int K, uint32_t r, uint32_t c) {
-    uint64_t d = 0;
-    uint32_t st = 0;
-    for (int lev = K - 1; lev >= 0; --lev) {
-        uint32_t q = (((r >> lev) & 1u) << 1) | ((c >> lev) & 1u);
-        uint32_t e = (uint32_t)(HILBERT_FWD >> (4 * (4 * st + q))) & 0xFu;
-        d = (d << 2) | (e >> 2);
-        st = e & 3u;
-    }
-    return d;
-}
-
-__host__ __device__ __forceinline__ void hilbert_cell(int K, uint64_t d, uint32_t *r, uint32_t *c) {
+// One level per step, straight from the packed machine (for the few cells that do not pay
+// for staging a table).
+__host__ __device__ __forceinline__ void hilbert_cell1(int K, uint64_t d, uint32_t *r, uint32_t *c) {
     uint32_t rr = 0, cc = 0, st = 0;
     for (int lev = K - 1; lev >= 0; --lev) {
-        uint32_t dig = (uint32_t)(d >> (2 * lev)) & 3u;
-        uint32_t e = (uint32_t)(HILBERT_INV >> (4 * (4 * st + dig))) & 0xFu;
-        uint32_t q = e >> 2;
-        rr |= (q >> 1) << lev;
-        cc |= (q & 1u) << lev;
-        st = e & 3u;
+        const uint32_t dd = (uint32_t)(d >> (2 * lev)) & 3u;
+        const uint32_t x = (uint32_t)(HILBERT_INV >> (4 * (4 * st + dd))) & 0xFu;
+        rr = (rr << 1) | (x >> 3);
+        cc = (cc << 1) | ((x >> 2) & 1u);
+        st = x & 3u;
     }
     *r = rr;
     *c = cc;
 }
 
-// Two levels per step.  fwd2[16 * state + (r1 c1 r0 c0)] = (d1 d0) << 2 | next and
-// inv2[16 * state + (d1 d0)] = (r1 c1 r0 c0) << 2 | next (bit pairs of two consecutive
-// levels, the higher level first), both derived from the one-level machine above.  Call
-// hilbert_tables2 from 64 threads of a block (entry = threadIdx.x) before use.
-__device__ __forceinline__ void hilbert_tables2(uint8_t *fwd2, uint8_t *inv2, int entry) {
-    const uint32_t st = (uint32_t)entry >> 4, in = (uint32_t)entry & 15u;
-    {   // forward: input bits r1 c1 r0 c0
-        const uint32_t q1 = ((in >> 3) & 1u) << 1 | ((in >> 2) & 1u), q0 = ((in >> 1) & 1u) << 1 | (in & 1u);
-        const uint32_t e1 = (uint32_t)(HILBERT_FWD >> (4 * (4 * st + q1))) & 0xFu;
-        const uint32_t e0 = (uint32_t)(HILBERT_FWD >> (4 * (4 * (e1 & 3u) + q0))) & 0xFu;
-        fwd2[entry] = (uint8_t)((((e1 >> 2) << 2 | (e0 >> 2)) << 2) | (e0 & 3u));
+// Four levels per step:
+//   fwd[256 * state + (r3 r2 r1 r0) * 16 + (c3 c2 c1 c0)] = (d3 d2 d1 d0) << 2 | next
+//   inv[256 * state + (d3 d2 d1 d0)] = ((r3 r2 r1 r0) * 16 + (c3 c2 c1 c0)) << 2 | next
+// (four row bits, four column bits, two bits per digit; the higher level first), both
+// composed from the one-level machine above at compile time.  Kernels copy the table they
+// need into shared memory first (hilbert_stage).
+struct Hilbert4 {
+    uint16_t fwd[1024];
+    uint16_t inv[1024];
+    constexpr Hilbert4() : fwd(), inv() {
+        for (int e = 0; e < 1024; ++e) {
+            const uint32_t st0 = (uint32_t)e >> 8, r4 = ((uint32_t)e >> 4) & 15u, c4 = (uint32_t)e & 15u;
+            uint32_t st = st0, dg = 0;
+            for (int l = 3; l >= 0; --l) {   // forward: consume (r, c) bit pairs, highest level first
+                const uint32_t q = (((r4 >> l) & 1u) << 1) | ((c4 >> l) & 1u);
+                const uint32_t x = (uint32_t)(HILBERT_FWD >> (4 * (4 * st + q))) & 0xFu;
+                dg = (dg << 2) | (x >> 2);
+                st = x & 3u;
+            }
+            fwd[e] = (uint16_t)((dg << 2) | st);
+            const uint32_t d8 = (uint32_t)e & 255u;
+            uint32_t rr = 0, cc = 0;
+            st = st0;
+            for (int l = 3; l >= 0; --l) {   // inverse: consume digits, highest level first
+                const uint32_t dd = (d8 >> (2 * l)) & 3u;
+                const uint32_t x = (uint32_t)(HILBERT_INV >> (4 * (4 * st + dd))) & 0xFu;
+                rr = (rr << 1) | (x >> 3);
+                cc = (cc << 1) | ((x >> 2) & 1u);
+                st = x & 3u;
+            }
+            inv[e] = (uint16_t)((((rr << 4) | cc) << 2) | st);
+        }
     }
-    {   // inverse: input digits d1 d0
-        const uint32_t d1 = in >> 2, d0 = in & 3u;
-        const uint32_t e1 = (uint32_t)(HILBERT_INV >> (4 * (4 * st + d1))) & 0xFu;
-        const uint32_t e0 = (uint32_t)(HILBERT_INV >> (4 * (4 * (e1 & 3u) + d0))) & 0xFu;
-        const uint32_t q1 = e1 >> 2, q0 = e0 >> 2;
-        const uint32_t bits = ((q1 >> 1) << 3) | ((q1 & 1u) << 2) | ((q0 >> 1) << 1) | (q0 & 1u);
-        inv2[entry] = (uint8_t)((bits << 2) | (e0 & 3u));
-    }
+};
+static __device__ const Hilbert4 g_hilbert4 = Hilbert4();
+
+// Copy one 2 KB table into shared memory (16 bytes per thread); the block synchronises
+// before use.
+__device__ __forceinline__ void hilbert_stage(uint16_t *dst, const uint16_t *src) {
+    for (int i = threadIdx.x; i < 1024 / 8; i += blockDim.x) ((uint4 *)dst)[i] = ((const uint4 *)src)[i];
 }
 
-__device__ __forceinline__ uint64_t hilbert_key2(int K, uint32_t r, uint32_t c, const uint8_t *fwd2) {
+__device__ __forceinline__ uint64_t hilbert_key4(int K, uint32_t r, uint32_t c, const uint16_t *fwd4) {
     uint64_t d = 0;
     uint32_t st = 0;
     int lev = K;
-    if (lev & 1) {   // odd order: one single level first
+    while (lev & 3) {   // the top K mod 4 levels one at a time
         --lev;
         const uint32_t q = (((r >> lev) & 1u) << 1) | ((c >> lev) & 1u);
-        const uint32_t e = (uint32_t)(HILBERT_FWD >> (4 * q)) & 0xFu;   // state 0
-        d = e >> 2;
-        st = e & 3u;
+        const uint32_t x = (uint32_t)(HILBERT_FWD >> (4 * (4 * st + q))) & 0xFu;
+        d = (d << 2) | (x >> 2);
+        st = x & 3u;
     }
     while (lev > 0) {
-        lev -= 2;
-        const uint32_t rb = (r >> lev) & 3u, cb = (c >> lev) & 3u;
-        const uint32_t in = ((rb >> 1) << 3) | ((cb >> 1) << 2) | ((rb & 1u) << 1) | (cb & 1u);
-        const uint32_t e = fwd2[(st << 4) | in];
-        d = (d << 4) | (e >> 2);
-        st = e & 3u;
+        lev -= 4;
+        const uint32_t x = fwd4[(st << 8) | (((r >> lev) & 15u) << 4) | ((c >> lev) & 15u)];
+        d = (d << 8) | (x >> 2);
+        st = x & 3u;
     }
     return d;
 }
 
-__device__ __forceinline__ void hilbert_cell2(int K, uint64_t d, uint32_t *r, uint32_t *c, const uint8_t *inv2) {
+__device__ __forceinline__ void hilbert_cell4(int K, uint64_t d, uint32_t *r, uint32_t *c, const uint16_t *inv4) {
     uint32_t rr = 0, cc = 0, st = 0;
     int lev = K;
-    if (lev & 1) {
+    while (lev & 3) {
         --lev;
-        const uint32_t dig = (uint32_t)(d >> (2 * lev)) & 3u;
-        const uint32_t e = (uint32_t)(HILBERT_INV >> (4 * dig)) & 0xFu;   // state 0
-        rr = (e >> 3) & 1u;
-        cc = (e >> 2) & 1u;
-        st = e & 3u;
+        const uint32_t dd = (uint32_t)(d >> (2 * lev)) & 3u;
+        const uint32_t x = (uint32_t)(HILBERT_INV >> (4 * (4 * st + dd))) & 0xFu;
+        rr = (rr << 1) | (x >> 3);
+        cc = (cc << 1) | ((x >> 2) & 1u);
+        st = x & 3u;
     }
     while (lev > 0) {
-        lev -= 2;
-        const uint32_t dd = (uint32_t)(d >> (2 * lev)) & 15u;
-        const uint32_t e = inv2[(st << 4) | dd];
-        const uint32_t bits = e >> 2;   // r1 c1 r0 c0
-        rr = (rr << 2) | ((bits >> 3) << 1) | ((bits >> 1) & 1u);
-        cc = (cc << 2) | (((bits >> 2) & 1u) << 1) | (bits & 1u);
-        st = e & 3u;
+        lev -= 4;
+        const uint32_t x = inv4[(st << 8) | ((uint32_t)(d >> (2 * lev)) & 255u)];
+        rr = (rr << 4) | (x >> 6);
+        cc = (cc << 4) | ((x >> 2) & 15u);
+        st = x & 3u;
     }
     *r = rr;
     *c = cc;
-}
-
-// U independent cells at once: the dependent table lookups of the U chains are
-// interleaved, so one thread keeps U of them in flight.
-template <int U>
-__device__ __forceinline__ void hilbert_cell2_n(int K, const uint64_t *d, uint32_t *r, uint32_t *c,
-                                                const uint8_t *inv2) {
-    uint32_t st[U];
-    int lev = K;
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        r[u] = 0;
-        c[u] = 0;
-        st[u] = 0;
-    }
-    if (lev & 1) {
-        --lev;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint32_t dig = (uint32_t)(d[u] >> (2 * lev)) & 3u;
-            const uint32_t e = (uint32_t)(HILBERT_INV >> (4 * dig)) & 0xFu;   // state 0
-            r[u] = (e >> 3) & 1u;
-            c[u] = (e >> 2) & 1u;
-            st[u] = e & 3u;
-        }
-    }
-    while (lev > 0) {
-        lev -= 2;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint32_t dd = (uint32_t)(d[u] >> (2 * lev)) & 15u;
-            const uint32_t e = inv2[(st[u] << 4) | dd];
-            const uint32_t bits = e >> 2;   // r1 c1 r0 c0
-            r[u] = (r[u] << 2) | ((bits >> 3) << 1) | ((bits >> 1) & 1u);
-            c[u] = (c[u] << 2) | (((bits >> 2) & 1u) << 1) | (bits & 1u);
-            st[u] = e & 3u;
-        }
-    }
 }
 
 }  // namespace spmv
