@@ -1242,7 +1242,7 @@ __device__ __forceinline__ void atomic_add_out(float *p, float v) { atomicAdd(p,
 // value loads are issued first, then the bisections (each starting at the previous block),
 // then the x gathers, then the additions to y (atomics; y is zeroed first).
 template <typename VT, typename XT, typename AT>
-__global__ __launch_bounds__(HB_BLOCK) void k_hb_spmv(int64_t nnz, int log2b, const int32_t *__restrict__ chunk_blk,
+__global__ __launch_bounds__(HB_BLOCK, 4) void k_hb_spmv(int64_t nnz, int log2b, const int32_t *__restrict__ chunk_blk,
                                                       const int32_t *__restrict__ blk_ptr,
                                                       const int32_t *__restrict__ blk_row,
                                                       const int32_t *__restrict__ blk_col,
@@ -1287,9 +1287,27 @@ __global__ __launch_bounds__(HB_BLOCK) void k_hb_spmv(int64_t nnz, int log2b, co
     AT xv[HB_IPT];
 #pragma unroll
     for (int j = 0; j < HB_IPT; ++j) xv[j] = e0 + j * HB_BLOCK + threadIdx.x < e1 ? ld_x<XT, AT>(x, cc[j]) : AT(0);
+    // Lanes hold consecutive nonzeros: a run of lanes with the same row is summed by a
+    // segmented warp scan and added to y once, by the run's last lane.
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int j = 0; j < HB_IPT; ++j)
-        if (e0 + j * HB_BLOCK + threadIdx.x < e1) atomic_add_out(y + rr[j], XT(v[j] * xv[j]));
+    for (int j = 0; j < HB_IPT; ++j) {
+        const bool valid = e0 + j * HB_BLOCK + threadIdx.x < e1;
+        const int64_t row = valid ? rr[j] : -1;
+        AT p = valid ? v[j] * xv[j] : AT(0);
+        const int64_t up = __shfl_up_sync(0xffffffffu, row, 1), down = __shfl_down_sync(0xffffffffu, row, 1);
+        bool f = lane == 0 || up != row;   // first lane of its run
+        if (!__all_sync(0xffffffffu, f)) {
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const AT pv = __shfl_up_sync(0xffffffffu, p, o);
+                const bool of = __shfl_up_sync(0xffffffffu, f, o);
+                if (lane >= o && !f) p += pv;
+                if (lane >= o) f = f || of;
+            }
+        }
+        if (valid && (lane == 31 || down != row)) atomic_add_out(y + row, XT(p));
+    }
 }
 
 template <typename VT, typename XT, typename AT>
