@@ -349,6 +349,22 @@ def test_hb_structure_bit_exact(sp, inner, log2beta):
         assert (np.abs(y - yh) <= TOL * oracle.csr_absmul(rp, co, vo, x)).all()
 
 
+@pytest.mark.parametrize("inner", [0, 1])
+def test_hb_product_integer_exact(sp, inner):
+    """Integer values and x: the blocked product (runs of equal rows summed in the warp, then
+    atomics in any order) is exact in both inner orders, on a hub-heavy R-MAT matrix."""
+    rows, cols = synth.rmat(13, 32, seed=4)
+    m = n = 1 << 13
+    vals = synth.values(rows, cols, 4, integer=True)
+    x = synth.vector(n, 5, integer=True)
+    rp, co, vo = oracle.coo_to_csr(m, n, rows, cols, vals)
+    ref = oracle.csr_spmv(rp, co, vo, x)
+    h = make_handle(sp, m, n, rows, cols, vals)
+    for lb in (0, 4, 9):
+        sp.spmv_convert(h, "hb", log2_beta=lb, inner_order=inner)
+        np.testing.assert_array_equal(gpu_mul(sp, h, x, m), ref)
+
+
 def test_formats_coexist_on_one_handle(sp):
     rows, cols = synth.rmat(11, 16, seed=2)
     m = n = 1 << 11
