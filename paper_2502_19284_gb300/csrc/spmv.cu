@@ -1116,38 +1116,51 @@ struct ClassTable {
     int64_t blk_begin[NUM_ROW_CLASSES + 1];   // first CTA of each class
 };
 
+// A group of G lanes per row; a warp-wide group (rows of 33..2048 nonzeros) takes
+// RS_ROWS_PER_WARP rows, whose row ids and bounds are all loaded first.  Each round loads U
+// column indices and values per lane before their x gathers; the last round is predicated
+// instead of finished one nonzero at a time.
+constexpr int RS_ROWS_PER_WARP = 4;
+__host__ __device__ constexpr int rs_rows_per_group(int G) { return G == 32 ? RS_ROWS_PER_WARP : 1; }
+
 template <typename VT, typename XT, typename AT, int G>
 __device__ __forceinline__ void rowsplit_group(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                                                const VT *__restrict__ val, const XT *__restrict__ x,
                                                XT *__restrict__ y, const int32_t *__restrict__ rows, int64_t count,
                                                int64_t local_blk) {
-    constexpr int RPB = RS_BLOCK / G;   // rows per CTA
+    constexpr int RPG = rs_rows_per_group(G);
+    constexpr int RPB = RS_BLOCK / G * RPG;   // rows per CTA
+    constexpr int U = G >= 8 ? 4 : 1;         // loads in flight per lane and round
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
-    const int64_t ridx = local_blk * RPB + g;
-    AT acc = AT(0);
-    int32_t row = -1;
-    if (ridx < count) {
-        row = rows[ridx];
-        const int32_t k0 = __ldg(row_ptr + row), k1 = __ldg(row_ptr + row + 1);
-        // U independent loads in flight per lane (long rows of the class take several rounds)
-        constexpr int U = G >= 8 ? 4 : 1;
-        int32_t k = k0 + lane;
-        for (; k + (U - 1) * G < k1; k += U * G) {
+    const int64_t r0 = local_blk * RPB + (int64_t)g * RPG;
+    int32_t row[RPG], k0[RPG], k1[RPG];
+#pragma unroll
+    for (int i = 0; i < RPG; ++i) row[i] = r0 + i < count ? rows[r0 + i] : -1;
+#pragma unroll
+    for (int i = 0; i < RPG; ++i) {
+        k0[i] = row[i] >= 0 ? __ldg(row_ptr + row[i]) : 0;
+        k1[i] = row[i] >= 0 ? __ldg(row_ptr + row[i] + 1) : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < RPG; ++i) {
+        AT acc = AT(0);
+        for (int32_t kb = k0[i]; kb < k1[i]; kb += U * G) {
             int32_t c[U];
             AT a[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                c[u] = __ldg(col + k + u * G);
-                a[u] = ld_val<VT, AT>(val, k + u * G);
+                const int32_t k = kb + u * G + lane;
+                c[u] = k < k1[i] ? __ldg(col + k) : -1;
+                a[u] = k < k1[i] ? ld_val<VT, AT>(val, k) : AT(0);
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) acc = acc + a[u] * ld_x<XT, AT>(x, c[u]);
+            for (int u = 0; u < U; ++u)
+                if (c[u] >= 0) acc = acc + a[u] * ld_x<XT, AT>(x, c[u]);
         }
-        for (; k < k1; k += G) acc = acc + ld_val<VT, AT>(val, k) * ld_x<XT, AT>(x, __ldg(col + k));
-    }
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc = acc + __shfl_xor_sync(0xffffffffu, acc, o, G);
-    if (row >= 0 && lane == 0) y[row] = XT(acc);
+        for (int o = G / 2; o > 0; o >>= 1) acc = acc + __shfl_xor_sync(0xffffffffu, acc, o, G);
+        if (row[i] >= 0 && lane == 0) y[row[i]] = XT(acc);
+    }
 }
 
 template <typename VT, typename XT, typename AT>
@@ -1216,7 +1229,7 @@ spmv_status launch_rowsplit(const spmv_matrix *h, const void *x, void *y, cudaSt
     for (int c = 0; c < NUM_ROW_CLASSES; ++c) {
         const int64_t cnt = h->bin_count[c];
         ct.begin[c + 1] = ct.begin[c] + cnt;
-        const int64_t rpb = c < NUM_ROW_CLASSES - 1 ? RS_BLOCK / class_lanes(c) : 1;
+        const int64_t rpb = c < NUM_ROW_CLASSES - 1 ? RS_BLOCK / class_lanes(c) * rs_rows_per_group(class_lanes(c)) : 1;
         ct.blk_begin[c + 1] = ct.blk_begin[c] + (cnt + rpb - 1) / rpb;
     }
     const int64_t blocks = ct.blk_begin[NUM_ROW_CLASSES];
