@@ -172,6 +172,31 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Pinned 16-byte status slots, carved from 4 KB pinned pages that are kept for the life of
+// the process: a handle takes one instead of a page-locking allocation of its own.
+std::mutex g_pin_mu;
+std::vector<uint32_t *> g_pin_free;
+
+uint32_t *pinned_slot() {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_free.empty()) {
+        void *page = nullptr;
+        if (cudaMallocHost(&page, 4096) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        for (int i = 4096 / 16 - 1; i >= 0; --i) g_pin_free.push_back((uint32_t *)((char *)page + 16 * i));
+    }
+    uint32_t *p = g_pin_free.back();
+    g_pin_free.pop_back();
+    return p;
+}
+
+void release_slot(uint32_t *p) {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
+}
+
 void free_all(spmv_matrix *h) {
     void *ptrs[] = {h->coo_row, h->coo_col, h->coo_val, h->row_ptr, h->col, h->val, h->bin_rows,
                     h->part_row, h->part_nz, h->carry_row, h->carry_val, h->merge_desc, h->hb_idx, h->hb_val,
@@ -179,7 +204,7 @@ void free_all(spmv_matrix *h) {
                     h->pr_inv, h->pr_z, h->pr_z2, h->pr_y, h->pr_part, h->status_dev};
     if (h->pr_graph) cudaGraphExecDestroy((cudaGraphExec_t)h->pr_graph);
     for (void *p : ptrs) dev_free(p);
-    if (h->status_host) cudaFreeHost(h->status_host);
+    if (h->status_host) release_slot(h->status_host);
 }
 
 // Eq. 2 rule (Section 3.1) for the block side: start at 3 + ceil(log2 sqrt(n)) and
@@ -294,10 +319,7 @@ spmv_status spmv_create_coo(int64_t m, int64_t n, int64_t nnz, const int32_t *ro
         return e;
     };
     if ((st = dev_alloc((void **)&h->status_dev, 16, "status word", s)) != SPMV_OK) return fail(st);
-    if (cudaMallocHost((void **)&h->status_host, 16) != cudaSuccess) {
-        h->status_host = nullptr;
-        return fail(cuda_status(cudaErrorMemoryAllocation, "pinned status slot"));
-    }
+    if (!(h->status_host = pinned_slot())) return fail(cuda_status(cudaErrorMemoryAllocation, "pinned status slot"));
     if (cudaMemsetAsync(h->status_dev, 0, 16, s) != cudaSuccess) return fail(cuda_status(cudaGetLastError(), "memset"));
     if (nnz > 0) {
         if ((st = dev_alloc((void **)&h->coo_row, (size_t)nnz * 4, "triplet rows", s)) != SPMV_OK ||
