@@ -450,7 +450,7 @@ __global__ void k_hb_keys(const int32_t *__restrict__ row_ptr, const int32_t *__
     if (k0 + HB_KEY_U - 1 <= e1) {   // a full run: vector loads and stores
         const int4 cv0 = *(const int4 *)(col + k0), cv1 = *(const int4 *)(col + k0 + 4);
         const int32_t cc[HB_KEY_U] = {cv0.x, cv0.y, cv0.z, cv0.w, cv1.x, cv1.y, cv1.z, cv1.w};
-        uint64_t h[HB_KEY_U];
+        uint32_t rr[HB_KEY_U];
 #pragma unroll
         for (int u = 0; u < HB_KEY_U; ++u) {
             const int64_t k = k0 + u;
@@ -458,7 +458,26 @@ __global__ void k_hb_keys(const int32_t *__restrict__ row_ptr, const int32_t *__
                 ++r;
                 rend = next_start(r);
             }
-            h[u] = hb_key((uint32_t)r, (uint32_t)cc[u], K, log2b, inner, s_fwd4);
+            rr[u] = (uint32_t)r;
+        }
+        uint64_t h[HB_KEY_U];   // the rows are known: the eight key chains run side by side
+        if (inner == SPMV_INNER_ROWMAJOR) {
+            const uint32_t mask = (1u << log2b) - 1u;
+            uint32_t br[HB_KEY_U], bc[HB_KEY_U];
+#pragma unroll
+            for (int u = 0; u < HB_KEY_U; ++u) {
+                br[u] = rr[u] >> log2b;
+                bc[u] = (uint32_t)cc[u] >> log2b;
+            }
+            hilbert_key4_n<HB_KEY_U>(K - log2b, br, bc, s_fwd4, h);
+#pragma unroll
+            for (int u = 0; u < HB_KEY_U; ++u)
+                h[u] = (h[u] << (2 * log2b)) | ((uint64_t)(rr[u] & mask) << log2b) | (uint64_t)((uint32_t)cc[u] & mask);
+        } else {
+            uint32_t cu[HB_KEY_U];
+#pragma unroll
+            for (int u = 0; u < HB_KEY_U; ++u) cu[u] = (uint32_t)cc[u];
+            hilbert_key4_n<HB_KEY_U>(K, rr, cu, s_fwd4, h);
         }
         ulonglong2 *kd = (ulonglong2 *)(keys + k0);
 #pragma unroll
@@ -479,21 +498,8 @@ __global__ void k_hb_keys(const int32_t *__restrict__ row_ptr, const int32_t *__
 }
 static_assert(HB_KEY_U == 8, "two int4 column loads per run");
 
-__device__ __forceinline__ void hb_cell(uint64_t key, int K, int log2b, int inner, uint32_t *r, uint32_t *c,
-                                        const uint16_t *inv4) {
-    if (inner == SPMV_INNER_ROWMAJOR) {
-        uint32_t br, bc;
-        hilbert_cell4(K - log2b, key >> (2 * log2b), &br, &bc, inv4);
-        uint32_t mask = (1u << log2b) - 1u;
-        *r = (br << log2b) | (uint32_t)((key >> log2b) & mask);
-        *c = (bc << log2b) | (uint32_t)(key & mask);
-    } else {
-        hilbert_cell4(K, key, r, c, inv4);
-    }
-}
-
 // Populate: packed in-block index, block-start flags.  Each thread decodes HB_FILL_U keys
-// (elements i, i + T, ... for T threads).
+// (elements i, i + T, ... for T threads) side by side.
 constexpr int HB_FILL_U = 4;
 __global__ void k_hb_fill(const uint64_t *__restrict__ keys, int64_t nnz, int K, int log2b, int inner,
                           uint32_t *__restrict__ idx, uint32_t *__restrict__ head) {
@@ -510,8 +516,19 @@ __global__ void k_hb_fill(const uint64_t *__restrict__ keys, int64_t nnz, int K,
         const int64_t t = t0 + u * T;
         key[u] = t < nnz ? keys[t] : 0ull;
     }
+    if (inner == SPMV_INNER_ROWMAJOR) {   // block cell from the top levels, in-block cell as stored
+        uint64_t bk[HB_FILL_U];
 #pragma unroll
-    for (int u = 0; u < HB_FILL_U; ++u) hb_cell(key[u], K, log2b, inner, &r[u], &c[u], s_inv4);
+        for (int u = 0; u < HB_FILL_U; ++u) bk[u] = key[u] >> (2 * log2b);
+        hilbert_cell4_n<HB_FILL_U>(K - log2b, bk, r, c, s_inv4);
+#pragma unroll
+        for (int u = 0; u < HB_FILL_U; ++u) {
+            r[u] = (r[u] << log2b) | (uint32_t)((key[u] >> log2b) & mask);
+            c[u] = (c[u] << log2b) | (uint32_t)(key[u] & mask);
+        }
+    } else {
+        hilbert_cell4_n<HB_FILL_U>(K, key, r, c, s_inv4);
+    }
 #pragma unroll
     for (int u = 0; u < HB_FILL_U; ++u) {
         const int64_t t = t0 + u * T;

@@ -120,6 +120,38 @@ __device__ __forceinline__ uint64_t hilbert_key4(int K, uint32_t r, uint32_t c, 
     return d;
 }
 
+// U keys at once, the levels outermost: the U table lookups of a level are independent.
+template <int U>
+__device__ __forceinline__ void hilbert_key4_n(int K, const uint32_t *r, const uint32_t *c, const uint16_t *fwd4,
+                                               uint64_t *d) {
+    uint32_t st[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        d[u] = 0;
+        st[u] = 0;
+    }
+    int lev = K;
+    while (lev & 3) {
+        --lev;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t q = (((r[u] >> lev) & 1u) << 1) | ((c[u] >> lev) & 1u);
+            const uint32_t x = (uint32_t)(HILBERT_FWD >> (4 * (4 * st[u] + q))) & 0xFu;
+            d[u] = (d[u] << 2) | (x >> 2);
+            st[u] = x & 3u;
+        }
+    }
+    while (lev > 0) {
+        lev -= 4;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t x = fwd4[(st[u] << 8) | (((r[u] >> lev) & 15u) << 4) | ((c[u] >> lev) & 15u)];
+            d[u] = (d[u] << 8) | (x >> 2);
+            st[u] = x & 3u;
+        }
+    }
+}
+
 __device__ __forceinline__ void hilbert_cell4(int K, uint64_t d, uint32_t *r, uint32_t *c, const uint16_t *inv4) {
     uint32_t rr = 0, cc = 0, st = 0;
     int lev = K;
@@ -140,6 +172,41 @@ __device__ __forceinline__ void hilbert_cell4(int K, uint64_t d, uint32_t *r, ui
     }
     *r = rr;
     *c = cc;
+}
+
+// U cells at once, the levels outermost.
+template <int U>
+__device__ __forceinline__ void hilbert_cell4_n(int K, const uint64_t *d, uint32_t *r, uint32_t *c,
+                                                const uint16_t *inv4) {
+    uint32_t st[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        r[u] = 0;
+        c[u] = 0;
+        st[u] = 0;
+    }
+    int lev = K;
+    while (lev & 3) {
+        --lev;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t dd = (uint32_t)(d[u] >> (2 * lev)) & 3u;
+            const uint32_t x = (uint32_t)(HILBERT_INV >> (4 * (4 * st[u] + dd))) & 0xFu;
+            r[u] = (r[u] << 1) | (x >> 3);
+            c[u] = (c[u] << 1) | ((x >> 2) & 1u);
+            st[u] = x & 3u;
+        }
+    }
+    while (lev > 0) {
+        lev -= 4;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t x = inv4[(st[u] << 8) | ((uint32_t)(d[u] >> (2 * lev)) & 255u)];
+            r[u] = (r[u] << 4) | (x >> 6);
+            c[u] = (c[u] << 4) | ((x >> 2) & 15u);
+            st[u] = x & 3u;
+        }
+    }
 }
 
 }  // namespace spmv
