@@ -146,6 +146,14 @@ spmv_status spmv_convert(spmv_handle h, spmv_format f, const spmv_convert_opts *
 spmv_status spmv_mul(spmv_handle h, const void *x, void *y, spmv_dtype vec_dt, uint32_t accum, void *stream);
 
 /*
+ * spmv_wait -- synchronise `stream` and report whether a product on this handle (spmv_mul,
+ * spmv_mul_batch, spmv_pagerank) enqueued on it gave up a bounded device wait since the last
+ * spmv_wait: SPMV_ERR_TIMEOUT (its results are not valid; the flag is cleared) or SPMV_OK.
+ * SPMV_ERR_CUDA if the synchronisation fails.
+ */
+spmv_status spmv_wait(spmv_handle h, void *stream);
+
+/*
  * spmv_mul_batch -- Y_i := A_i X_i for `count` handles and k right-hand sides each
  * (the multiple-vector product of Section 3; the batch over many matrices has no
  * counterpart in the paper).
@@ -397,6 +405,15 @@ int spmv_trace_read(int max_entries, const char **names, long long *counts, doub
 /* Test hook: the allocation after `n` further successful ones fails with
  * SPMV_ERR_OOM, without touching the device (n < 0 turns the hook off). */
 void spmv_test_fail_alloc(long long n);
+
+/* Test hook for the bounded device waits (every mbarrier wait of the persistent kernels
+ * gives up after a fixed number of polls, sets a timeout bit in a status word and returns):
+ * one warp waits `polls` polls (1 <= polls <= 2^22) on an mbarrier that nothing arrives at.
+ * On return *status_out (host memory, owned by the caller) holds the status word the
+ * kernel wrote: bit 2 (value 4) set when the wait gave up, as it always should.  The device
+ * stays usable.  Returns SPMV_ERR_INVALID_ARG for a bad argument, SPMV_ERR_OOM or
+ * SPMV_ERR_CUDA if the status word cannot be allocated or read. */
+spmv_status spmv_test_wait_timeout(long long polls, uint32_t *status_out);
 
 #ifdef __cplusplus
 }

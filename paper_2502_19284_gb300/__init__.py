@@ -78,6 +78,7 @@ _SIG = {
     "spmv_create_coo": [_i64, _i64, _i64, _p, _p, _p, _i32, _u32, _p, ctypes.POINTER(_p)],
     "spmv_convert": [_p, _i32, ctypes.POINTER(spmv_convert_opts), _p],
     "spmv_mul": [_p, _p, _p, _i32, _u32, _p],
+    "spmv_wait": [_p, _p],
     "spmv_mul_batch": [_i32, ctypes.POINTER(_p), _i32, ctypes.POINTER(_p), ctypes.POINTER(_p), _i32, _u32, _p],
     "spmv_destroy": [_p],
     "spmv_info": [_p, ctypes.POINTER(spmv_info_t)],
@@ -111,6 +112,8 @@ _lib.spmv_trace_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), 
                                  ctypes.POINTER(ctypes.c_double)]
 _lib.spmv_test_fail_alloc.restype = None
 _lib.spmv_test_fail_alloc.argtypes = [ctypes.c_longlong]
+_lib.spmv_test_wait_timeout.restype = ctypes.c_int
+_lib.spmv_test_wait_timeout.argtypes = [ctypes.c_longlong, ctypes.POINTER(ctypes.c_uint32)]
 
 
 class SpmvError(RuntimeError):
@@ -206,6 +209,12 @@ def spmv_mul(h: Handle, x, y, accum=SPMV_ACC_DEFAULT, stream=None):
     vdt = dtype_code(x)
     _check(_lib.spmv_mul(h.ptr, _addr(x), _addr(y), vdt, accum, _stream(stream)), "spmv_mul")
     return y
+
+
+def spmv_wait(h: Handle, stream=None):
+    """Synchronise `stream`; raise SpmvError(SPMV_ERR_TIMEOUT) if a product on h gave up a
+    bounded device wait since the last call (see spmv.h)."""
+    _check(_lib.spmv_wait(h.ptr, _stream(stream)), "spmv_wait")
 
 
 def spmv_mul_batch(handles, X, Y, k=1, accum=SPMV_ACC_DEFAULT, stream=None):
@@ -305,6 +314,13 @@ def spmv_last_error() -> str:
 
 def spmv_test_fail_alloc(n: int):
     _lib.spmv_test_fail_alloc(n)
+
+
+def spmv_test_wait_timeout(polls: int) -> int:
+    """Run the bounded-wait check kernel (see spmv.h); returns the status word it wrote."""
+    out = ctypes.c_uint32(0)
+    _check(_lib.spmv_test_wait_timeout(int(polls), ctypes.byref(out)), "spmv_test_wait_timeout")
+    return int(out.value)
 
 
 def _host_values(dt, nnz):

@@ -243,6 +243,27 @@ const char *spmv_status_string(spmv_status s) {
 // fails with SPMV_ERR_OOM (n < 0 disables).
 void spmv_test_fail_alloc(long long n) { g_fail_after.store(n); }
 
+// Device-side check of the bounded waits: a kernel waits on an mbarrier that nothing arrives
+// at, gives up after `polls` polls and reports ST_TIMEOUT through a status word.
+spmv_status spmv_test_wait_timeout(long long polls, uint32_t *status_out) {
+    g_err.clear();
+    if (polls < 1 || polls > (1ll << 22) || !status_out) {
+        set_error("spmv_test_wait_timeout: polls outside [1, 2^22] or NULL output");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    uint32_t *word = nullptr;
+    cudaStream_t s = nullptr;
+    SPMV_TRY(dev_alloc((void **)&word, 16, "test status word", s));
+    spmv_status st = SPMV_OK;
+    cudaError_t e = cudaMemsetAsync(word, 0, 4, s);
+    if (e != cudaSuccess) st = cuda_status(e, "memset");
+    if (st == SPMV_OK) st = test_wait(polls, word, s);
+    if (st == SPMV_OK && (e = cudaMemcpy(status_out, word, 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        st = cuda_status(e, "status read");
+    dev_free(word);
+    return st;
+}
+
 spmv_status spmv_trace_enable(int on) {
     cudaError_t e = cudaDeviceSynchronize();
     {
@@ -413,6 +434,21 @@ spmv_status spmv_mul(spmv_handle h, const void *x, void *y, spmv_dtype vec_dt, u
     }
     set_error("spmv_mul: bad format");
     return SPMV_ERR_INVALID_ARG;
+}
+
+spmv_status spmv_wait(spmv_handle h, void *stream) {
+    g_err.clear();
+    SPMV_TRY(check_handle(h));
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(h->status_host + 3, h->status_dev + 3, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e, "spmv_wait");
+    if (h->status_host[3] & ST_TIMEOUT) {
+        if ((e = cudaMemsetAsync(h->status_dev + 3, 0, 4, s)) != cudaSuccess) return cuda_status(e, "spmv_wait");
+        set_error("spmv_wait: a bounded device wait of a product gave up");
+        return SPMV_ERR_TIMEOUT;
+    }
+    return SPMV_OK;
 }
 
 spmv_status spmv_tune(spmv_handle h, spmv_dtype vec_dt, uint32_t accum, uint32_t flags, spmv_tune_result *out,

@@ -56,6 +56,9 @@ spmv_status mul_merge(const spmv_matrix *h, const void *x, void *y, spmv_dtype v
 // (the FP64 products use double-float arithmetic when acc == SPMV_ACC_DEFAULT and h->df_ok)
 spmv_status mul_rowsplit(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s);
 spmv_status mul_hb(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s);
+// Bounded-wait check: one warp waits `polls` polls on an mbarrier nothing arrives at and sets
+// ST_TIMEOUT in *status (device word) when it gives up.
+spmv_status test_wait(long long polls, uint32_t *status, cudaStream_t s);
 // Pattern product (values taken as 1) y = A x through the merge warp tiles, with x already
 // split into float pairs in x2 (*xflag non-zero: use native FP64 on x).
 spmv_status mul_merge_pattern_split(const spmv_matrix *h, const double *x, const float2 *x2, const uint32_t *xflag,

@@ -389,9 +389,9 @@ __device__ __forceinline__ void merge_warp_issue(const uint32_t *__restrict__ de
 }
 
 // Bounded wait for phase `parity` of a slot barrier (all lanes); false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit = MW_SPIN_LIMIT) {
     uint32_t done = 0;
-    for (long long it = 0; it < MW_SPIN_LIMIT && !done; ++it)
+    for (long long it = 0; it < limit && !done; ++it)
         asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
                      : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
     return __all_sync(0xffffffffu, done);
@@ -1334,6 +1334,26 @@ spmv_status launch_hb(const spmv_matrix *h, const void *x, void *y, cudaStream_t
     return SPMV_OK;
 }
 
+// ================================================================ bounded-wait test
+// One warp waits on an mbarrier that nothing arrives at, with the same bounded wait as the
+// persistent kernels but `polls` polls; when it gives up it sets the timeout bit and returns,
+// which leaves the context usable.
+__global__ void k_test_wait(long long polls, uint32_t *__restrict__ status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (!mbar_wait(&bar, 0u, polls) && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+}
+
+spmv_status launch_test_wait(long long polls, uint32_t *status, cudaStream_t s) {
+    SPMV_LAUNCH("k_test_wait", s, (k_test_wait<<<1, 32, 0, s>>>(polls, status)));
+    SPMV_LAUNCH_CHECK("test wait");
+    return SPMV_OK;
+}
+
 // ================================================================ dispatch
 // Supported (values, vectors, accumulation): F64/F64/F64; F32/F32/F32; F32/F32/F64;
 // BF16/F32/F32; BF16/F32/F64; PATTERN/F64/F64; PATTERN/F32/F32.
@@ -1489,6 +1509,7 @@ spmv_status mul_merge(const spmv_matrix *h, const void *x, void *y, spmv_dtype v
 spmv_status mul_rowsplit(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s) {
     return dispatch(ROWSPLIT, h, x, y, vdt, acc, s);
 }
+spmv_status test_wait(long long polls, uint32_t *status, cudaStream_t s) { return launch_test_wait(polls, status, s); }
 spmv_status mul_hb(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s) {
     return dispatch(HB, h, x, y, vdt, acc, s);
 }

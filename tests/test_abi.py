@@ -48,6 +48,7 @@ def test_status_strings_and_argument_checks_without_gpu():
     assert lib.spmv_create_coo(4, 4, 0, None, None, None, sp.SPMV_F64, 0, None, None) == sp.SPMV_ERR_INVALID_ARG
     assert lib.spmv_convert(None, 0, None, None) == sp.SPMV_ERR_INVALID_ARG
     assert lib.spmv_mul(None, None, None, 0, 0, None) == sp.SPMV_ERR_INVALID_ARG
+    assert lib.spmv_wait(None, None) == sp.SPMV_ERR_INVALID_ARG
     assert lib.spmv_mul_batch(1, None, 1, None, None, 0, 0, None) == sp.SPMV_ERR_INVALID_ARG
     assert lib.spmv_destroy(None) == sp.SPMV_OK
     # serving: option limits are checked before any device call
@@ -57,6 +58,11 @@ def test_status_strings_and_argument_checks_without_gpu():
         assert lib.spmv_server_create(ctypes.byref(opts), ctypes.byref(out)) == sp.SPMV_ERR_INVALID_ARG
     assert lib.spmv_server_add(None, None, None) == sp.SPMV_ERR_INVALID_ARG
     assert lib.spmv_server_destroy(None) == sp.SPMV_OK
+    # bounded-wait hook: poll counts outside [1, 2^22] are refused before any device call
+    word = ctypes.c_uint32(0)
+    for polls in (0, -5, (1 << 22) + 1):
+        assert lib.spmv_test_wait_timeout(polls, ctypes.byref(word)) == sp.SPMV_ERR_INVALID_ARG
+    assert lib.spmv_test_wait_timeout(10, None) == sp.SPMV_ERR_INVALID_ARG
 
 
 def test_server_struct_layouts_match_header():

@@ -365,6 +365,22 @@ def test_hb_product_integer_exact(sp, inner):
         np.testing.assert_array_equal(gpu_mul(sp, h, x, m), ref)
 
 
+def test_bounded_wait_gives_up_and_device_stays_usable(sp):
+    """A kernel waiting on an mbarrier that nothing arrives at gives up after its poll limit,
+    reports the timeout bit through the status word and returns; products run afterwards."""
+    for polls in (1, 1000):
+        assert sp.spmv_test_wait_timeout(polls) & 4
+    rows, cols = synth.rmat(10, 8, seed=6)
+    m = n = 1 << 10
+    vals = synth.values(rows, cols, 6, integer=True)
+    x = synth.vector(n, 6, integer=True)
+    rp, co, vo = oracle.coo_to_csr(m, n, rows, cols, vals)
+    h = make_handle(sp, m, n, rows, cols, vals)
+    sp.spmv_convert(h, "merge")
+    np.testing.assert_array_equal(gpu_mul(sp, h, x, m), oracle.csr_spmv(rp, co, vo, x))
+    sp.spmv_wait(h)   # no product wait gave up
+
+
 def test_formats_coexist_on_one_handle(sp):
     rows, cols = synth.rmat(11, 16, seed=2)
     m = n = 1 << 11
