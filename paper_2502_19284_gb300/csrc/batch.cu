@@ -246,6 +246,7 @@ __global__ __launch_bounds__(BW * 32) void k_batch(const MatEntry *__restrict__ 
                 if (!all_heads) {
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
+                        if (__all_sync(0xffffffffu, f)) break;   // every lane has reached its segment head
                         Acc ov = sv.shfl_up(o);
                         const bool of = __shfl_up_sync(0xffffffffu, f, o);
                         if (lane >= o) {

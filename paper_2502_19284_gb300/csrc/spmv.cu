@@ -227,6 +227,7 @@ __device__ __forceinline__ void merge_tile(const int32_t *__restrict__ row_ptr, 
         bool f = head;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
+            if (__all_sync(0xffffffffu, f)) break;   // every lane has reached its segment head
             Acc ov = sv.shfl_up(o);
             const bool of = __shfl_up_sync(0xffffffffu, f, o);
             if (lane >= o) {
@@ -472,6 +473,7 @@ __device__ __forceinline__ void merge_warp_compute(uint32_t d, int64_t t, int64_
     if (!__all_sync(0xffffffffu, head)) {
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
+            if (__all_sync(0xffffffffu, f)) break;   // every lane has reached its segment head
             Acc ov = sv.shfl_up(o);
             const bool of = __shfl_up_sync(0xffffffffu, f, o);
             if (lane >= o) {
@@ -737,6 +739,7 @@ __device__ __forceinline__ void slot_compute(int64_t t, unsigned char *slot, con
     if (!__all_sync(0xffffffffu, head)) {
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
+            if (__all_sync(0xffffffffu, f)) break;   // every lane has reached its segment head
             Acc ov = run.shfl_up(o);
             const bool of = __shfl_up_sync(0xffffffffu, f, o);
             if (lane >= o) {
@@ -1313,6 +1316,7 @@ __global__ __launch_bounds__(HB_BLOCK, 4) void k_hb_spmv(int64_t nnz, int log2b,
         if (!__all_sync(0xffffffffu, f)) {
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
+                if (__all_sync(0xffffffffu, f)) break;   // every lane has reached its segment head
                 const AT pv = __shfl_up_sync(0xffffffffu, p, o);
                 const bool of = __shfl_up_sync(0xffffffffu, f, o);
                 if (lane >= o && !f) p += pv;
