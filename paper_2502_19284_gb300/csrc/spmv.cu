@@ -1267,10 +1267,12 @@ __global__ __launch_bounds__(HB_BLOCK, 4) void k_hb_spmv(int64_t nnz, int log2b,
     __shared__ int32_t s_ptr[HB_CHUNK + 2];
     __shared__ int32_t s_r0[HB_CHUNK + 1];
     __shared__ int32_t s_c0[HB_CHUNK + 1];
-    const int64_t e0 = (int64_t)blockIdx.x * HB_CHUNK;
+    const int64_t nchunks = (nnz + HB_CHUNK - 1) / HB_CHUNK;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {   // persistent: chunks ch, ch + grid, ...
+    const int64_t e0 = ch * HB_CHUNK;
     const int64_t e1 = min(e0 + (int64_t)HB_CHUNK, nnz);   // exclusive
-    const int32_t b0 = chunk_blk[blockIdx.x];
-    const int nb = chunk_blk[blockIdx.x + 1] - b0 + 1;     // blocks touching the chunk (maybe one more)
+    const int32_t b0 = chunk_blk[ch];
+    const int nb = chunk_blk[ch + 1] - b0 + 1;             // blocks touching the chunk (maybe one more)
     uint32_t p[HB_IPT];
     AT v[HB_IPT];
 #pragma unroll
@@ -1325,13 +1327,17 @@ __global__ __launch_bounds__(HB_BLOCK, 4) void k_hb_spmv(int64_t nnz, int log2b,
         }
         if (valid && (lane == 31 || down != row)) atomic_add_out(y + row, XT(p));
     }
+    __syncthreads();   // the block table of this chunk is read until here
+    }
 }
 
 template <typename VT, typename XT, typename AT>
 spmv_status launch_hb(const spmv_matrix *h, const void *x, void *y, cudaStream_t s) {
     SPMV_CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)h->m * sizeof(XT), s));
     if (h->nnz == 0) return SPMV_OK;
-    SPMV_LAUNCH("k_hb_spmv", s, (k_hb_spmv<VT, XT, AT><<<cdivu(h->nnz, HB_CHUNK), HB_BLOCK, 0, s>>>(
+    const unsigned hb_grid = std::min<unsigned>(cdivu(h->nnz, HB_CHUNK),
+                                                 persistent_grid((const void *)k_hb_spmv<VT, XT, AT>, HB_BLOCK, 0, h->nnz));
+    SPMV_LAUNCH("k_hb_spmv", s, (k_hb_spmv<VT, XT, AT><<<hb_grid, HB_BLOCK, 0, s>>>(
         h->nnz, h->log2beta, h->hb_chunk_blk, h->blk_ptr, h->blk_row, h->blk_col, h->hb_idx, (const VT *)h->hb_val,
         (const XT *)x, (XT *)y)));
     SPMV_LAUNCH_CHECK("hb spmv");
