@@ -1200,6 +1200,7 @@ __device__ __forceinline__ void rowsplit_cta(const int32_t *__restrict__ row_ptr
         for (int w = 0; w < RS_BLOCK / 32; ++w) s = s + red[w];
         y[row] = XT(s);
     }
+    __syncthreads();   // red[] is free for the CTA's next row
 }
 
 template <typename VT, typename XT, typename AT>
@@ -1207,20 +1208,22 @@ __global__ __launch_bounds__(RS_BLOCK) void k_rowsplit(const int32_t *__restrict
                                                        const int32_t *__restrict__ col, const VT *__restrict__ val,
                                                        const XT *__restrict__ x, XT *__restrict__ y,
                                                        const int32_t *__restrict__ bin_rows, ClassTable ct) {
-    const int64_t b = blockIdx.x;
-    int c = 0;
-    while (c < NUM_ROW_CLASSES - 1 && b >= ct.blk_begin[c + 1]) ++c;
-    const int64_t lb = b - ct.blk_begin[c];
-    const int32_t *rows = bin_rows + ct.begin[c];
-    const int64_t count = ct.begin[c + 1] - ct.begin[c];
-    switch (c) {
-        case 0: rowsplit_group<VT, XT, AT, 1>(row_ptr, col, val, x, y, rows, count, lb); break;
-        case 1: rowsplit_group<VT, XT, AT, 2>(row_ptr, col, val, x, y, rows, count, lb); break;
-        case 2: rowsplit_group<VT, XT, AT, 4>(row_ptr, col, val, x, y, rows, count, lb); break;
-        case 3: rowsplit_group<VT, XT, AT, 8>(row_ptr, col, val, x, y, rows, count, lb); break;
-        case 4: rowsplit_group<VT, XT, AT, 16>(row_ptr, col, val, x, y, rows, count, lb); break;
-        case 5: rowsplit_group<VT, XT, AT, 32>(row_ptr, col, val, x, y, rows, count, lb); break;
-        default: rowsplit_cta<VT, XT, AT>(row_ptr, col, val, x, y, rows[lb]); break;
+    const int64_t nblocks = ct.blk_begin[NUM_ROW_CLASSES];
+    for (int64_t b = blockIdx.x; b < nblocks; b += gridDim.x) {   // persistent over the class blocks
+        int c = 0;
+        while (c < NUM_ROW_CLASSES - 1 && b >= ct.blk_begin[c + 1]) ++c;
+        const int64_t lb = b - ct.blk_begin[c];
+        const int32_t *rows = bin_rows + ct.begin[c];
+        const int64_t count = ct.begin[c + 1] - ct.begin[c];
+        switch (c) {
+            case 0: rowsplit_group<VT, XT, AT, 1>(row_ptr, col, val, x, y, rows, count, lb); break;
+            case 1: rowsplit_group<VT, XT, AT, 2>(row_ptr, col, val, x, y, rows, count, lb); break;
+            case 2: rowsplit_group<VT, XT, AT, 4>(row_ptr, col, val, x, y, rows, count, lb); break;
+            case 3: rowsplit_group<VT, XT, AT, 8>(row_ptr, col, val, x, y, rows, count, lb); break;
+            case 4: rowsplit_group<VT, XT, AT, 16>(row_ptr, col, val, x, y, rows, count, lb); break;
+            case 5: rowsplit_group<VT, XT, AT, 32>(row_ptr, col, val, x, y, rows, count, lb); break;
+            default: rowsplit_cta<VT, XT, AT>(row_ptr, col, val, x, y, rows[lb]); break;
+        }
     }
 }
 
@@ -1237,7 +1240,8 @@ spmv_status launch_rowsplit(const spmv_matrix *h, const void *x, void *y, cudaSt
     }
     const int64_t blocks = ct.blk_begin[NUM_ROW_CLASSES];
     if (blocks == 0) return SPMV_OK;
-    SPMV_LAUNCH("k_rowsplit", s, (k_rowsplit<VT, XT, AT><<<(unsigned)blocks, RS_BLOCK, 0, s>>>(h->row_ptr, h->col, (const VT *)h->val,
+    const unsigned grid = (unsigned)std::min<int64_t>(blocks, persistent_grid((const void *)k_rowsplit<VT, XT, AT>, RS_BLOCK, 0, blocks * MW_WARPS));
+    SPMV_LAUNCH("k_rowsplit", s, (k_rowsplit<VT, XT, AT><<<grid, RS_BLOCK, 0, s>>>(h->row_ptr, h->col, (const VT *)h->val,
                                                                  (const XT *)x, (XT *)y, h->bin_rows, ct)));
     SPMV_LAUNCH_CHECK("rowsplit spmv");
     return SPMV_OK;
