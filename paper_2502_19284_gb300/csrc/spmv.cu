@@ -931,13 +931,22 @@ __global__ __launch_bounds__(MW_WARPS * 32) void k_merge_warp_pat_df(const uint3
 }
 
 // x -> (hi, lo) float pairs; flags values outside the double-float window.
+// Two entries per thread (one 16-byte load, one 16-byte store) when x is 16-byte aligned.
 __global__ void k_df_split_x(const double *__restrict__ x, int64_t n, float2 *__restrict__ x2, uint32_t *flag) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     bool bad = false;
-    if (i < n) {
-        float2 r;
-        bad = !df_split(x[i], &r.x, &r.y);
-        x2[i] = r;
+    if (i + 1 < n && ((reinterpret_cast<uintptr_t>(x) & 15u) == 0u)) {
+        const double2 v = *reinterpret_cast<const double2 *>(x + i);
+        float4 r;
+        bad = !df_split(v.x, &r.x, &r.y);
+        bad |= !df_split(v.y, &r.z, &r.w);
+        *reinterpret_cast<float4 *>(x2 + i) = r;
+    } else {
+        for (int64_t j = i; j < i + 2 && j < n; ++j) {
+            float2 r;
+            bad |= !df_split(x[j], &r.x, &r.y);
+            x2[j] = r;
+        }
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
 }
@@ -1082,7 +1091,7 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
             SPMV_CUDA_TRY(cudaMemsetAsync(h->xsplit_flag, 0, 4, s));
             if (h->n > 0) {
                 SPMV_LAUNCH("k_df_split_x", s,
-                            (k_df_split_x<<<cdivu(h->n, 256), 256, 0, s>>>((const double *)x, h->n, h->xsplit,
+                            (k_df_split_x<<<cdivu((h->n + 1) / 2, 256), 256, 0, s>>>((const double *)x, h->n, h->xsplit,
                                                                               h->xsplit_flag)));
                 SPMV_LAUNCH_CHECK("x split");
             }
