@@ -131,27 +131,56 @@ constexpr int GAP_INLINE = 64;
 // rows) are recorded for k_fill_gaps.  With col != nullptr it also writes the column of
 // every key and flags equal neighbouring keys (ST_DUPLICATE), the whole finish of a
 // conversion without duplicates in one read of the keys.
+constexpr int RPF_U = 4;   // entries per thread of k_row_ptr_fill
 __global__ void k_row_ptr_fill(const uint64_t *__restrict__ keys, int64_t nnz, int cbits, int64_t m,
                                int32_t *__restrict__ row_ptr, int64_t *__restrict__ gaps,
                                unsigned long long *__restrict__ ngaps, int32_t *__restrict__ col,
                                uint32_t *__restrict__ status) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // entries i0 .. i0 + RPF_U - 1 (entry nnz closes the last rows); kk[u + 1] = keys[i0 + u],
+    // kk[0] = keys[i0 - 1]
+    const int64_t i0 = RPF_U * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    const uint64_t cmask = (1ull << cbits) - 1ull;
     bool dup = false;
-    if (i <= nnz) {
-        const uint64_t kc = i < nnz ? keys[i] : 0ull, kp = i > 0 ? keys[i - 1] : 0ull;
-        if (col && i < nnz) {
-            col[i] = (int32_t)(kc & ((1ull << cbits) - 1ull));
-            dup = i > 0 && kc == kp;
-        }
-        const int64_t hi = i < nnz ? (int64_t)(kc >> cbits) : m;
-        const int64_t lo = i > 0 ? (int64_t)(kp >> cbits) + 1 : 0;   // rows lo..hi get value i
-        if (hi - lo + 1 <= GAP_INLINE) {
-            for (int64_t r = lo; r <= hi; ++r) row_ptr[r] = (int32_t)i;
+    if (i0 <= nnz) {
+        uint64_t kk[RPF_U + 1];
+        kk[0] = i0 > 0 ? keys[i0 - 1] : 0ull;
+        const bool full = i0 + RPF_U <= nnz;   // keys + i0 is 32-byte aligned (i0 a multiple of 4)
+        if (full) {
+            const ulonglong2 a = *(const ulonglong2 *)(keys + i0), b2 = *(const ulonglong2 *)(keys + i0 + 2);
+            kk[1] = a.x;
+            kk[2] = a.y;
+            kk[3] = b2.x;
+            kk[4] = b2.y;
         } else {
-            const unsigned long long g = atomicAdd(ngaps, 1ull);
-            gaps[3 * g + 0] = lo;
-            gaps[3 * g + 1] = hi;
-            gaps[3 * g + 2] = i;
+#pragma unroll
+            for (int u = 0; u < RPF_U; ++u) kk[u + 1] = i0 + u < nnz ? keys[i0 + u] : 0ull;
+        }
+        if (col) {
+            if (full) {
+                *(int4 *)(col + i0) = make_int4((int32_t)(kk[1] & cmask), (int32_t)(kk[2] & cmask),
+                                                (int32_t)(kk[3] & cmask), (int32_t)(kk[4] & cmask));
+            } else {
+#pragma unroll
+                for (int u = 0; u < RPF_U; ++u)
+                    if (i0 + u < nnz) col[i0 + u] = (int32_t)(kk[u + 1] & cmask);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < RPF_U; ++u) {
+            const int64_t i = i0 + u;
+            if (i > nnz) break;
+            const uint64_t kc = kk[u + 1], kp = kk[u];
+            if (col && i < nnz) dup |= i > 0 && kc == kp;
+            const int64_t hi = i < nnz ? (int64_t)(kc >> cbits) : m;
+            const int64_t lo = i > 0 ? (int64_t)(kp >> cbits) + 1 : 0;   // rows lo..hi get value i
+            if (hi - lo + 1 <= GAP_INLINE) {
+                for (int64_t r = lo; r <= hi; ++r) row_ptr[r] = (int32_t)i;
+            } else {
+                const unsigned long long g = atomicAdd(ngaps, 1ull);
+                gaps[3 * g + 0] = lo;
+                gaps[3 * g + 1] = hi;
+                gaps[3 * g + 2] = i;
+            }
         }
     }
     if (col && __any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) atomicOr(status, ST_DUPLICATE);
@@ -643,7 +672,7 @@ spmv_status fill_row_ptr(const uint64_t *keys, int64_t nnz, int cbits, int64_t m
     SPMV_TRY(gaps.alloc((size_t)cap * 3 * sizeof(int64_t), "row_ptr gaps"));
     SPMV_TRY(ngaps.alloc(sizeof(unsigned long long), "row_ptr gap count"));
     SPMV_CUDA_TRY(cudaMemsetAsync(ngaps.p, 0, sizeof(unsigned long long), s));
-    SPMV_LAUNCH("k_row_ptr_fill", s, (k_row_ptr_fill<<<grid_for(nnz + 1), CB, 0, s>>>(keys, nnz, cbits, m, row_ptr, gaps.as<int64_t>(),
+    SPMV_LAUNCH("k_row_ptr_fill", s, (k_row_ptr_fill<<<grid_for((nnz + 1 + RPF_U - 1) / RPF_U), CB, 0, s>>>(keys, nnz, cbits, m, row_ptr, gaps.as<int64_t>(),
                                                     ngaps.as<unsigned long long>(), col, status)));
     SPMV_LAUNCH_CHECK("row_ptr fill");
     SPMV_LAUNCH("k_fill_gaps", s, (k_fill_gaps<<<1184, CB, 0, s>>>(gaps.as<int64_t>(), ngaps.as<unsigned long long>(), row_ptr)));
