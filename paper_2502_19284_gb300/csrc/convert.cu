@@ -33,13 +33,19 @@ inline unsigned grid_for(int64_t n, int per_block = CB) {
 // ---------------------------------------------------------------- validation
 __global__ void k_validate(const int32_t *__restrict__ row, const int32_t *__restrict__ col, int64_t nnz, int64_t m,
                            int64_t n, uint32_t *status) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // four triplets per 16-byte load of each array when both are 16-byte aligned (the library's
+    // own copies are)
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    auto out = [&](int32_t r, int32_t c) { return (r < 0) | ((int64_t)r >= m) | (c < 0) | ((int64_t)c >= n); };
     bool bad = false;
-    for (; i < nnz; i += stride) {
-        int32_t r = row[i], c = col[i];
-        bad |= (r < 0) | ((int64_t)r >= m) | (c < 0) | ((int64_t)c >= n);
+    const int64_t ngrp = ((reinterpret_cast<uintptr_t>(row) | reinterpret_cast<uintptr_t>(col)) & 15u) ? 0 : nnz / 4;
+#pragma unroll 2
+    for (int64_t g = t; g < ngrp; g += stride) {
+        const int4 r4 = ((const int4 *)row)[g], c4 = ((const int4 *)col)[g];
+        bad |= out(r4.x, c4.x) | out(r4.y, c4.y) | out(r4.z, c4.z) | out(r4.w, c4.w);
     }
+    for (int64_t i = 4 * ngrp + t; i < nnz; i += stride) bad |= out(row[i], col[i]);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_INDEX_RANGE);
 }
 
@@ -685,7 +691,7 @@ spmv_status fill_row_ptr(const uint64_t *keys, int64_t nnz, int cbits, int64_t m
 spmv_status launch_validate(const int32_t *row, const int32_t *col, int64_t nnz, int64_t m, int64_t n,
                             uint32_t *status, cudaStream_t s) {
     if (nnz <= 0) return SPMV_OK;
-    SPMV_LAUNCH("k_validate", s, (k_validate<<<grid_for(nnz, CB * 8), CB, 0, s>>>(row, col, nnz, m, n, status)));
+    SPMV_LAUNCH("k_validate", s, (k_validate<<<grid_for((nnz + 3) / 4, CB * 4), CB, 0, s>>>(row, col, nnz, m, n, status)));
     SPMV_LAUNCH_CHECK("validate");
     return SPMV_OK;
 }
