@@ -129,7 +129,9 @@ spmv_status spmv_create_coo(int64_t m, int64_t n, int64_t nnz, const int32_t *ro
  *   packed indices ((r mod beta) << 16 | (c mod beta)).  Requires beta <= 2^16.
  * opt may be NULL (defaults).  The CRS arrays are kept once built, so a later
  * conversion to another CSR algorithm or to HB reuses them.  The converted format
- * becomes the one spmv_mul uses.  Synchronises `stream` once (status read-back).
+ * becomes the one spmv_mul uses.  Synchronises `stream` (status read-backs).  Errors:
+ * SPMV_ERR_DUPLICATE (duplicates with SPMV_DUP_ERROR), SPMV_ERR_TIMEOUT (a bounded wait of
+ * a radix sort gave up; the handle keeps its previous formats), SPMV_ERR_OOM, SPMV_ERR_CUDA.
  */
 spmv_status spmv_convert(spmv_handle h, spmv_format f, const spmv_convert_opts *opt, void *stream);
 
@@ -141,7 +143,8 @@ spmv_status spmv_convert(spmv_handle h, spmv_format f, const spmv_convert_opts *
  * Asynchronous: enqueues kernels on `stream` and returns.  Uses the format of the
  * last successful spmv_convert.  The handle's internal scratch is shared by its
  * calls, so two spmv_mul calls on one handle must be ordered (same stream or
- * events); calls on different handles may overlap freely.
+ * events); calls on different handles may overlap freely.  A bounded device wait that
+ * gives up is reported by spmv_wait.
  */
 spmv_status spmv_mul(spmv_handle h, const void *x, void *y, spmv_dtype vec_dt, uint32_t accum, void *stream);
 
