@@ -362,9 +362,9 @@ spmv_status spmv_server_destroy(spmv_server_t srv);
  * device, with the merge-path product, without allocating any device memory.
  *
  * The paper has no counterpart: this entry point exists for callers that cannot allocate,
- * for example code recording work into a CUDA graph, callers that reserved all device
- * memory up front for their own allocator, or serving loops that cannot afford the device
- * synchronisation that cudaMalloc and cudaFree imply.  The library's other calls keep
+ * for example callers that reserved all device memory up front for their own allocator,
+ * code that runs under a memory budget enforced by someone else, or serving loops that
+ * cannot afford the device synchronisation that cudaMalloc and cudaFree imply.  The library's other calls keep
  * their scratch in memory they allocate; this one keeps the merge-path partition and the
  * tile carries in a fixed array that is part of the library itself (about 1.3 MB, held on
  * every GPU that loads the library until the process exits).

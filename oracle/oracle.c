@@ -14,7 +14,7 @@
  * Functions and the passages they follow:
  *   oracle_coo_to_csr      Section 2 (triplet format, CRS format) + Section 5.1 (conversion
  *                          = sort into the format's order, then populate/compress)
- *   oracle_csr_spmv        Algorithm 1 (CRS SpMV), exactly: y = 0, rows ascending, k ascending
+ *   oracle_csr_spmv        Algorithm 1 (CRS SpMV): rows in order, entries in storage order, FP64
  *   oracle_coo_spmv        Eq. 1 (triplet SpMV) -- used only as a cross-check
  *   oracle_hilbert_index   Section 3.2 and the Hilbert recursion figure: quadrant order
  *                          TL, BL, BR, TR; TL sub-curve transposed, TR anti-transposed
@@ -114,9 +114,11 @@ int oracle_coo_to_csr(int64_t m, int64_t n, int64_t nnz, const int32_t *row, con
 /* ---------------------------------------------------------------- Algorithm 1 */
 
 /*
- * Algorithm 1 (SpMV for the CRS format): y = 0; for i = 0..m-1, for
- * k = row_ptr[i]..row_ptr[i+1]-1: j = col_ind[k]; y[i] = y[i] + data[k] * x[j].
- * data == NULL means a pattern matrix (every stored value is 1).
+ * The CRS product of Algorithm 1 (Section 2).  Contract: y is overwritten; every
+ * row is summed on its own, its stored entries taken in storage order, each product
+ * rounded to FP64 and then added to the running FP64 row sum (no fused multiply-add,
+ * the file is built with -ffp-contract=off).  data == NULL means a pattern matrix
+ * (every stored value is 1).
  */
 void oracle_csr_spmv(int64_t m, const int32_t *row_ptr, const int32_t *col_ind, const double *data,
                      const double *x, double *y) {

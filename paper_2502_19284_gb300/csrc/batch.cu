@@ -376,11 +376,8 @@ template <typename VT, typename XT, typename T, typename Acc, int KB>
 spmv_status enqueue_batch(Plan *p, cudaStream_t s) {
     using Slot = BSlot<VT, Acc, KB>;
     const size_t smem = (size_t)BW * Slot::BYTES;
-    static bool attr = false;
-    if (!attr) {
-        SPMV_TRY(set_smem_ctas((const void *)k_batch<VT, XT, T, Acc, KB>, smem, 5));
-        attr = true;
-    }
+    static DeviceOnce attr;
+    SPMV_TRY(attr([&] { return set_smem_ctas((const void *)k_batch<VT, XT, T, Acc, KB>, smem, 5); }));
     int dev = 0, sms = 1, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -6,6 +6,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <string>
 
 #include "../../include/spmv.h"
@@ -30,6 +32,30 @@ spmv_status cuda_status(cudaError_t e, const char *what);   // records text, map
 
 // Launch error check (kernel launches report configuration errors lazily).
 #define SPMV_LAUNCH_CHECK(what) SPMV_CUDA_TRY(cudaPeekAtLastError())
+
+// Kernel attributes (cudaFuncSetAttribute) belong to the current device: a DeviceOnce runs
+// its set-up once per device, under a lock, so that a process that drives several GPUs, from
+// one thread or several, launches every kernel with its attributes on each of them.  A
+// failed set-up is retried on the next call.
+class DeviceOnce {
+public:
+    template <typename F>
+    spmv_status operator()(F &&setup) {
+        int dev = 0;
+        SPMV_CUDA_TRY(cudaGetDevice(&dev));
+        const uint64_t bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0ull;   // beyond 64: every call
+        if (bit && (done_.load(std::memory_order_acquire) & bit)) return SPMV_OK;
+        std::lock_guard<std::mutex> g(mu_);
+        if (bit && (done_.load(std::memory_order_relaxed) & bit)) return SPMV_OK;
+        const spmv_status st = setup();
+        if (st == SPMV_OK && bit) done_.fetch_or(bit, std::memory_order_release);
+        return st;
+    }
+
+private:
+    std::mutex mu_;
+    std::atomic<uint64_t> done_{0};
+};
 
 // ------------------------------------------------------------------ tracing
 // When tracing is on (spmv_trace_enable), every kernel launch is bracketed by two CUDA

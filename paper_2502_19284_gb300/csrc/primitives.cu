@@ -334,11 +334,8 @@ spmv_status radix_sort_pairs(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals,
                              int begin_bit, int end_bit, void *temp, cudaStream_t s, bool *in_alt, uint32_t *err) {
     *in_alt = false;
     if (n <= 1 || end_bit <= begin_bit) return SPMV_OK;
-    static bool attr_set = false;
-    if (!attr_set) {
-        SPMV_TRY(set_smem((const void *)k_rs_scatter, RS_SMEM));
-        attr_set = true;
-    }
+    static DeviceOnce attr_set;
+    SPMV_TRY(attr_set([&] { return set_smem((const void *)k_rs_scatter, RS_SMEM); }));
     const int64_t ntiles = cdiv(n, RS_TILE);
     uint32_t *cnt = (uint32_t *)temp;
     void *scan_tmp = (char *)temp + align256((size_t)ntiles * RADIX * 4);

@@ -1054,11 +1054,8 @@ constexpr size_t merge_smem(int ipt) {
 template <typename SV, typename Acc>
 spmv_status launch_slot(const spmv_matrix *h, const void *x, void *y, cudaStream_t s) {
     constexpr size_t smem = slot_smem<SV, Acc>();
-    static bool attr = false;
-    if (!attr) {
-        SPMV_TRY(set_smem_ctas((const void *)k_merge_slot<SV, Acc>, smem, SLOT_CTAS));
-        attr = true;
-    }
+    static DeviceOnce attr;
+    SPMV_TRY(attr([&] { return set_smem_ctas((const void *)k_merge_slot<SV, Acc>, smem, SLOT_CTAS); }));
     const unsigned grid = persistent_grid((const void *)k_merge_slot<SV, Acc>, SLOT_WARPS * 32, smem, h->tiles);
     SPMV_LAUNCH("k_merge_spmv", s, (k_merge_slot<SV, Acc><<<grid, SLOT_WARPS * 32, smem, s>>>(
                                        h->slot_desc, h->slot_col, (const SV *)h->slot_val, (const float *)x, (float *)y,
@@ -1082,11 +1079,8 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
     if constexpr (FP64) {
         if (allow_df && h->df_ok && h->xsplit && h->slot_val2) {
             constexpr size_t ssmem = slot_smem<float2, DfAcc>();
-            static bool attr = false;
-            if (!attr) {
-                SPMV_TRY(set_smem_ctas((const void *)k_merge_slot_df<float2>, ssmem, SLOT_CTAS));
-                attr = true;
-            }
+            static DeviceOnce attr;
+            SPMV_TRY(attr([&] { return set_smem_ctas((const void *)k_merge_slot_df<float2>, ssmem, SLOT_CTAS); }));
             const unsigned grid = persistent_grid((const void *)k_merge_slot_df<float2>, SLOT_WARPS * 32, ssmem, h->tiles);
             SPMV_CUDA_TRY(cudaMemsetAsync(h->xsplit_flag, 0, 4, s));
             if (h->n > 0) {
@@ -1106,11 +1100,8 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
     }
     if constexpr (std::is_same<XT, float>::value && !std::is_same<VT, double>::value)
         if (has_slot_vals<VT>(h)) return launch_slot<VT, NativeAcc<AT>>(h, x, y, s);
-    static bool attr = false;
-    if (!attr) {
-        SPMV_TRY(set_smem_ctas((const void *)k_merge_warp<VT, XT, AT>, smem, 5));
-        attr = true;
-    }
+    static DeviceOnce attr;
+    SPMV_TRY(attr([&] { return set_smem_ctas((const void *)k_merge_warp<VT, XT, AT>, smem, 5); }));
     const unsigned grid = persistent_grid((const void *)k_merge_warp<VT, XT, AT>, MW_WARPS * 32, smem, h->tiles);
     SPMV_LAUNCH("k_merge_spmv", s, (k_merge_warp<VT, XT, AT><<<grid, MW_WARPS * 32, smem, s>>>(
                                        h->merge_desc, h->col, (const VT *)h->val, (const XT *)x, (XT *)y, h->part_row,
@@ -1386,11 +1377,8 @@ template <typename VT, typename Acc>
 spmv_status launch_merge_comp(const spmv_matrix *h, const void *x, void *y, cudaStream_t s) {
     if (has_slot_vals<VT>(h)) return launch_slot<VT, Acc>(h, x, y, s);
     constexpr size_t smem = (size_t)MW_WARPS * 2 * WarpSlot<VT>::BYTES;
-    static bool attr = false;
-    if (!attr) {
-        SPMV_TRY(set_smem_ctas((const void *)k_merge_warp_comp<VT, Acc>, smem, 5));
-        attr = true;
-    }
+    static DeviceOnce attr;
+    SPMV_TRY(attr([&] { return set_smem_ctas((const void *)k_merge_warp_comp<VT, Acc>, smem, 5); }));
     const unsigned grid = persistent_grid((const void *)k_merge_warp_comp<VT, Acc>, MW_WARPS * 32, smem, h->tiles);
     SPMV_LAUNCH("k_merge_spmv", s, (k_merge_warp_comp<VT, Acc><<<grid, MW_WARPS * 32, smem, s>>>(
                                        h->merge_desc, h->col, (const VT *)h->val, (const float *)x, (float *)y,
@@ -1508,12 +1496,7 @@ spmv_status noalloc_merge(int64_t m, int64_t n, int64_t nnz, const int32_t *row_
     int32_t *carry_row = (int32_t *)(base + 2 * pb);
     double *carry_val = (double *)(base + 2 * pb + (size_t)NOALLOC_MAX_TILES * 4);
     constexpr size_t smem = merge_smem<NativeAcc<double>>(MERGE_IPT);
-    static bool attr = false;
-    if (!attr) {
-        SPMV_CUDA_TRY(cudaFuncSetAttribute(k_merge_spmv<double, double, double, MERGE_IPT>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    static_assert(smem <= 48 * 1024, "within the default dynamic shared memory limit: no attribute to set");
     k_noalloc_partition<<<cdivu(tiles + 1, 256), 256, 0, s>>>(row_ptr, m, nnz, tiles, MERGE_TILE_ITEMS, part_row, part_nz);
     SPMV_LAUNCH_CHECK("noalloc partition");
     k_merge_spmv<double, double, double, MERGE_IPT><<<(unsigned)tiles, MP_BLOCK, smem, s>>>(
@@ -1546,11 +1529,8 @@ spmv_status mul_merge_pattern_split(const spmv_matrix *h, const double *x, const
                                     double *y, cudaStream_t s) {
     if (h->slot_desc) {
         constexpr size_t ssmem = slot_smem<Pattern, DfAcc>();
-        static bool sattr = false;
-        if (!sattr) {
-            SPMV_TRY(set_smem_ctas((const void *)k_merge_slot_df<Pattern>, ssmem, SLOT_CTAS));
-            sattr = true;
-        }
+        static DeviceOnce sattr;
+        SPMV_TRY(sattr([&] { return set_smem_ctas((const void *)k_merge_slot_df<Pattern>, ssmem, SLOT_CTAS); }));
         const unsigned grid = persistent_grid((const void *)k_merge_slot_df<Pattern>, SLOT_WARPS * 32, ssmem, h->tiles);
         SPMV_LAUNCH("k_merge_spmv", s, (k_merge_slot_df<Pattern><<<grid, SLOT_WARPS * 32, ssmem, s>>>(
                                            h->slot_desc, h->slot_col, (const Pattern *)nullptr, x, x2, xflag, y,
@@ -1560,11 +1540,8 @@ spmv_status mul_merge_pattern_split(const spmv_matrix *h, const double *x, const
         return SPMV_OK;
     }
     constexpr size_t smem = (size_t)MW_WARPS * 2 * WarpSlot<Pattern>::BYTES;
-    static bool attr = false;
-    if (!attr) {
-        SPMV_TRY(set_smem_ctas((const void *)k_merge_warp_pat_df, smem, 5));
-        attr = true;
-    }
+    static DeviceOnce attr;
+    SPMV_TRY(attr([&] { return set_smem_ctas((const void *)k_merge_warp_pat_df, smem, 5); }));
     const unsigned grid = persistent_grid((const void *)k_merge_warp_pat_df, MW_WARPS * 32, smem, h->tiles);
     SPMV_LAUNCH("k_merge_spmv", s, (k_merge_warp_pat_df<<<grid, MW_WARPS * 32, smem, s>>>(
                                        h->merge_desc, h->col, x, x2, xflag, y, h->part_row, h->part_nz, h->carry_row,

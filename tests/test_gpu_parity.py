@@ -399,7 +399,8 @@ def test_formats_coexist_on_one_handle(sp):
 @pytest.mark.slow
 def test_rmat_scale22_full_size(sp):
     """R-MAT scale 22 (the benchmark workload): CSR bit-exact against the oracle; every
-    product algorithm within tolerance on all rows; integer variant bit-exact (merge)."""
+    product algorithm within tolerance on all rows; the blocked arrays at beta = 2^14 bit-exact
+    in both inner orders; the integer variant bit-exact for every product."""
     rows, cols = synth.rmat(22, 16, seed=0)
     m = n = 1 << 22
     vals = synth.values(rows, cols, 0)
@@ -417,10 +418,44 @@ def test_rmat_scale22_full_size(sp):
         sp.spmv_convert(h, algo)
         y = gpu_mul(sp, h, x, m)
         assert (np.abs(y - ref) <= TOL * scale).all(), algo
+    # the blocked structure at the benchmark's block side 2^14 (K = 22), both inner orders,
+    # bit for bit against the oracle's Hilbert sort (the curve's high levels included)
+    for inner in (0, 1):
+        sp.spmv_convert(h, "hb", log2_beta=14, inner_order=inner)
+        got = sp.spmv_export_hb(h)
+        want = oracle.csr_to_hb(m, n, rp, co, vo, 14, inner)
+        assert got["nblk"] == want["nblk"] and got["log2beta"] == 14
+        for k in ("idx", "val", "blk_ptr", "blk_row", "blk_col"):
+            np.testing.assert_array_equal(got[k], want[k], err_msg=f"{k} inner={inner}")
+        del got, want
     del h
     vi = synth.values(rows, cols, 0, integer=True)
     xi = synth.vector(n, 1, integer=True)
     rp, co, vo = oracle.coo_to_csr(m, n, rows, cols, vi)
+    refi = oracle.csr_spmv(rp, co, vo, xi)
     h = make_handle(sp, m, n, rows, cols, vi)
-    sp.spmv_convert(h, "merge")
-    np.testing.assert_array_equal(gpu_mul(sp, h, xi, m), oracle.csr_spmv(rp, co, vo, xi))
+    for algo in ALGOS:
+        sp.spmv_convert(h, algo)
+        np.testing.assert_array_equal(gpu_mul(sp, h, xi, m), refi, err_msg=algo)
+    sp.spmv_convert(h, "hb", inner_order=1)
+    np.testing.assert_array_equal(gpu_mul(sp, h, xi, m), refi, err_msg="hb row-major inner order")
+
+
+@pytest.mark.parametrize("log2beta", [9, 14])
+@pytest.mark.parametrize("inner", [0, 1])
+def test_hb_structure_rmat_scale17(sp, log2beta, inner):
+    """Mid-size R-MAT (scale 17, K = 17): the blocked arrays bit for bit against the oracle
+    at a small and at the benchmark's block side, and the integer product exact."""
+    rows, cols = synth.rmat(17, 16, seed=17)
+    m = n = 1 << 17
+    vals = synth.values(rows, cols, 17, integer=True)
+    rp, co, vo = oracle.coo_to_csr(m, n, rows, cols, vals)
+    h = make_handle(sp, m, n, rows, cols, vals)
+    sp.spmv_convert(h, "hb", log2_beta=log2beta, inner_order=inner)
+    got = sp.spmv_export_hb(h)
+    want = oracle.csr_to_hb(m, n, rp, co, vo, log2beta, inner)
+    assert got["nblk"] == want["nblk"]
+    for k in ("idx", "val", "blk_ptr", "blk_row", "blk_col"):
+        np.testing.assert_array_equal(got[k], want[k], err_msg=k)
+    x = synth.vector(n, 18, integer=True)
+    np.testing.assert_array_equal(gpu_mul(sp, h, x, m), oracle.csr_spmv(rp, co, vo, x))

@@ -10,7 +10,8 @@ with u = 2^-24 and L the row length:
   segmented compensation     |y - ref| <= (gamma(8) + 8 L u^2) (|A||x|) + u |ref| + 2^-140
                              (FP32 inside a lane's <= 7 items, TwoSum where lanes and tiles join)
   FP64 accumulation          |y - ref| <= u |ref| + 1e-14 (|A||x|)     (output rounded to FP32)
-Integer-valued data with integer x is exact in every mode (all partial sums < 2^24).
+Integer-valued data with integer x is exact in every mode (all partial sums < 2^24).  The
+FP32 bound holds for any order of the additions (the blocked product adds through atomics).
 """
 import numpy as np
 import pytest
@@ -71,7 +72,8 @@ def test_precision_modes(sp, kind):
             xd = torch.from_numpy(x32).to(DEV)
             for algo, modes in (("merge", (sp.SPMV_ACC_F32, sp.SPMV_ACC_COMPENSATED, sp.SPMV_ACC_SEGMENT,
                                            sp.SPMV_ACC_F64)),
-                                ("rowsplit", (sp.SPMV_ACC_F32, sp.SPMV_ACC_F64))):
+                                ("rowsplit", (sp.SPMV_ACC_F32, sp.SPMV_ACC_F64)),
+                                ("hb", (sp.SPMV_ACC_F32,))):
                 sp.spmv_convert(h, algo)
                 for acc in modes:
                     if kind == "pattern" and acc == sp.SPMV_ACC_F64:

@@ -540,3 +540,56 @@ def test_csr_spmm_matches_dense_brute_force():
     assert Y.shape == (m, k)
     assert np.array_equal(Y, want)
 
+
+
+# ------------------------------------------------------------------ tolerance scale (|A| |x|)
+
+@pytest.mark.parametrize("seed", range(8))
+def test_csr_absmul_dense_brute_force(orc, seed):
+    """(|A| |x|)_i, the scale of every floating-point tolerance of the parity tests, against
+    a dense product of the absolute values written out element by element.  Values and x
+    carry mixed signs; integer data makes every sum exact, so the comparison is exact, and a
+    stray term (a nonzero of the next row, a doubled entry) or a lost absolute value shows."""
+    rng = np.random.default_rng(700 + seed)
+    m, n = int(rng.integers(1, 48)), int(rng.integers(1, 48))
+    rp, co, vo = _random_csr(m, n, int(rng.integers(0, 4 * m + 1)), 700 + seed, integer=True)
+    x = synth.vector(n, 701 + seed, integer=True)
+    assert (vo < 0).any() or vo.size < 4           # mixed signs present
+    D = _dense(m, n, rp, co, vo)
+    want = np.zeros(m)
+    for i in range(m):
+        for j in range(n):
+            want[i] += abs(D[i, j]) * abs(x[j])
+    np.testing.assert_array_equal(oracle.csr_absmul(rp, co, vo, x, orc), want)
+    # pattern matrix: |1| |x_j| summed over the row's columns
+    Dp = _dense(m, n, rp, co, None)
+    np.testing.assert_array_equal(oracle.csr_absmul(rp, co, None, x, orc), Dp @ np.abs(x))
+
+
+def test_csr_absmul_float_bounds(orc):
+    """Floating values: the row sum of |a||x| equals math.fsum of the same products within
+    the row length's rounding bound, and is never below the magnitude of Algorithm 1's y."""
+    rp, co, vo = _random_csr(30, 30, 200, 71)
+    x = synth.vector(30, 72)
+    s = oracle.csr_absmul(rp, co, vo, x, orc)
+    y = oracle.csr_spmv(rp, co, vo, x, orc)
+    for i in range(30):
+        terms = [abs(float(vo[k])) * abs(float(x[co[k]])) for k in range(rp[i], rp[i + 1])]
+        L = len(terms)
+        assert abs(s[i] - math.fsum(terms)) <= 2 * L * 2.0 ** -53 * math.fsum(terms)
+        assert abs(y[i]) <= s[i] * (1 + 4 * L * 2.0 ** -53)
+
+
+def test_planted_absmul_row_overrun_fails_brute_force(orc):
+    """Summing one entry past each row's end (an off-by-one in the row loop) inflates the
+    tolerance scale; the dense pin catches it."""
+    m, n = 12, 12
+    rp, co, vo = _random_csr(m, n, 60, 73, integer=True)
+    x = synth.vector(n, 74, integer=True)
+    good = oracle.csr_absmul(rp, co, vo, x, orc)
+    bad_rp = rp.copy()
+    bad_rp[1:-1] += 1                  # every row but the last reaches into the next one
+    bad = oracle.csr_absmul(bad_rp, co, vo, x, orc)
+    D = _dense(m, n, rp, co, vo)
+    want = np.abs(D) @ np.abs(x)
+    assert np.array_equal(good, want) and not np.array_equal(bad, want)
