@@ -46,6 +46,58 @@ def build(force: bool = False, extra_flags: list[str] | None = None, out: str | 
     return so
 
 
+_PAR_SO = os.path.join(_HERE, "_build", "libparcrs.so")
+_par = None
+
+
+def build_parcrs(force: bool = False) -> str:
+    """Compile parcrs.c (the paper's OpenMP row-parallel CRS baseline) with gcc -fopenmp;
+    without OpenMP support it is built sequential (parcrs_threads() then reports 1)."""
+    src = os.path.join(_HERE, "parcrs.c")
+    if not force and os.path.exists(_PAR_SO) and os.path.getmtime(_PAR_SO) >= os.path.getmtime(src):
+        return _PAR_SO
+    os.makedirs(os.path.dirname(_PAR_SO), exist_ok=True)
+    tmp = _PAR_SO + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+    try:
+        subprocess.check_call(base + ["-fopenmp", src, "-o", tmp], stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(base + [src, "-o", tmp])
+    os.replace(tmp, _PAR_SO)
+    return _PAR_SO
+
+
+def load_parcrs():
+    """Load the ParCRS baseline.  OMP_PROC_BIND defaults to true (Section 5.1); the OpenMP
+    runtime reads it when the library is loaded."""
+    global _par
+    with _lock:
+        if _par is None:
+            build_parcrs()
+            os.environ.setdefault("OMP_PROC_BIND", "true")
+            lib = ctypes.CDLL(_PAR_SO)
+            lib.parcrs_spmv.restype = None
+            lib.parcrs_spmv.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 5
+            lib.parcrs_threads.restype = ctypes.c_int
+            lib.parcrs_threads.argtypes = []
+            _par = lib
+    return _par
+
+
+def parcrs_spmv(row_ptr, col, val, x, out=None):
+    """y = A x by ParCRS on all host threads (FP64; equal to csr_spmv row for row)."""
+    lib = load_parcrs()
+    rp, co, vo, xx = _i32(row_ptr), _i32(col), _f64(val), _f64(x)
+    m = rp.size - 1
+    y = out if out is not None else np.empty(m)
+    lib.parcrs_spmv(m, _p(rp), _p(co), _p(vo), _p(xx), _p(y))
+    return y
+
+
+def parcrs_threads():
+    return int(load_parcrs().parcrs_threads())
+
+
 def _declare(lib):
     i64, u64, i32, dbl, p, f32, u16 = (ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_void_p, ctypes.c_float, ctypes.c_uint16)

@@ -1057,7 +1057,7 @@ spmv_status launch_slot(const spmv_matrix *h, const void *x, void *y, cudaStream
     static DeviceOnce attr;
     SPMV_TRY(attr([&] { return set_smem_ctas((const void *)k_merge_slot<SV, Acc>, smem, SLOT_CTAS); }));
     const unsigned grid = persistent_grid((const void *)k_merge_slot<SV, Acc>, SLOT_WARPS * 32, smem, h->tiles);
-    SPMV_LAUNCH("k_merge_spmv", s, (k_merge_slot<SV, Acc><<<grid, SLOT_WARPS * 32, smem, s>>>(
+    SPMV_LAUNCH("k_merge_slot", s, (k_merge_slot<SV, Acc><<<grid, SLOT_WARPS * 32, smem, s>>>(
                                        h->slot_desc, h->slot_col, (const SV *)h->slot_val, (const float *)x, (float *)y,
                                        h->carry_row, h->carry_val, h->tiles, h->status_dev + 3)));
     SPMV_LAUNCH_CHECK("merge spmv");
@@ -1089,7 +1089,7 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
                                                                               h->xsplit_flag)));
                 SPMV_LAUNCH_CHECK("x split");
             }
-            SPMV_LAUNCH("k_merge_spmv", s,
+            SPMV_LAUNCH("k_merge_slot_df", s,
                         (k_merge_slot_df<float2><<<grid, SLOT_WARPS * 32, ssmem, s>>>(
                             h->slot_desc, h->slot_col, h->slot_val2, (const double *)x, h->xsplit, h->xsplit_flag,
                             (double *)y, h->carry_row, h->carry_val, h->tiles, h->status_dev + 3)));
@@ -1103,7 +1103,7 @@ spmv_status launch_merge(const spmv_matrix *h, const void *x, void *y, bool allo
     static DeviceOnce attr;
     SPMV_TRY(attr([&] { return set_smem_ctas((const void *)k_merge_warp<VT, XT, AT>, smem, 5); }));
     const unsigned grid = persistent_grid((const void *)k_merge_warp<VT, XT, AT>, MW_WARPS * 32, smem, h->tiles);
-    SPMV_LAUNCH("k_merge_spmv", s, (k_merge_warp<VT, XT, AT><<<grid, MW_WARPS * 32, smem, s>>>(
+    SPMV_LAUNCH("k_merge_warp", s, (k_merge_warp<VT, XT, AT><<<grid, MW_WARPS * 32, smem, s>>>(
                                        h->merge_desc, h->col, (const VT *)h->val, (const XT *)x, (XT *)y, h->part_row,
                                        h->part_nz, h->carry_row, h->carry_val, h->tiles, h->status_dev + 3)));
     SPMV_LAUNCH_CHECK("merge spmv");
@@ -1380,7 +1380,7 @@ spmv_status launch_merge_comp(const spmv_matrix *h, const void *x, void *y, cuda
     static DeviceOnce attr;
     SPMV_TRY(attr([&] { return set_smem_ctas((const void *)k_merge_warp_comp<VT, Acc>, smem, 5); }));
     const unsigned grid = persistent_grid((const void *)k_merge_warp_comp<VT, Acc>, MW_WARPS * 32, smem, h->tiles);
-    SPMV_LAUNCH("k_merge_spmv", s, (k_merge_warp_comp<VT, Acc><<<grid, MW_WARPS * 32, smem, s>>>(
+    SPMV_LAUNCH("k_merge_warp_comp", s, (k_merge_warp_comp<VT, Acc><<<grid, MW_WARPS * 32, smem, s>>>(
                                        h->merge_desc, h->col, (const VT *)h->val, (const float *)x, (float *)y,
                                        h->part_row, h->part_nz, h->carry_row, h->carry_val, h->tiles,
                                        h->status_dev + 3)));
@@ -1532,7 +1532,7 @@ spmv_status mul_merge_pattern_split(const spmv_matrix *h, const double *x, const
         static DeviceOnce sattr;
         SPMV_TRY(sattr([&] { return set_smem_ctas((const void *)k_merge_slot_df<Pattern>, ssmem, SLOT_CTAS); }));
         const unsigned grid = persistent_grid((const void *)k_merge_slot_df<Pattern>, SLOT_WARPS * 32, ssmem, h->tiles);
-        SPMV_LAUNCH("k_merge_spmv", s, (k_merge_slot_df<Pattern><<<grid, SLOT_WARPS * 32, ssmem, s>>>(
+        SPMV_LAUNCH("k_merge_slot_df", s, (k_merge_slot_df<Pattern><<<grid, SLOT_WARPS * 32, ssmem, s>>>(
                                            h->slot_desc, h->slot_col, (const Pattern *)nullptr, x, x2, xflag, y,
                                            h->carry_row, h->carry_val, h->tiles, h->status_dev + 3)));
         SPMV_LAUNCH_CHECK("pattern merge spmv");
@@ -1543,7 +1543,7 @@ spmv_status mul_merge_pattern_split(const spmv_matrix *h, const double *x, const
     static DeviceOnce attr;
     SPMV_TRY(attr([&] { return set_smem_ctas((const void *)k_merge_warp_pat_df, smem, 5); }));
     const unsigned grid = persistent_grid((const void *)k_merge_warp_pat_df, MW_WARPS * 32, smem, h->tiles);
-    SPMV_LAUNCH("k_merge_spmv", s, (k_merge_warp_pat_df<<<grid, MW_WARPS * 32, smem, s>>>(
+    SPMV_LAUNCH("k_merge_warp_pat_df", s, (k_merge_warp_pat_df<<<grid, MW_WARPS * 32, smem, s>>>(
                                        h->merge_desc, h->col, x, x2, xflag, y, h->part_row, h->part_nz, h->carry_row,
                                        h->carry_val, h->tiles, h->status_dev + 3)));
     SPMV_LAUNCH_CHECK("pattern merge spmv");
