@@ -70,10 +70,15 @@ typedef enum {
 #define SPMV_INNER_HILBERT 0    /* Hilbert order (BCOHCH, Section 4.2)                  */
 #define SPMV_INNER_ROWMAJOR 1   /* row-wise (BCOHC, Section 4.2)                        */
 
+/* Product of the HB format. */
+#define SPMV_HB_STAGED 0        /* block column by block column, x slice staged on chip   */
+#define SPMV_HB_CHUNKED 1       /* Hilbert-ordered chunks, x gathered per nonzero          */
+
 typedef struct {
     int32_t log2_beta;    /* HB block side 2^log2_beta; 0 = Eq. 2 rule (Section 3.1)     */
     int32_t inner_order;  /* SPMV_INNER_*                                                */
     int32_t tile;         /* CSR_MERGE: path items per CTA tile; 0 = library default     */
+    int32_t hb_product;   /* HB: SPMV_HB_STAGED (default) or SPMV_HB_CHUNKED             */
 } spmv_convert_opts;
 
 /*
@@ -126,7 +131,16 @@ spmv_status spmv_create_coo(int64_t m, int64_t n, int64_t nnz, const int32_t *ro
  *   resolution, row_ptr by boundary fill, plus the algorithm's partition tables.
  *   HB: Hilbert key h(r, c) on the 2^K grid (K = ceil(log2 max(m, n))), radix sort on h
  *   (or on (h >> 2 log2_beta, r, c) for SPMV_INNER_ROWMAJOR), block segmentation,
- *   packed indices ((r mod beta) << 16 | (c mod beta)).  Requires beta <= 2^16.
+ *   packed indices ((r mod beta) << 16 | (c mod beta)).  Requires beta <= 2^16.  With
+ *   hb_product = SPMV_HB_STAGED (the default) the conversion also lays the blocks out for
+ *   the staged product (Sections 3.1, 3.2: the x slice of a block column held on chip):
+ *   the entries of every block column (a slice of beta columns) in CRS order, in warp tiles
+ *   of 256 entries of one 32-bit (row delta, column offset) word and the value each (one
+ *   stable radix pass on the block column from the CRS arrays).  Its product visits the
+ *   block columns in turn, copies each column's x slice into shared memory once per CTA and
+ *   adds row sums into y with reductions (y is zeroed first; the order of the additions
+ *   across runs is not fixed).  SPMV_HB_CHUNKED keeps the Hilbert-ordered product that
+ *   gathers x per nonzero.
  * opt may be NULL (defaults).  The CRS arrays are kept once built, so a later
  * conversion to another CSR algorithm or to HB reuses them.  The converted format
  * becomes the one spmv_mul uses.  Synchronises `stream` (status read-backs).  Errors:

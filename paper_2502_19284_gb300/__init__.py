@@ -31,6 +31,7 @@ SPMV_DEVICE_PTRS = 0x1
 SPMV_DUP_SUM = 0x0
 SPMV_DUP_ERROR = 0x2
 SPMV_INNER_HILBERT, SPMV_INNER_ROWMAJOR = 0, 1
+SPMV_HB_STAGED, SPMV_HB_CHUNKED = 0, 1
 SPMV_ACC_DEFAULT, SPMV_ACC_F32, SPMV_ACC_F64, SPMV_ACC_COMPENSATED, SPMV_ACC_SEGMENT = range(5)
 
 FORMATS = {"rowsplit": SPMV_FMT_CSR_ROWSPLIT, "merge": SPMV_FMT_CSR_MERGE, "hb": SPMV_FMT_HB, "auto": SPMV_FMT_AUTO}
@@ -38,7 +39,8 @@ ELEM_SIZE = {SPMV_F64: 8, SPMV_F32: 4, SPMV_BF16: 2, SPMV_PATTERN: 0}
 
 
 class spmv_convert_opts(ctypes.Structure):
-    _fields_ = [("log2_beta", ctypes.c_int32), ("inner_order", ctypes.c_int32), ("tile", ctypes.c_int32)]
+    _fields_ = [("log2_beta", ctypes.c_int32), ("inner_order", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("hb_product", ctypes.c_int32)]
 
 
 class spmv_info_t(ctypes.Structure):
@@ -197,10 +199,11 @@ def spmv_create_coo(m, n, row_ind, col_ind, data=None, dtype=None, flags=SPMV_DU
     return Handle(out.value)
 
 
-def spmv_convert(h: Handle, fmt="merge", log2_beta=0, inner_order=SPMV_INNER_HILBERT, tile=0, stream=None):
+def spmv_convert(h: Handle, fmt="merge", log2_beta=0, inner_order=SPMV_INNER_HILBERT, tile=0,
+                 hb_product=SPMV_HB_STAGED, stream=None):
     """Build a storage format (Section 5.1) and make it the active one."""
     f = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
-    opts = spmv_convert_opts(log2_beta, inner_order, tile)
+    opts = spmv_convert_opts(log2_beta, inner_order, tile, hb_product)
     _check(_lib.spmv_convert(h.ptr, f, ctypes.byref(opts), _stream(stream)), "spmv_convert")
 
 

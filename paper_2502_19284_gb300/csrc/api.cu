@@ -200,7 +200,7 @@ void release_slot(uint32_t *p) {
 void free_all(spmv_matrix *h) {
     void *ptrs[] = {h->coo_row, h->coo_col, h->coo_val, h->row_ptr, h->col, h->val, h->bin_rows,
                     h->part_row, h->part_nz, h->carry_row, h->carry_val, h->merge_desc, h->hb_idx, h->hb_val,
-                    h->blk_ptr, h->blk_row, h->blk_col, h->hb_chunk_blk, h->xsplit, h->xsplit_flag, h->slot_desc, h->slot_col, h->slot_val2, h->slot_val, h->fix_len, h->fix_long,
+                    h->blk_ptr, h->blk_row, h->blk_col, h->hb_chunk_blk, h->st_hdr, h->st_words, h->st_vals, h->st_slice_tile, h->st_lmeta, h->st_part, h->xsplit, h->xsplit_flag, h->slot_desc, h->slot_col, h->slot_val2, h->slot_val, h->fix_len, h->fix_long,
                     h->pr_inv, h->pr_z, h->pr_z2, h->pr_y, h->pr_part, h->status_dev};
     if (h->pr_graph) cudaGraphExecDestroy((cudaGraphExec_t)h->pr_graph);
     for (void *p : ptrs) dev_free(p);
@@ -371,7 +371,7 @@ spmv_status spmv_convert(spmv_handle h, spmv_format f, const spmv_convert_opts *
     SPMV_TRY(check_handle(h));
     forget_batch_plans(h);
     cudaStream_t s = (cudaStream_t)stream;
-    spmv_convert_opts o = {0, SPMV_INNER_HILBERT, 0};
+    spmv_convert_opts o = {0, SPMV_INNER_HILBERT, 0, SPMV_HB_STAGED};
     if (opt) o = *opt;
     if (f == SPMV_FMT_AUTO) {
         // Row-length statistics decide: very long rows favour the merge path (it splits
@@ -392,6 +392,10 @@ spmv_status spmv_convert(spmv_handle h, spmv_format f, const spmv_convert_opts *
         set_error("spmv_convert: log2_beta must be in [1, 16] (0 = Eq. 2 rule)");
         return SPMV_ERR_INVALID_ARG;
     }
+    if (o.hb_product != SPMV_HB_STAGED && o.hb_product != SPMV_HB_CHUNKED) {
+        set_error("spmv_convert: unknown HB product");
+        return SPMV_ERR_INVALID_ARG;
+    }
     if (o.tile != 0 && o.tile != MERGE_WARP_ITEMS) {
         set_error("spmv_convert: only the default merge tile (224 path items per warp) is built in");
         return SPMV_ERR_UNSUPPORTED;
@@ -399,12 +403,14 @@ spmv_status spmv_convert(spmv_handle h, spmv_format f, const spmv_convert_opts *
     if (!h->has_csr) SPMV_TRY(build_csr(h, s));
     if (f == SPMV_FMT_CSR_ROWSPLIT && !h->has_bins) SPMV_TRY(build_bins(h, s));
     if (f == SPMV_FMT_CSR_MERGE && !h->has_merge) SPMV_TRY(build_merge(h, MERGE_WARP_ITEMS, s));
-    if (f != SPMV_FMT_HB) SPMV_TRY(build_df(h, s));
+    SPMV_TRY(build_df(h, s));
     if (f == SPMV_FMT_HB) {
         int lb = o.log2_beta ? o.log2_beta : default_log2_beta(h->n, h->dt == SPMV_F64 ? 8 : 4);
         const int K = bits_for(std::max<int64_t>(std::max(h->m, h->n), 2));
         if (lb > K) lb = K;
         if (!h->has_hb || h->log2beta != lb || h->inner != o.inner_order) SPMV_TRY(build_hb(h, lb, o.inner_order, s));
+        if (o.hb_product == SPMV_HB_STAGED && (!h->has_stage || h->stage_lb != lb)) SPMV_TRY(build_stage(h, lb, s));
+        h->hb_chunked = o.hb_product == SPMV_HB_CHUNKED;
     }
     SPMV_CUDA_TRY(cudaStreamSynchronize(s));
     h->format = (int32_t)f;

@@ -206,6 +206,21 @@ struct spmv_matrix {
     int32_t *blk_ptr = nullptr, *blk_row = nullptr, *blk_col = nullptr;
     int32_t *hb_chunk_blk = nullptr;  // block of the first nonzero of every HB_CHUNK chunk (+ last block)
 
+    // blocked layout of the staged-x product (stage.cu): the block columns (slices of 2^stage_lb
+    // columns) in CRS order, cut into warp tiles of 256 entries (32-bit row delta | column
+    // word plus the value), with a 16-byte header per tile and the first tile of every slice
+    bool has_stage = false;
+    int32_t stage_lb = 0, stage_kind = 0;
+    int64_t stage_nsl = 0, stage_tiles = 0, stage_bytes = 0;
+    int4 *st_hdr = nullptr;
+    uint32_t *st_words = nullptr;
+    void *st_vals = nullptr;
+    uint32_t *st_slice_tile = nullptr;
+    uint2 *st_lmeta = nullptr;        // per tile and lane: row of the lane's first item, output offset and flags
+    int32_t *st_part = nullptr;       // first tile of every CTA of the product (cost-balanced)
+    int32_t stage_parts = 0;
+    bool hb_chunked = false;          // the HB product walks the Hilbert-ordered chunks instead
+
     // FP64 through double-float arithmetic (df64.cuh): set when every stored value lies in
     // the double-float window; x is split into float pairs per product (scratch below)
     bool df_checked = false, df_ok = false;

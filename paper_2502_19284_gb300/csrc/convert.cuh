@@ -56,6 +56,13 @@ spmv_status mul_merge(const spmv_matrix *h, const void *x, void *y, spmv_dtype v
 // (the FP64 products use double-float arithmetic when acc == SPMV_ACC_DEFAULT and h->df_ok)
 spmv_status mul_rowsplit(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s);
 spmv_status mul_hb(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s);
+// Staged-x blocked layout and product (stage.cu), built from the CRS arrays with slices of
+// 2^lb columns; free_stage releases it in stream order.
+spmv_status build_stage(spmv_matrix *h, int lb, cudaStream_t s);
+void free_stage(spmv_matrix *h, cudaStream_t s);
+spmv_status mul_stage(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s);
+// x -> float pairs in h->xsplit, with the window flag h->xsplit_flag reset and set (spmv.cu).
+spmv_status split_x(const spmv_matrix *h, const double *x, cudaStream_t s);
 // Bounded-wait check: one warp waits `polls` polls on an mbarrier nothing arrives at and sets
 // ST_TIMEOUT in *status (device word) when it gives up.
 spmv_status test_wait(long long polls, uint32_t *status, cudaStream_t s);

@@ -22,6 +22,8 @@
 #include "common.cuh"
 #include "convert.cuh"
 #include "df64.cuh"
+#include "acc.cuh"
+#include "tma.cuh"
 
 #include <algorithm>
 #include <mutex>
@@ -30,95 +32,10 @@ namespace spmv {
 
 namespace {
 
-// ---------------------------------------------------------------- element access
-struct Pattern {};   // value type tag of a pattern matrix (every stored value is 1)
-
-template <typename VT, typename AT>
-__device__ __forceinline__ AT ld_val(const VT *__restrict__ v, int64_t k) {
-    if constexpr (std::is_same<VT, Pattern>::value) {
-        return AT(1);
-    } else if constexpr (std::is_same<VT, __nv_bfloat16>::value) {
-        return AT(__bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16 *>(v) + k)));
-    } else {
-        return AT(__ldg(v + k));
-    }
-}
-
-template <typename XT, typename AT>
-__device__ __forceinline__ AT ld_x(const XT *__restrict__ x, int64_t j) {
-    return AT(__ldg(x + j));
-}
-
 inline unsigned cdivu(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 // ================================================================ merge path
 constexpr int MP_BLOCK = MERGE_BLOCK;
-
-// Accumulators.  NativeAcc<AT> sums in AT with one fma per nonzero.  DfAcc keeps an FP64
-// sum as a float pair (double-float, df64.cuh) so that the FP64 path runs on the FP32
-// pipes; its operands arrive already split into (hi, lo) floats.
-template <typename AT>
-struct NativeAcc {
-    using Op = AT;   // operand type of one side of a product
-    AT v;
-    __device__ __forceinline__ void zero() { v = AT(0); }
-    __device__ __forceinline__ void mad(Op a, Op x) { v = fma(a, x, v); }
-    __device__ __forceinline__ void add(const NativeAcc &o) { v = v + o.v; }
-    __device__ __forceinline__ NativeAcc shfl_up(int o) const { NativeAcc r; r.v = __shfl_up_sync(0xffffffffu, v, o); return r; }
-    __device__ __forceinline__ double to_double() const { return (double)v; }
-    template <typename XT> __device__ __forceinline__ XT out() const { return XT(v); }
-};
-
-struct DfAcc {
-    using Op = float2;
-    float s, c;
-    __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
-    __device__ __forceinline__ void mad(float2 a, float2 x) { df_fma(a.x, a.y, x.x, x.y, s, c); }
-    __device__ __forceinline__ void add(const DfAcc &o) { df_add(s, c, o.s, o.c); }
-    __device__ __forceinline__ DfAcc shfl_up(int o) const {
-        DfAcc r;
-        r.s = __shfl_up_sync(0xffffffffu, s, o);
-        r.c = __shfl_up_sync(0xffffffffu, c, o);
-        return r;
-    }
-    __device__ __forceinline__ double to_double() const { return df_to_double(s, c); }
-    template <typename XT> __device__ __forceinline__ XT out() const { return XT(df_to_double(s, c)); }
-};
-
-// FP32 sum with compensation (SPMV_ACC_COMPENSATED): the rounding error of every product
-// (FMA) and of every addition (TwoSum, Knuth) is collected in a second float, as in
-// Neumaier's compensated summation; the result carries ~2^-46 relative error in the sum of
-// |terms| instead of FP32's L * 2^-24.
-struct CompAcc {
-    using Op = float;
-    float s, c;
-    __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
-    __device__ __forceinline__ void mad(float a, float x) { df_fma(a, 0.f, x, 0.f, s, c); }
-    __device__ __forceinline__ void add(const CompAcc &o) { df_add(s, c, o.s, o.c); }
-    __device__ __forceinline__ CompAcc shfl_up(int o) const {
-        CompAcc r;
-        r.s = __shfl_up_sync(0xffffffffu, s, o);
-        r.c = __shfl_up_sync(0xffffffffu, c, o);
-        return r;
-    }
-    __device__ __forceinline__ double to_double() const { return df_to_double(s, c); }
-    template <typename XT> __device__ __forceinline__ XT out() const { return XT(__fadd_rn(s, c)); }
-};
-
-// FP32 products and sums inside a lane (at most MERGE_WARP_IPT terms), compensated only in
-// the segmented reduction that joins lanes and tiles (SPMV_ACC_SEGMENT): a row contained in
-// one lane costs plain FP32; a longer row's lane partials are combined with TwoSum, so its
-// error stays at the short in-lane sums' ~7u instead of growing with the row length.
-struct SegAcc : CompAcc {
-    __device__ __forceinline__ void mad(float a, float x) { s = __fmaf_rn(a, x, s); }
-    __device__ __forceinline__ SegAcc shfl_up(int o) const {
-        SegAcc r;
-        r.s = __shfl_up_sync(0xffffffffu, s, o);
-        r.c = __shfl_up_sync(0xffffffffu, c, o);
-        return r;
-    }
-    __device__ __forceinline__ void add(const SegAcc &o) { df_add(s, c, o.s, o.c); }
-};
 
 // Operand loaders: native (value converted to AT) or split into double-float pairs.
 template <typename VT, typename AT>
@@ -295,29 +212,6 @@ __global__ __launch_bounds__(MP_BLOCK) void k_merge_spmv(const int32_t *__restri
 constexpr int MW_WARPS = 4;
 constexpr int MW_IPT = MERGE_WARP_IPT;
 constexpr int MW_ITEMS = 32 * MW_IPT;
-constexpr long long MW_SPIN_LIMIT = 1ll << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// L2 eviction policies: the streamed matrix arrays are read once (evict first), the gathered
-// x is reused across the whole product (evict last), so the stream does not push x out of L2.
-__device__ __forceinline__ uint64_t l2_policy_evict_first() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ uint64_t l2_policy_evict_last() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-// 1-D bulk copy global -> shared (TMA), completion counted on an mbarrier.
-__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar, uint64_t pol) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
-        :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol) : "memory");
-}
 
 // Widen the element range [e0, e1) of an array of `es`-byte elements to 16-byte boundaries:
 // returns the first element copied and the byte count.
@@ -328,12 +222,6 @@ __device__ __forceinline__ void widen16(int64_t e0, int64_t e1, int es, int64_t 
     *bytes = e1 > e0 ? (uint32_t)((a1 - a0) * es) : 0u;
 }
 
-template <typename VT, typename AT>
-__device__ __forceinline__ AT sval(const VT *v, int k) {
-    if constexpr (std::is_same<VT, Pattern>::value) return AT(1);
-    else if constexpr (std::is_same<VT, __nv_bfloat16>::value) return AT(__bfloat162float(v[k]));
-    else return AT(v[k]);
-}
 
 // Operand loaders from a tile slot (values as stored, x from the gather buffer).
 template <typename VT, typename AT>
@@ -387,15 +275,6 @@ __device__ __forceinline__ void merge_warp_issue(const uint32_t *__restrict__ de
     if (col_bytes) tma_load_1d(slot + Slot::OFF_COL, col + col_first, col_bytes, bar, pol);
     if constexpr (Slot::VAL_BYTES > 0)
         if (val_bytes) tma_load_1d(slot + Slot::OFF_VAL, val + val_first, val_bytes, bar, pol);
-}
-
-// Bounded wait for phase `parity` of a slot barrier (all lanes); false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit = MW_SPIN_LIMIT) {
-    uint32_t done = 0;
-    for (long long it = 0; it < limit && !done; ++it)
-        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                     : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-    return __all_sync(0xffffffffu, done);
 }
 
 // Lane descriptor fields (see k_merge_desc in the conversion).
@@ -1517,7 +1396,18 @@ spmv_status mul_rowsplit(const spmv_matrix *h, const void *x, void *y, spmv_dtyp
 }
 spmv_status test_wait(long long polls, uint32_t *status, cudaStream_t s) { return launch_test_wait(polls, status, s); }
 spmv_status mul_hb(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s) {
+    if (h->has_stage && !h->hb_chunked) return mul_stage(h, x, y, vdt, acc, s);
     return dispatch(HB, h, x, y, vdt, acc, s);
+}
+
+spmv_status split_x(const spmv_matrix *h, const double *x, cudaStream_t s) {
+    SPMV_CUDA_TRY(cudaMemsetAsync(h->xsplit_flag, 0, 4, s));
+    if (h->n > 0) {
+        SPMV_LAUNCH("k_df_split_x", s,
+                    (k_df_split_x<<<cdivu((h->n + 1) / 2, 256), 256, 0, s>>>(x, h->n, h->xsplit, h->xsplit_flag)));
+        SPMV_LAUNCH_CHECK("x split");
+    }
+    return SPMV_OK;
 }
 
 spmv_status mul_csr_merge_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col,

@@ -73,7 +73,7 @@ def test_precision_modes(sp, kind):
             for algo, modes in (("merge", (sp.SPMV_ACC_F32, sp.SPMV_ACC_COMPENSATED, sp.SPMV_ACC_SEGMENT,
                                            sp.SPMV_ACC_F64)),
                                 ("rowsplit", (sp.SPMV_ACC_F32, sp.SPMV_ACC_F64)),
-                                ("hb", (sp.SPMV_ACC_F32,))):
+                                ("hb", (sp.SPMV_ACC_F32, sp.SPMV_ACC_SEGMENT, sp.SPMV_ACC_COMPENSATED))):
                 sp.spmv_convert(h, algo)
                 for acc in modes:
                     if kind == "pattern" and acc == sp.SPMV_ACC_F64:
@@ -86,7 +86,9 @@ def test_precision_modes(sp, kind):
                     if integer:
                         np.testing.assert_array_equal(yg, ref, err_msg=f"{name} {algo} acc{acc}")
                         continue
-                    if acc == sp.SPMV_ACC_F32:
+                    if acc == sp.SPMV_ACC_F32 or algo == "hb":
+                        # the blocked product joins a row's runs with FP32 reductions in y, so
+                        # its compensated modes keep the FP32 bound (any order of L + 1 roundings)
                         g = (L + 1) * U / (1 - (L + 1) * U)
                         bound = g * scale + U * np.abs(ref)
                     elif acc == sp.SPMV_ACC_COMPENSATED:
