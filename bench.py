@@ -73,11 +73,12 @@ def row_bytes(m, n, nnz, nblk):
 PRODUCTS = ("spmv_rowsplit", "spmv_merge", "spmv_merge_f64", "spmv_hb")
 # the main kernel of each product row (its name in the library's trace and in ncu)
 PRODUCT_KERNEL = {"spmv_rowsplit": "k_rowsplit", "spmv_merge": "k_merge_slot_df", "spmv_merge_f64": "k_merge_warp",
-                  "spmv_hb": "k_hb_spmv"}
+                  "spmv_hb": "k_hb_stage"}
 PRODUCT_DESC = {"spmv_rowsplit": "row-split CSR (the paper's ParCRS on the GPU), FP64 through double-float",
                 "spmv_merge": "merge-path CSR, FP64 through double-float (split FP64 operands, ~2^-47 relative)",
                 "spmv_merge_f64": "merge-path CSR, native FP64 arithmetic (SPMV_ACC_F64)",
-                "spmv_hb": "Hilbert-blocked (beta 2^14), FP64"}
+                "spmv_hb": ("Hilbert-blocked (beta 2^14), block columns with x slices staged in shared memory, "
+                            "FP64 through double-float")}
 
 
 def sort_passes(bits):
@@ -107,6 +108,7 @@ def kernel_bytes(name, m, n, nnz, nblk):
         "k_merge_warp": spmv_bytes(m, n, nnz),
         "k_rowsplit": spmv_bytes(m, n, nnz),
         "k_hb_spmv": nnz * 12 + nblk * 12 + n * 8 + m * 8,
+        "k_hb_stage": nnz * 12 + nblk * 12 + n * 8 + m * 8,
     }
     return table.get(name)
 
@@ -117,7 +119,8 @@ def kernel_units(name, m, n, nnz):
     cbits = max(1, (n - 1).bit_length()) if n > 1 else 1
     rbits = max(1, (m - 1).bit_length()) if m > 1 else 1
     return {"k_rs_scatter": (sort_passes(cbits + rbits) + sort_passes(2 * K)) * nnz + m,
-            "k_merge_slot_df": nnz, "k_hb_spmv": nnz, "k_rowsplit": nnz, "k_merge_warp": nnz}.get(name)
+            "k_merge_slot_df": nnz, "k_hb_spmv": nnz, "k_hb_stage": nnz, "k_rowsplit": nnz,
+            "k_merge_warp": nnz}.get(name)
 
 
 def rel_err(y, ref, scale):

@@ -847,12 +847,11 @@ __global__ void k_merge_fixup(int64_t tiles, int64_t m, const int32_t *__restric
 // Persistent grid: resident CTAs on every SM (occupancy from the runtime), never more
 // warps than tiles.
 inline unsigned persistent_grid(const void *kernel, int block, size_t smem, int64_t tiles) {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
+    int dev = 0, sms = 1;   // the current device's SM count (a process may drive several GPUs)
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        sms = 1;
     }
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess || per_sm < 1) {

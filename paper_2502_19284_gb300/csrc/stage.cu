@@ -211,6 +211,8 @@ __global__ void k_st_counts(const int32_t *__restrict__ slice_start, const uint3
     }
     const int64_t tot = (int64_t)(E[slice_start[lo + 1]] - E[slice_start[lo]]);
     hdr[t].z = (int)min((int64_t)ST_TILE, tot - (t - (int64_t)slice_tile[lo]) * ST_TILE);
+    // bit 1 of .w: the first tile of a slice large enough to be staged (its copy costs time)
+    if (t == (int64_t)slice_tile[lo] && slice_tile[lo + 1] - slice_tile[lo] >= (uint32_t)ST_STAGE_MIN) hdr[t].w |= 2;
 }
 
 // Lane headers of every tile (one warp per tile), computed from the words exactly as the
@@ -261,14 +263,23 @@ __global__ void k_st_meta(const uint32_t *__restrict__ words, int4 *__restrict__
 
 // Cost of every tile for the split between CTAs, in units of one run sum (a shared-memory
 // round trip and a reduction in L2): ST_TILE_COST for the tile's 256 entries plus its run
-// sums (the weight that balanced the CTAs best on R-MAT scale 22); cost[ntiles] = 0.
+// sums, plus ST_STAGE_COST at the first tile of a slice whose x slice gets staged (the
+// weights that balanced the CTAs best on R-MAT scale 22); cost[ntiles] = 0.
 #ifndef ST_TILE_COST_CFG
 #define ST_TILE_COST_CFG 256
+#endif
+#ifndef ST_STAGE_COST_CFG
+#define ST_STAGE_COST_CFG 8192
 #endif
 __global__ void k_st_cost(const int4 *__restrict__ hdr, int64_t ntiles, uint32_t *__restrict__ cost) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t > ntiles) return;
-    cost[t] = t == ntiles ? 0u : (uint32_t)ST_TILE_COST_CFG + ((uint32_t)hdr[t].w >> 8);
+    if (t == ntiles) {
+        cost[t] = 0u;
+        return;
+    }
+    const uint32_t w = (uint32_t)hdr[t].w;
+    cost[t] = (uint32_t)ST_TILE_COST_CFG + (w >> 8) + ((w & 2u) ? (uint32_t)ST_STAGE_COST_CFG : 0u);
 }
 
 // First tile of every CTA: equal shares of the prefix-summed cost.
@@ -608,7 +619,7 @@ __device__ __forceinline__ void st_run(const StArgs<SV, YT> &a, const XS *__rest
     auto tile = [&](const StRegs<SV> &T, int64_t t) {
         wk.advance(a, t, xs, xg, &sbar);
         if (wk.dead) return;
-        const bool clean = T.hd.z == ST_TILE && (T.hd.w & 0xFF) == 0;
+        const bool clean = T.hd.z == ST_TILE && (T.hd.w & 1) == 0;
         if (wk.staged) {
             if (clean) st_tile<true, true, Acc, SV, XS, YT>(T, xs, xg, a.lb, a.n, a.m, obuf, a.y, a.err);
             else st_tile<true, false, Acc, SV, XS, YT>(T, xs, xg, a.lb, a.n, a.m, obuf, a.y, a.err);
