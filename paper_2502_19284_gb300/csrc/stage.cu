@@ -64,62 +64,54 @@ inline unsigned cdivu(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b)
 
 // ================================================================ conversion
 
-// Row of every CRS entry: a thread takes 8 consecutive entries, finds the row of the first
-// by bisection of row_ptr and walks forward.
-__global__ void k_st_rowid(const int32_t *__restrict__ row_ptr, int64_t m, int64_t nnz, int32_t *__restrict__ rowid) {
-    const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8;
-    if (k0 >= nnz) return;
-    int64_t lo = 0, hi = m - 1;   // largest r with row_ptr[r] <= k0
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if ((int64_t)row_ptr[mid] <= k0) lo = mid;
-        else hi = mid - 1;
-    }
-    int64_t r = lo;
-    const int64_t k1 = min(k0 + 8, nnz);
-    for (int64_t k = k0; k < k1; ++k) {
-        while ((int64_t)row_ptr[r + 1] <= k) ++r;
-        rowid[k] = (int32_t)r;
-    }
+// Rows of the CRS entries without a search: f[k] counts the rows r >= 1 that start at entry
+// k (empty rows share their start), so the row of entry k is the sum of f[0..k].
+__global__ void k_st_rowflags(const int32_t *__restrict__ row_ptr, int64_t m, int64_t nnz, uint32_t *__restrict__ f) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1;
+    if (r >= m) return;
+    const int64_t k = row_ptr[r];
+    if (k < nnz) atomicAdd(f + k, 1u);
 }
 
-// Sort keys: the slice of every CRS entry (stable sort keeps the CRS order inside a slice).
-__global__ void k_st_keys(const int32_t *__restrict__ col, int64_t nnz, int lb, uint64_t *__restrict__ keys,
-                          uint32_t *__restrict__ perm) {
+// Sort keys: (row << 32) | column of every CRS entry, with the entry's position as the
+// payload; the sort runs on the block-column bits (column >> lb), so that it keeps the CRS
+// order inside a block column and every later pass reads rows and columns from the keys.
+// rows[k + 1] is the row of entry k (exclusive prefix sum of the row flags).
+__global__ void k_st_keys(const uint32_t *__restrict__ rows, const int32_t *__restrict__ col, int64_t nnz,
+                          uint64_t *__restrict__ keys, uint32_t *__restrict__ perm) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nnz) return;
-    keys[k] = (uint64_t)((uint32_t)col[k] >> lb);
+    keys[k] = ((uint64_t)rows[k + 1] << 32) | (uint32_t)col[k];
     perm[k] = (uint32_t)k;
 }
 
+__device__ __forceinline__ int64_t st_slice(uint64_t key, int lb) { return (int64_t)((uint32_t)key >> lb); }
+__device__ __forceinline__ int64_t st_row(uint64_t key) { return (int64_t)(key >> 32); }
+
 // Row delta of sorted entry e to the previous entry of its slice (0 for a slice's first).
-__device__ __forceinline__ int64_t st_delta(const uint64_t *skey, const uint32_t *perm, const int32_t *rowid,
-                                            int64_t e, int64_t *row) {
-    const uint64_t s = skey[e];
-    *row = rowid[perm[e]];
-    if (e == 0 || skey[e - 1] != s) return 0;
-    return *row - (int64_t)rowid[perm[e - 1]];
+__device__ __forceinline__ int64_t st_delta(const uint64_t *skey, int64_t e, int lb) {
+    const uint64_t k = skey[e];
+    if (e == 0 || st_slice(skey[e - 1], lb) != st_slice(k, lb)) return 0;
+    return st_row(k) - st_row(skey[e - 1]);
 }
 
 // cnt[e] = 1 + the fillers that precede entry e; slice_start[s] = first sorted entry of
 // slice s (entries of empty slices point at the next non-empty one); cnt[nnz] = 0.
-__global__ void k_st_count(const uint64_t *__restrict__ skey, const uint32_t *__restrict__ perm,
-                           const int32_t *__restrict__ rowid, int64_t nnz, int64_t nsl, int64_t dmax,
+__global__ void k_st_count(const uint64_t *__restrict__ skey, int64_t nnz, int64_t nsl, int lb, int64_t dmax,
                            uint32_t *__restrict__ cnt, int32_t *__restrict__ slice_start) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e > nnz) return;
     if (e == nnz) {
         cnt[nnz] = 0;
-        const int64_t last = nnz ? (int64_t)skey[nnz - 1] : -1;
+        const int64_t last = nnz ? st_slice(skey[nnz - 1], lb) : -1;
         for (int64_t q = last + 1; q <= nsl; ++q) slice_start[q] = (int32_t)nnz;
         return;
     }
-    const int64_t s = (int64_t)skey[e];
-    const int64_t sp = e ? (int64_t)skey[e - 1] : -1;
+    const int64_t s = st_slice(skey[e], lb);
+    const int64_t sp = e ? st_slice(skey[e - 1], lb) : -1;
     if (sp != s)
         for (int64_t q = sp + 1; q <= s; ++q) slice_start[q] = (int32_t)e;
-    int64_t row;
-    const int64_t dr = st_delta(skey, perm, rowid, e, &row);
+    const int64_t dr = st_delta(skey, e, lb);
     cnt[e] = 1u + (uint32_t)(dr > dmax ? (dr - 1) / dmax : 0);
 }
 
@@ -164,15 +156,16 @@ __device__ __forceinline__ SV st_value(const VT *val, int64_t p) {
 // tile that holds a filler.  Padding and the headers stay as zeroed by the caller.
 template <typename SV, typename VT>
 __global__ void k_st_fill(const uint64_t *__restrict__ skey, const uint32_t *__restrict__ perm,
-                          const int32_t *__restrict__ rowid, const int32_t *__restrict__ col, const VT *__restrict__ val,
-                          const uint32_t *__restrict__ E, const int32_t *__restrict__ slice_start,
-                          const uint32_t *__restrict__ slice_tile, int64_t nnz, int lb, int64_t dmax,
-                          uint32_t *__restrict__ words, SV *__restrict__ sval, int4 *__restrict__ hdr) {
+                          const VT *__restrict__ val, const uint32_t *__restrict__ E,
+                          const int32_t *__restrict__ slice_start, const uint32_t *__restrict__ slice_tile,
+                          int64_t nnz, int lb, int64_t dmax, uint32_t *__restrict__ words, SV *__restrict__ sval,
+                          int4 *__restrict__ hdr) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nnz) return;
-    const int64_t s = (int64_t)skey[e];
-    int64_t row;
-    const int64_t dr = st_delta(skey, perm, rowid, e, &row);
+    const uint64_t key = skey[e];
+    const int64_t s = st_slice(key, lb);
+    const int64_t row = st_row(key);
+    const int64_t dr = st_delta(skey, e, lb);
     const int64_t f = dr > dmax ? (dr - 1) / dmax : 0;
     const int64_t base = (int64_t)slice_tile[s] * ST_TILE;
     const int64_t q0 = base + (int64_t)(E[e] - E[slice_start[s]]);
@@ -188,7 +181,7 @@ __global__ void k_st_fill(const uint64_t *__restrict__ skey, const uint32_t *__r
         }
     }
     const int64_t q = q0 + f;
-    const uint32_t coff = (uint32_t)col[perm[e]] & ((1u << lb) - 1u);
+    const uint32_t coff = (uint32_t)key & ((1u << lb) - 1u);
     words[st_pos<4>(q)] = ((uint32_t)(dr - f * dmax) << lb) | coff;
     if constexpr (!std::is_same<SV, Pattern>::value) sval[st_pos<(int)sizeof(SV)>(q)] = st_value<SV, VT>(val, perm[e]);
     if ((q & (ST_TILE - 1)) == 0) {
@@ -664,12 +657,12 @@ inline unsigned st_grid(int64_t n) { return std::max(1u, cdivu(n, ST_CB)); }
 enum : int32_t { ST_NONE = 0, ST_F2 = 1, ST_F64 = 2, ST_F32 = 3, ST_BF16 = 4 };
 
 template <typename SV, typename VT>
-spmv_status st_fill_launch(const uint64_t *Ks, const uint32_t *Ps, const int32_t *rowid, const spmv_matrix *h,
-                           const uint32_t *E, const int32_t *sstart, const uint32_t *stile, int lb, int64_t dmax,
-                           uint32_t *words, void *vals, int4 *hdr, cudaStream_t s) {
+spmv_status st_fill_launch(const uint64_t *Ks, const uint32_t *Ps, const spmv_matrix *h, const uint32_t *E,
+                           const int32_t *sstart, const uint32_t *stile, int lb, int64_t dmax, uint32_t *words,
+                           void *vals, int4 *hdr, cudaStream_t s) {
     SPMV_LAUNCH("k_st_fill", s, (k_st_fill<SV, VT><<<st_grid(h->nnz), ST_CB, 0, s>>>(
-                                     Ks, Ps, rowid, h->col, (const VT *)h->val, E, sstart, stile, h->nnz, lb, dmax,
-                                     words, (SV *)vals, hdr)));
+                                     Ks, Ps, (const VT *)h->val, E, sstart, stile, h->nnz, lb, dmax, words, (SV *)vals,
+                                     hdr)));
     SPMV_LAUNCH_CHECK("stage fill");
     return SPMV_OK;
 }
@@ -821,8 +814,7 @@ spmv_status build_stage(spmv_matrix *h, int lb, cudaStream_t s) {
     int64_t ntiles = 0;
     int G = 0;
     if (nnz > 0 && nsl > 0) {
-        DevBuf rowid(s), keys(s), keys_alt(s), perm(s), perm_alt(s), cnt(s), E(s), sstart(s), tiles(s), tmp(s);
-        SPMV_TRY(rowid.alloc((size_t)nnz * 4, "stage rows"));
+        DevBuf keys(s), keys_alt(s), perm(s), perm_alt(s), cnt(s), E(s), sstart(s), tiles(s), tmp(s);
         SPMV_TRY(keys.alloc((size_t)nnz * 8, "stage keys"));
         SPMV_TRY(keys_alt.alloc((size_t)nnz * 8, "stage keys"));
         SPMV_TRY(perm.alloc((size_t)nnz * 4, "stage perm"));
@@ -833,21 +825,25 @@ spmv_status build_stage(spmv_matrix *h, int lb, cudaStream_t s) {
         SPMV_TRY(tiles.alloc((size_t)(nsl + 1) * 4, "stage slice tiles"));
         SPMV_TRY(stile.alloc((size_t)(nsl + 1) * 4, "stage slice tiles"));
         SPMV_TRY(tmp.alloc(std::max(radix_temp_bytes(nnz), scan_temp_bytes(nnz + 1)), "stage sort temp"));
-        SPMV_LAUNCH("k_st_rowid", s, (k_st_rowid<<<st_grid((nnz + 7) / 8), ST_CB, 0, s>>>(h->row_ptr, m, nnz,
-                                                                                        rowid.as<int32_t>())));
-        SPMV_LAUNCH_CHECK("stage rows");
-        SPMV_LAUNCH("k_st_keys", s, (k_st_keys<<<st_grid(nnz), ST_CB, 0, s>>>(h->col, nnz, lb, keys.as<uint64_t>(),
-                                                                             perm.as<uint32_t>())));
+        SPMV_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, (size_t)(nnz + 1) * 4, s));
+        if (m > 1) {
+            SPMV_LAUNCH("k_st_rowflags", s, (k_st_rowflags<<<st_grid(m - 1), ST_CB, 0, s>>>(h->row_ptr, m, nnz,
+                                                                                          cnt.as<uint32_t>())));
+            SPMV_LAUNCH_CHECK("stage row flags");
+        }
+        SPMV_TRY(exclusive_scan_u32(cnt.as<uint32_t>(), E.as<uint32_t>(), nnz + 1, tmp.p, s));
+        SPMV_LAUNCH("k_st_keys", s, (k_st_keys<<<st_grid(nnz), ST_CB, 0, s>>>(E.as<uint32_t>(), h->col, nnz,
+                                                                             keys.as<uint64_t>(), perm.as<uint32_t>())));
         SPMV_LAUNCH_CHECK("stage keys");
         bool alt = false;
         SPMV_CUDA_TRY(cudaMemsetAsync(h->status_dev + 1, 0, 4, s));
         SPMV_TRY(radix_sort_pairs(keys.as<uint64_t>(), keys_alt.as<uint64_t>(), perm.as<uint32_t>(),
-                                  perm_alt.as<uint32_t>(), nnz, 0, bits_for(std::max<int64_t>(nsl, 2)), tmp.p, s, &alt,
+                                  perm_alt.as<uint32_t>(), nnz, lb, lb + bits_for(std::max<int64_t>(nsl, 2)), tmp.p, s, &alt,
                                   h->status_dev + 1));
         const uint64_t *Ks = alt ? keys_alt.as<uint64_t>() : keys.as<uint64_t>();
         const uint32_t *Ps = alt ? perm_alt.as<uint32_t>() : perm.as<uint32_t>();
         SPMV_LAUNCH("k_st_count", s, (k_st_count<<<st_grid(nnz + 1), ST_CB, 0, s>>>(
-                                         Ks, Ps, rowid.as<int32_t>(), nnz, nsl, dmax, cnt.as<uint32_t>(),
+                                         Ks, nnz, nsl, lb, dmax, cnt.as<uint32_t>(),
                                          sstart.as<int32_t>())));
         SPMV_LAUNCH_CHECK("stage count");
         SPMV_TRY(exclusive_scan_u32(cnt.as<uint32_t>(), E.as<uint32_t>(), nnz + 1, tmp.p, s));
@@ -877,19 +873,18 @@ spmv_status build_stage(spmv_matrix *h, int lb, cudaStream_t s) {
             SPMV_TRY(vals.alloc((size_t)ntiles * ST_TILE * vs, "stage values"));
             SPMV_CUDA_TRY(cudaMemsetAsync(vals.p, 0, (size_t)ntiles * ST_TILE * vs, s));
         }
-        const int32_t *rid = rowid.as<int32_t>();
         const uint32_t *Ep = E.as<uint32_t>(), *st = stile.as<uint32_t>();
         const int32_t *ss = sstart.as<int32_t>();
         uint32_t *w = words.as<uint32_t>();
         int4 *hp = hdr.as<int4>();
         switch (kind) {
-            case ST_F2: SPMV_TRY((st_fill_launch<float2, double>(Ks, Ps, rid, h, Ep, ss, st, lb, dmax, w, vals.p, hp, s))); break;
-            case ST_F64: SPMV_TRY((st_fill_launch<double, double>(Ks, Ps, rid, h, Ep, ss, st, lb, dmax, w, vals.p, hp, s))); break;
-            case ST_F32: SPMV_TRY((st_fill_launch<float, float>(Ks, Ps, rid, h, Ep, ss, st, lb, dmax, w, vals.p, hp, s))); break;
+            case ST_F2: SPMV_TRY((st_fill_launch<float2, double>(Ks, Ps, h, Ep, ss, st, lb, dmax, w, vals.p, hp, s))); break;
+            case ST_F64: SPMV_TRY((st_fill_launch<double, double>(Ks, Ps, h, Ep, ss, st, lb, dmax, w, vals.p, hp, s))); break;
+            case ST_F32: SPMV_TRY((st_fill_launch<float, float>(Ks, Ps, h, Ep, ss, st, lb, dmax, w, vals.p, hp, s))); break;
             case ST_BF16:
-                SPMV_TRY((st_fill_launch<__nv_bfloat16, __nv_bfloat16>(Ks, Ps, rid, h, Ep, ss, st, lb, dmax, w, vals.p, hp, s)));
+                SPMV_TRY((st_fill_launch<__nv_bfloat16, __nv_bfloat16>(Ks, Ps, h, Ep, ss, st, lb, dmax, w, vals.p, hp, s)));
                 break;
-            default: SPMV_TRY((st_fill_launch<Pattern, Pattern>(Ks, Ps, rid, h, Ep, ss, st, lb, dmax, w, vals.p, hp, s))); break;
+            default: SPMV_TRY((st_fill_launch<Pattern, Pattern>(Ks, Ps, h, Ep, ss, st, lb, dmax, w, vals.p, hp, s))); break;
         }
         SPMV_LAUNCH("k_st_counts", s, (k_st_counts<<<st_grid(ntiles), ST_CB, 0, s>>>(ss, Ep, st, nsl, ntiles, hp)));
         SPMV_LAUNCH_CHECK("stage counts");
