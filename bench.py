@@ -262,32 +262,32 @@ def cpu_baselines(ref, reps_oracle=3, reps_par=10):
 
 # ------------------------------------------------------------------ serving leg
 
-SERVE = dict(n_matrices=16, scales=(14, 20), edge_factor=16, budget=150 << 30, slots=8, max_batch=64,
-             rates=(2000.0, 10000.0), requests=2000, pagerank_frac=0.2, pagerank_iters=20, damping=0.85)
+SERVE = dict(n_matrices=64, scales=(14, 24), edge_factor=16, budget=150 << 30, slots=8, max_batch=64,
+             rates=(1000.0, 5000.0, 10000.0, 20000.0, 50000.0), requests=2000, pagerank_frac=0.2, pagerank_iters=20,
+             damping=0.85, check_scale=18)
 
 
 def serving_leg(sp, torch, dev, synth, np):
     """Poisson arrivals of SpMV (FP32 values and vectors) and 20-iteration PageRank requests
     on a resident set of R-MAT matrices, through the serving loop, against the same trace on
     the plain one-at-a-time FP64 path (FP64 copies of the matrices, one synchronous call per
-    request in arrival order).  Latency = completion - arrival."""
+    request in arrival order).  Latency = completion - arrival.  Edges are drawn on the GPU
+    (synth's twin of the host generator), duplicates summed at ingestion."""
     cfg = SERVE
     rng = np.random.Generator(np.random.PCG64(77))
     scales = rng.integers(cfg["scales"][0], cfg["scales"][1] + 1, size=cfg["n_matrices"])
     h32, h64, xs, ys, prs, x64s, y64s, pr64s, ns = [], [], [], [], [], [], [], [], []
-    big = int(np.argmax(scales))
-    big_inputs = None
+    big = int(np.argmin(np.abs(scales - cfg["check_scale"])))   # the matrix checked against the oracle
+    nnz_total = 0
     for i, sc in enumerate(scales):
         n = 1 << int(sc)
-        r, c = synth.rmat(int(sc), cfg["edge_factor"], seed=1000 + i)
-        v = synth.values(r, c, seed=1000 + i)
-        if i == big:
-            big_inputs = (r, c, v)
-        rd, cd = torch.from_numpy(r).to(dev), torch.from_numpy(c).to(dev)
-        a = sp.spmv_create_coo(n, n, rd, cd, torch.from_numpy(v.astype(np.float32)).to(dev))
+        rd, cd = synth.gpu_rmat_raw(int(sc), cfg["edge_factor"], seed=1000 + i, device=dev)
+        a = sp.spmv_create_coo(n, n, rd, cd, synth.gpu_values(rd, cd, seed=1000 + i, f32=True))
         sp.spmv_convert(a, "merge")
-        b = sp.spmv_create_coo(n, n, rd, cd, torch.from_numpy(v).to(dev))
+        b = sp.spmv_create_coo(n, n, rd, cd, synth.gpu_values(rd, cd, seed=1000 + i))
         sp.spmv_convert(b, "auto")
+        del rd, cd
+        nnz_total += sp.spmv_info(a)["nnz"]
         h32.append(a)
         h64.append(b)
         x = synth.vector(n, seed=2000 + i)
@@ -304,35 +304,61 @@ def serving_leg(sp, torch, dev, synth, np):
     dx = [torch.empty(n, dtype=torch.float64, device=dev) for n in ns]
     dy = [torch.empty(n, dtype=torch.float64, device=dev) for n in ns]
     out = {"config": {"matrices": int(cfg["n_matrices"]), "scales": [int(v) for v in scales],
-                      "edge_factor": cfg["edge_factor"], "values": "f32 (served) / f64 (plain)",
+                      "nnz": int(nnz_total), "edge_factor": cfg["edge_factor"],
+                      "values": "f32 (served) / f64 (plain); duplicate edges summed",
                       "mix": f"{1 - cfg['pagerank_frac']:.0%} SpMV / {cfg['pagerank_frac']:.0%} PageRank-"
                              f"{cfg['pagerank_iters']}", "budget_bytes": cfg["budget"], "slots": cfg["slots"],
                       "max_batch": cfg["max_batch"], "requests_per_rate": cfg["requests"],
                       "resident_bytes": srv.stats()["resident_bytes"]},
            "rates": []}
-    # accuracy of a served FP32 product against the oracle (largest matrix): Algorithm 1 in
-    # FP64 on the stored FP32 values and FP32 x (accumulation error) and on the original FP64
-    # values and x (total error), both as max_i |y_i - ref_i| / (|A||x|)_i
+    # accuracy of a served FP32 product against the oracle (the matrix of scale closest to
+    # check_scale): Algorithm 1 in FP64 on the FP32-rounded triplet values and FP32 x
+    # (accumulation error; the library also sums duplicate triplets in FP32) and on the
+    # original FP64 values and x (total error), both as max_i |y_i - ref_i| / (|A||x|)_i
     import oracle
     t = srv.submit(sp.Server.request(sp.SPMV_REQ_SPMV, ids[big], ys[big], x=xs[big]))
     srv.wait(t)
     a_ = ys[big].numpy().astype(np.float64)
-    br, bc, bv = big_inputs
+    br, bc = synth.rmat_raw(int(scales[big]), cfg["edge_factor"], seed=1000 + big)
+    bv = synth.values(br, bc, seed=1000 + big)
     nb = ns[big]
     rp, co, vo = oracle.coo_to_csr(nb, nb, br, bc, bv)
+    _, _, vo32 = oracle.coo_to_csr(nb, nb, br, bc, bv.astype(np.float32).astype(np.float64))
     x64 = x64s[big].numpy()
     x32r = xs[big].numpy().astype(np.float64)
-    vo32 = vo.astype(np.float32).astype(np.float64)
     out["accuracy"] = {
         "reference": "oracle (Algorithm 1, FP64)",
         "max_accumulation_err": rel_err(a_, oracle.csr_spmv(rp, co, vo32, x32r), oracle.csr_absmul(rp, co, vo32, x32r)),
         "max_total_err": rel_err(a_, oracle.csr_spmv(rp, co, vo, x64), oracle.csr_absmul(rp, co, vo, x64)),
         "matrix_scale": int(scales[big])}
     del rp, co, vo, vo32
+    # service time of every request kind and matrix alone (device events, FP32 handles): the
+    # bound on throughput for a trace served one request at a time with the GPU to itself
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    t_spmv, t_pr = [], []
+    for i, h in enumerate(h32):
+        xd = xs[i].to(dev)
+        yd = torch.empty(ns[i], dtype=torch.float32, device=dev)
+        prd = torch.empty(ns[i], dtype=torch.float64, device=dev)
+        sp.spmv_mul(h, xd, yd)
+        sp.spmv_pagerank(h, prd, cfg["damping"], cfg["pagerank_iters"])
+        e = [ev() for _ in range(3)]
+        e[0].record()
+        sp.spmv_mul(h, xd, yd)
+        e[1].record()
+        sp.spmv_pagerank(h, prd, cfg["damping"], cfg["pagerank_iters"])
+        e[2].record()
+        torch.cuda.synchronize()
+        t_spmv.append(e[0].elapsed_time(e[1]))
+        t_pr.append(e[1].elapsed_time(e[2]))
+        del xd, yd, prd
+    out["service_ms_alone"] = {"spmv_mean": round(float(np.mean(t_spmv)), 4), "pagerank_mean": round(float(np.mean(t_pr)), 3),
+                               "spmv_max": round(float(np.max(t_spmv)), 4), "pagerank_max": round(float(np.max(t_pr)), 3)}
     for rate in cfg["rates"]:
         N = cfg["requests"]
         kind, mat = synth.request_mix(N, len(ns), cfg["pagerank_frac"], seed=int(rate))
         arr = synth.poisson_arrivals(rate, N, seed=int(rate))
+        busy_ms = float(sum(t_pr[m] if k == 1 else t_spmv[m] for k, m in zip(kind, mat)))
         reqs = []
         for k, m in zip(kind, mat):
             if k == 1:
@@ -371,7 +397,8 @@ def serving_leg(sp, torch, dev, synth, np):
         plain = {"p50_ms": round(float(np.percentile(plat, 50)) * 1e3, 3),
                  "p99_ms": round(float(np.percentile(plat, 99)) * 1e3, 3),
                  "throughput_rps": round(N / float(np.max(arr + plat)), 1)}
-        out["rates"].append({"rate_rps": rate, "served": served, "plain_fp64": plain})
+        out["rates"].append({"rate_rps": rate, "served": served, "plain_fp64": plain,
+                             "one_at_a_time_capacity_rps": round(N / (busy_ms * 1e-3), 1)})
     srv.close()
     for h in h32 + h64:
         sp.spmv_destroy(h)
@@ -380,47 +407,86 @@ def serving_leg(sp, torch, dev, synth, np):
 
 # ------------------------------------------------------------------ batched leg
 
-BATCH = dict(n_matrices=64, scales=(10, 18), edge_factors=(8, 32), ks=(1, 4, 16), reps=5)
-BATCH_FULL = dict(n_matrices=512, scales=(10, 20), edge_factors=(8, 32), ks=(1, 4, 16), reps=3)
+BATCH = dict(n_matrices=512, scales=(10, 20), edge_factors=(8, 32), ks=(1, 4, 16), reps=3, oracle_checks=6)
+BATCH_SMALL = dict(n_matrices=64, scales=(10, 18), edge_factors=(8, 32), ks=(1, 4, 16), reps=5, oracle_checks=6)
 
 
 def batched_leg(sp, torch, dev, synth, np, cfg):
     """Many R-MAT matrices of uneven size (FP32 values) times k FP32 right-hand sides in one
     captured batched launch (spmv_mul_batch), against the plain path: one FP64 spmv_mul per
-    matrix and right-hand side.  GFLOP/s = 2 nnz k / time (device events)."""
+    matrix and right-hand side.  Edges are drawn on the GPU (synth's GPU twin of the host
+    generator) and ingested with duplicates summed.  Before the k = 1 batch the autotuner
+    times every format and product per matrix and keeps the fastest (row-split, merge-path,
+    staged blocked, chunked blocked); k > 1 batches run on the merge-path tiles.  A sample of
+    matrices is checked against the oracle.  GFLOP/s = 2 nnz k / time (device events)."""
+    import oracle
     rng = np.random.Generator(np.random.PCG64(88))
     scales = rng.integers(cfg["scales"][0], cfg["scales"][1] + 1, size=cfg["n_matrices"])
     efs = rng.integers(cfg["edge_factors"][0], cfg["edge_factors"][1] + 1, size=cfg["n_matrices"])
-    h32, h64, ns, nnz_total = [], [], [], 0
+    h32, h64, ns, nnz_total, edges_total = [], [], [], 0, 0
+    t0 = time.perf_counter()
     for i, (sc, ef) in enumerate(zip(scales, efs)):
         n = 1 << int(sc)
-        r, c = synth.rmat(int(sc), int(ef), seed=5000 + i)
-        v = synth.values(r, c, seed=5000 + i)
-        rd, cd = torch.from_numpy(r).to(dev), torch.from_numpy(c).to(dev)
-        a = sp.spmv_create_coo(n, n, rd, cd, torch.from_numpy(v.astype(np.float32)).to(dev))
+        rd, cd = synth.gpu_rmat_raw(int(sc), int(ef), seed=5000 + i, device=dev)
+        a = sp.spmv_create_coo(n, n, rd, cd, synth.gpu_values(rd, cd, seed=5000 + i, f32=True))
         sp.spmv_convert(a, "merge")
-        b = sp.spmv_create_coo(n, n, rd, cd, torch.from_numpy(v).to(dev))
+        b = sp.spmv_create_coo(n, n, rd, cd, synth.gpu_values(rd, cd, seed=5000 + i))
         sp.spmv_convert(b, "merge")
+        del rd, cd
         h32.append(a)
         h64.append(b)
         ns.append(n)
         nnz_total += sp.spmv_info(a)["nnz"]
-    out = {"config": {"matrices": int(cfg["n_matrices"]), "scales": [int(cfg["scales"][0]), int(cfg["scales"][1])],
-                      "edge_factors": [int(cfg["edge_factors"][0]), int(cfg["edge_factors"][1])], "nnz": int(nnz_total),
-                      "values": "f32 batched / f64 plain", "rhs": "f32 batched / f64 plain"}, "k": []}
+        edges_total += int(ef) << int(sc)
+    build_s = time.perf_counter() - t0
     ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def time_batch(k, X, Y, reps):
+        sp.spmv_mul_batch(h32, X, Y, k=k, accum=sp.SPMV_ACC_F32)          # plan + graph capture
+        torch.cuda.synchronize()
+        a_, b_ = ev(), ev()
+        a_.record()
+        for _ in range(reps):
+            sp.spmv_mul_batch(h32, X, Y, k=k, accum=sp.SPMV_ACC_F32)
+        b_.record()
+        torch.cuda.synchronize()
+        return a_.elapsed_time(b_) / reps
+
+    X1 = [torch.randn(n, 1, dtype=torch.float32, device=dev) for n in ns]
+    Y1 = [torch.empty(n, 1, dtype=torch.float32, device=dev) for n in ns]
+    ms_untuned = time_batch(1, X1, Y1, cfg["reps"])     # every matrix on the merge-path tiles
+    del X1, Y1
+    t0 = time.perf_counter()
+    choice = {}
+    for h in h32:
+        res = sp.spmv_tune(h, "f32", accum=sp.SPMV_ACC_F32, hb=True)
+        choice[res["chosen"]] = choice.get(res["chosen"], 0) + 1
+    tune_s = time.perf_counter() - t0
+    out = {"config": {"matrices": int(cfg["n_matrices"]), "scales": [int(cfg["scales"][0]), int(cfg["scales"][1])],
+                      "edge_factors": [int(cfg["edge_factors"][0]), int(cfg["edge_factors"][1])],
+                      "edges": int(edges_total), "nnz": int(nnz_total),
+                      "values": "f32 batched / f64 plain (duplicate edges summed)", "rhs": "f32 batched / f64 plain",
+                      "generate_convert_s": round(build_s, 2), "tune_s": round(tune_s, 2)},
+           "autotuner_choice": choice,
+           "k1_all_merge_ms": round(ms_untuned, 4),
+           "k1_all_merge_gflops": round(2.0 * nnz_total / ms_untuned / 1e6, 1), "k": []}
+    checked = []
+    t0, t1 = ev(), ev()
     for k in cfg["ks"]:
         X = [torch.randn(n, k, dtype=torch.float32, device=dev) for n in ns]
         Y = [torch.empty(n, k, dtype=torch.float32, device=dev) for n in ns]
-        sp.spmv_mul_batch(h32, X, Y, k=k)          # plan + graph capture
-        torch.cuda.synchronize()
-        t0, t1 = ev(), ev()
-        t0.record()
-        for _ in range(cfg["reps"]):
-            sp.spmv_mul_batch(h32, X, Y, k=k)
-        t1.record()
-        torch.cuda.synchronize()
-        ms_b = t0.elapsed_time(t1) / cfg["reps"]
+        ms_b = time_batch(k, X, Y, cfg["reps"])
+        if k == 1:   # oracle check of a sample of matrices (evenly spaced over the batch)
+            for i in np.linspace(0, len(ns) - 1, cfg["oracle_checks"]).astype(int).tolist():
+                n = ns[i]
+                rr, cc = synth.rmat_raw(int(scales[i]), int(efs[i]), seed=5000 + i)
+                vv = synth.values(rr, cc, seed=5000 + i).astype(np.float32).astype(np.float64)
+                rp, co, vo = oracle.coo_to_csr(n, n, rr, cc, vv)
+                xr = X[i][:, 0].double().cpu().numpy()
+                yr = oracle.csr_spmv(rp, co, vo, xr)
+                sc_ = oracle.csr_absmul(rp, co, vo, xr)
+                checked.append({"matrix": i, "scale": int(scales[i]), "nnz": int(co.size),
+                                "max_err": rel_err(Y[i][:, 0].double().cpu().numpy(), yr, sc_)})
         # plain: one FP64 product per matrix and column
         X64 = [x.double() for x in X]
         cols = [[x[:, q].contiguous() for q in range(k)] for x in X64]
@@ -437,10 +503,14 @@ def batched_leg(sp, torch, dev, synth, np, cfg):
         ms_p = t0.elapsed_time(t1)
         flops = 2.0 * nnz_total * k
         out["k"].append({"k": k, "batched_ms": round(ms_b, 4), "batched_gflops": round(flops / ms_b / 1e6, 1),
-                         "plain_fp64_ms": round(ms_p, 4), "plain_fp64_gflops": round(flops / ms_p / 1e6, 1)})
+                         "plain_fp64_ms": round(ms_p, 4), "plain_fp64_gflops": round(flops / ms_p / 1e6, 1),
+                         "speedup": round(ms_p / ms_b, 2)})
         del X, Y, X64, cols, y64
+    out["oracle_checks"] = {"reference": "oracle (Algorithm 1, FP64) on the FP32-rounded values, k = 1",
+                            "accumulation": "f32", "matrices": checked}
     for h in h32 + h64:
         sp.spmv_destroy(h)
+    torch.cuda.synchronize()
     return out
 
 
@@ -534,7 +604,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
-    ap.add_argument("--batched-full", action="store_true", help="512 matrices, scales 10-20")
+    ap.add_argument("--batched-small", action="store_true", help="64 matrices, scales 10-18")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -766,7 +836,7 @@ def main():
     # ---- extension legs (outside the timed region)
     serving = None if args.no_serving else serving_leg(sp, torch, dev, synth, np)
     batched = None if args.no_batched else batched_leg(sp, torch, dev, synth, np,
-                                                         BATCH_FULL if args.batched_full else BATCH)
+                                                         BATCH_SMALL if args.batched_small else BATCH)
     precision = None if args.no_precision else precision_leg(sp, torch, dev, synth, np)
 
     if world > 1:

@@ -51,7 +51,8 @@ class spmv_info_t(ctypes.Structure):
 
 
 class spmv_tune_result(ctypes.Structure):
-    _fields_ = [("chosen", ctypes.c_int32), ("reps", ctypes.c_int32), ("ms", ctypes.c_float * 3), ("pad_", ctypes.c_int32)]
+    _fields_ = [("chosen", ctypes.c_int32), ("reps", ctypes.c_int32), ("ms", ctypes.c_float * 4),
+                ("hb_product", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 SPMV_TUNE_HB = 0x1
@@ -342,7 +343,11 @@ def spmv_tune(h: Handle, vec_dtype="f64", accum=SPMV_ACC_DEFAULT, hb=False, stre
     vdt = SPMV_F64 if vec_dtype in ("f64", SPMV_F64) else SPMV_F32
     _check(_lib.spmv_tune(h.ptr, vdt, accum, SPMV_TUNE_HB if hb else 0, ctypes.byref(r), _stream(stream)), "spmv_tune")
     names = {SPMV_FMT_CSR_ROWSPLIT: "rowsplit", SPMV_FMT_CSR_MERGE: "merge", SPMV_FMT_HB: "hb"}
-    return {"chosen": names[r.chosen], "ms": dict(zip(["rowsplit", "merge", "hb"], [float(v) for v in r.ms]))}
+    chosen = names[r.chosen]
+    if r.chosen == SPMV_FMT_HB and r.hb_product == SPMV_HB_CHUNKED:
+        chosen = "hb_chunked"
+    ms = dict(zip(["rowsplit", "merge", "hb", "hb_chunked"], [float(v) for v in r.ms]))
+    return {"chosen": chosen, "ms": {k: v for k, v in ms.items() if v >= 0}}
 
 
 class Server:

@@ -473,25 +473,30 @@ spmv_status spmv_tune(spmv_handle h, spmv_dtype vec_dt, uint32_t accum, uint32_t
     if (h->dt == SPMV_F64) SPMV_TRY(build_df(h, s));
     if ((flags & SPMV_TUNE_HB) && !h->has_hb)
         SPMV_TRY(build_hb(h, default_log2_beta(h->n, h->dt == SPMV_F64 ? 8 : 4), SPMV_INNER_HILBERT, s));
+    if ((flags & SPMV_TUNE_HB) && h->has_hb && !h->has_stage) SPMV_TRY(build_stage(h, h->log2beta, s));
     spmv_tune_result r;
     r.reps = 5;
     r.pad_ = 0;
+    r.hb_product = SPMV_HB_STAGED;
     for (float &v : r.ms) v = -1.f;
     const int es = vec_dt == SPMV_F64 ? 8 : 4;
     DevBuf x(s), y(s);
     SPMV_TRY(x.alloc((size_t)std::max<int64_t>(h->n, 1) * es, "tune x"));
     SPMV_TRY(y.alloc((size_t)std::max<int64_t>(h->m, 1) * es, "tune y"));
     SPMV_CUDA_TRY(cudaMemsetAsync(x.p, 0, (size_t)std::max<int64_t>(h->n, 1) * es, s));
-    const int32_t fmts[3] = {SPMV_FMT_CSR_ROWSPLIT, SPMV_FMT_CSR_MERGE, SPMV_FMT_HB};
+    const int32_t fmts[4] = {SPMV_FMT_CSR_ROWSPLIT, SPMV_FMT_CSR_MERGE, SPMV_FMT_HB, SPMV_FMT_HB};
+    const bool chunked[4] = {false, false, false, true};
     cudaEvent_t e0, e1;
     SPMV_CUDA_TRY(cudaEventCreate(&e0));
     SPMV_CUDA_TRY(cudaEventCreate(&e1));
     const int32_t keep = h->format;
+    const bool keep_chunked = h->hb_chunked;
     spmv_status st = SPMV_OK;
     int best = -1;
-    for (int f = 0; f < 3 && st == SPMV_OK; ++f) {
-        if (fmts[f] == SPMV_FMT_HB && !h->has_hb) continue;
+    for (int f = 0; f < 4 && st == SPMV_OK; ++f) {
+        if (fmts[f] == SPMV_FMT_HB && (!h->has_hb || (!chunked[f] && !h->has_stage))) continue;
         h->format = fmts[f];
+        h->hb_chunked = chunked[f];
         std::vector<float> t;
         for (int rep = 0; rep < 2 + 2 * r.reps && st == SPMV_OK; ++rep) {
             cudaEventRecord(e0, s);
@@ -517,6 +522,7 @@ spmv_status spmv_tune(spmv_handle h, spmv_dtype vec_dt, uint32_t accum, uint32_t
     cudaEventDestroy(e1);
     if (st != SPMV_OK || best < 0) {
         h->format = keep;
+        h->hb_chunked = keep_chunked;
         if (st == SPMV_OK) {
             set_error("spmv_tune: no format supports this product");
             st = SPMV_ERR_UNSUPPORTED;
@@ -524,7 +530,9 @@ spmv_status spmv_tune(spmv_handle h, spmv_dtype vec_dt, uint32_t accum, uint32_t
         return st;
     }
     h->format = fmts[best];
+    h->hb_chunked = chunked[best];
     r.chosen = fmts[best];
+    r.hb_product = chunked[best] ? SPMV_HB_CHUNKED : SPMV_HB_STAGED;
     if (out) *out = r;
     return SPMV_OK;
 }

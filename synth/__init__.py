@@ -37,6 +37,69 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+_GPU_SO = os.path.join(_HERE, "_build", "libsynth_gpu.so")
+_gpu = None
+
+
+def build_gpu(force: bool = False) -> str:
+    """Compile synth_gpu.cu (the GPU twin of the R-MAT and value draws) for sm_103a."""
+    src = os.path.join(_HERE, "synth_gpu.cu")
+    if not force and os.path.exists(_GPU_SO) and os.path.getmtime(_GPU_SO) >= os.path.getmtime(src):
+        return _GPU_SO
+    os.makedirs(os.path.dirname(_GPU_SO), exist_ok=True)
+    tmp = _GPU_SO + f".tmp{os.getpid()}"
+    nvcc = os.environ.get("NVCC") or "nvcc"
+    if not os.path.exists(nvcc) and os.path.exists("/usr/local/cuda/bin/nvcc"):
+        nvcc = "/usr/local/cuda/bin/nvcc"
+    subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-Xcompiler", "-fPIC",
+                           "-shared", src, "-o", tmp])
+    os.replace(tmp, _GPU_SO)
+    return _GPU_SO
+
+
+def _load_gpu():
+    global _gpu
+    with _lock:
+        if _gpu is None:
+            build_gpu()
+            lib = ctypes.CDLL(_GPU_SO)
+            i64, u64, i32, dbl, p = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+            lib.synth_gpu_rmat.restype = i32
+            lib.synth_gpu_rmat.argtypes = [i32, i64, dbl, dbl, dbl, u64, p, p, p]
+            lib.synth_gpu_values.restype = i32
+            lib.synth_gpu_values.argtypes = [i64, p, p, u64, i32, i32, p, p]
+            _gpu = lib
+    return _gpu
+
+
+def gpu_rmat_raw(scale: int, edge_factor: int = 16, seed: int = 0, abcd=RMAT_ABCD, device="cuda", stream=None):
+    """R-MAT edges drawn on the GPU, duplicates kept: (rows, cols) int32 torch tensors on
+    `device`, equal to rmat_raw's arrays."""
+    import torch
+    e = int(edge_factor * (1 << scale))
+    rows = torch.empty(e, dtype=torch.int32, device=device)
+    cols = torch.empty(e, dtype=torch.int32, device=device)
+    a, b, c, _ = abcd
+    st = stream if stream is not None else torch.cuda.current_stream(rows.device).cuda_stream
+    rc = _load_gpu().synth_gpu_rmat(scale, e, a, b, c, seed, rows.data_ptr(), cols.data_ptr(), st)
+    if rc != 0:
+        raise RuntimeError(f"synth_gpu_rmat: CUDA error {rc}")
+    return rows, cols
+
+
+def gpu_values(rows, cols, seed: int = 0, integer: bool = False, f32: bool = False, stream=None):
+    """values(rows, cols, seed) computed on the GPU (torch tensors in, a float64 or, with f32,
+    float32 tensor out: the doubles rounded to nearest even)."""
+    import torch
+    out = torch.empty(rows.numel(), dtype=torch.float32 if f32 else torch.float64, device=rows.device)
+    st = stream if stream is not None else torch.cuda.current_stream(rows.device).cuda_stream
+    rc = _load_gpu().synth_gpu_values(rows.numel(), rows.data_ptr(), cols.data_ptr(), seed, 1 if integer else 0,
+                                      1 if f32 else 0, out.data_ptr(), st)
+    if rc != 0:
+        raise RuntimeError(f"synth_gpu_values: CUDA error {rc}")
+    return out
+
+
 def _load():
     global _lib
     with _lock:
@@ -48,6 +111,8 @@ def _load():
             lib.synth_draw.argtypes = [u64, u64]
             lib.synth_stream_key.restype = u64
             lib.synth_stream_key.argtypes = [u64, u64]
+            lib.synth_rmat_raw.restype = None
+            lib.synth_rmat_raw.argtypes = [i32, i64, dbl, dbl, dbl, u64, p, p]
             lib.synth_rmat.restype = i64
             lib.synth_rmat.argtypes = [i32, i64, dbl, dbl, dbl, u64, p, p]
             lib.synth_values.restype = None
@@ -87,6 +152,17 @@ def rmat(scale: int, edge_factor: int = 16, seed: int = 0, abcd=RMAT_ABCD, edges
     if nnz < 0:
         raise MemoryError("synth_rmat: out of host memory")
     return rows[:nnz].copy(), cols[:nnz].copy()
+
+
+def rmat_raw(scale: int, edge_factor: int = 16, seed: int = 0, abcd=RMAT_ABCD):
+    """The R-MAT edges exactly as drawn (duplicates kept, edge order): (rows, cols) int32."""
+    lib = _load()
+    e = int(edge_factor * (1 << scale))
+    rows = np.empty(e, dtype=np.int32)
+    cols = np.empty(e, dtype=np.int32)
+    a, b, c, _ = abcd
+    lib.synth_rmat_raw(scale, e, a, b, c, seed, _ptr(rows), _ptr(cols))
+    return rows, cols
 
 
 def values(rows: np.ndarray, cols: np.ndarray, seed: int = 0, integer: bool = False) -> np.ndarray:

@@ -176,6 +176,13 @@ int64_t synth_rmat(int scale, int64_t edges, double a, double b, double c, uint6
     return w;
 }
 
+/* R-MAT edges exactly as drawn, duplicates kept (the first step of synth_rmat). */
+void synth_rmat_raw(int scale, int64_t edges, double a, double b, double c, uint64_t seed, int32_t *rows,
+                    int32_t *cols) {
+    rmat_arg g = {scale, synth_stream_key(seed, STREAM_EDGES), a, a + b, a + b + c, rows, cols};
+    parallel_for(edges, rmat_body, &g);
+}
+
 /* ------------------------------------------------------------------ values */
 typedef struct { uint64_t key; int kind; const int32_t *rows, *cols; double *out; } val_arg;
 

@@ -1,5 +1,6 @@
 """Input generators: determinism, shapes and distributions of the synthetic workloads."""
 import numpy as np
+import pytest
 
 import oracle
 import synth
@@ -65,3 +66,31 @@ def test_poisson_arrivals_and_mix():
     assert np.array_equal(t, synth.poisson_arrivals(1000.0, 20000, seed=3))
     kind, mat = synth.request_mix(20000, 7, 0.2, seed=3)
     assert abs(kind.mean() - 0.2) < 0.02 and set(np.unique(mat)) == set(range(7))
+
+
+def test_rmat_raw_dedup_is_rmat():
+    """The raw edge list, reduced to the first occurrence of every (row, col), in edge order,
+    is synth.rmat's output."""
+    r, c = synth.rmat_raw(11, 16, seed=5)
+    key = r.astype(np.int64) << 32 | c.astype(np.int64)
+    _, first = np.unique(key, return_index=True)
+    first.sort()
+    r2, c2 = synth.rmat(11, 16, seed=5)
+    assert np.array_equal(r[first], r2) and np.array_equal(c[first], c2)
+
+
+@pytest.mark.gpu
+def test_gpu_generator_matches_host_bit_for_bit():
+    """The GPU twin draws the same edges and values as the host generator."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    for scale, ef, seed in [(12, 16, 0), (9, 8, 77)]:
+        rd, cd = synth.gpu_rmat_raw(scale, ef, seed, device="cuda:0")
+        r, c = synth.rmat_raw(scale, ef, seed)
+        assert np.array_equal(rd.cpu().numpy(), r) and np.array_equal(cd.cpu().numpy(), c)
+        for integer in (False, True):
+            v = synth.values(r, c, seed, integer=integer)
+            assert np.array_equal(synth.gpu_values(rd, cd, seed, integer=integer).cpu().numpy(), v)
+            assert np.array_equal(synth.gpu_values(rd, cd, seed, integer=integer, f32=True).cpu().numpy(),
+                                  v.astype(np.float32))
