@@ -583,10 +583,33 @@ def precision_leg(sp, torch, dev, synth, np):
                                        "gbs": round(nbytes / ms / 1e6, 1), "gflops": round(2 * r.size / ms / 1e6, 1),
                                        "max_accumulation_err": rel_err(yh, y_ref, s_ref),
                                        "max_total_err": None if kind == "pattern" else rel_err(yh, y_exact, s_exact)})
+            if kind == "f32":   # compensation threshold tau of the row-split product
+                sp.spmv_convert(h, "rowsplit")
+                sweep = []
+                for tau in TAUS:
+                    sp.spmv_set_compensation_threshold(h, tau)
+                    sp.spmv_mul(h, xin, y, accum=sp.SPMV_ACC_SEGMENT)
+                    torch.cuda.synchronize()
+                    t0, t1 = ev(), ev()
+                    t0.record()
+                    for _ in range(5):
+                        sp.spmv_mul(h, xin, y, accum=sp.SPMV_ACC_SEGMENT)
+                    t1.record()
+                    torch.cuda.synchronize()
+                    sweep.append({"tau": tau, "ms": round(t0.elapsed_time(t1) / 5, 4),
+                                  "max_accumulation_err": rel_err(y.double().cpu().numpy(), y_ref, s_ref)})
+                full = sweep[0]["max_accumulation_err"]
+                ok = [e for e in sweep if e["max_accumulation_err"] <= 1.5 * full]
+                entry["tau_sweep"] = {"product": "row-split, FP32 values and vectors, SPMV_ACC_SEGMENT",
+                                      "rule": "largest tau whose error stays within 1.5x of compensating every row",
+                                      "chosen_tau": max(e["tau"] for e in ok), "points": sweep}
             sp.spmv_destroy(h)
         out.append(entry)
         del rp, co, vo
     return out
+
+
+TAUS = (0, 2, 4, 8, 16, 32, 2048, 1 << 40)
 
 
 # ------------------------------------------------------------------ main

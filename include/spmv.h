@@ -226,6 +226,23 @@ typedef struct {
 spmv_status spmv_tune(spmv_handle h, spmv_dtype vec_dt, uint32_t accum, uint32_t flags, spmv_tune_result *out,
                       void *stream);
 
+/*
+ * spmv_set_compensation_threshold -- the threshold tau of SPMV_ACC_SEGMENT for the row-split
+ * product (FP32 vectors): rows are summed in plain FP32 where their length class (<= 2, 4, 8,
+ * 16, 32, 2048 entries, or longer) lies within tau entries, and with compensated FP32 (the FMA
+ * error of every product and the TwoSum error of every addition, through the lane sums and
+ * the butterfly that joins them) where it can reach beyond tau.  tau = 0 compensates every
+ * row (as SPMV_ACC_COMPENSATED); a tau at or beyond the longest row compensates none.  The
+ * paper has no counterpart (it does not discuss precision).  The merge-path product's
+ * SPMV_ACC_SEGMENT keeps its structural threshold: rows longer than one lane's seven items,
+ * whose partial sums it joins across lanes and tiles.  Default SPMV_COMP_TAU_DEFAULT = 0, from a
+ * sweep over tau on Erdos-Renyi (8 per row) and Zipf(1.8) rows on GB300: the row-split product is
+ * memory-bound, so compensating every row costs no measurable time (within 0.5%), while plain
+ * FP32 sums of rows of 8 entries already double the error.  SPMV_ERR_INVALID_ARG for tau < 0.
+ */
+#define SPMV_COMP_TAU_DEFAULT 0
+spmv_status spmv_set_compensation_threshold(spmv_handle h, int64_t tau);
+
 /* ---------------------------------------------------------------- inspection */
 
 typedef struct {

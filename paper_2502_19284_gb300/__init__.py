@@ -32,6 +32,7 @@ SPMV_DUP_SUM = 0x0
 SPMV_DUP_ERROR = 0x2
 SPMV_INNER_HILBERT, SPMV_INNER_ROWMAJOR = 0, 1
 SPMV_HB_STAGED, SPMV_HB_CHUNKED = 0, 1
+SPMV_COMP_TAU_DEFAULT = 0   # include/spmv.h
 SPMV_ACC_DEFAULT, SPMV_ACC_F32, SPMV_ACC_F64, SPMV_ACC_COMPENSATED, SPMV_ACC_SEGMENT = range(5)
 
 FORMATS = {"rowsplit": SPMV_FMT_CSR_ROWSPLIT, "merge": SPMV_FMT_CSR_MERGE, "hb": SPMV_FMT_HB, "auto": SPMV_FMT_AUTO}
@@ -92,6 +93,7 @@ _SIG = {
     "spmv_mul_csr_merge_noalloc": [_i64, _i64, _i64, _p, _p, _p, _p, _p, _p],
     "spmv_pagerank": [_p, ctypes.c_double, _i32, _p, _p],
     "spmv_tune": [_p, _i32, _u32, _u32, ctypes.POINTER(spmv_tune_result), _p],
+    "spmv_set_compensation_threshold": [_p, ctypes.c_int64],
     "spmv_server_create": [ctypes.POINTER(spmv_server_opts), ctypes.POINTER(_p)],
     "spmv_server_add": [_p, _p, ctypes.POINTER(ctypes.c_int32)],
     "spmv_server_submit": [_p, ctypes.POINTER(spmv_request), ctypes.POINTER(ctypes.c_int64)],
@@ -335,6 +337,12 @@ def _host_values(dt, nnz):
     if dt == SPMV_BF16:
         return np.empty(max(nnz, 1), np.uint16)
     return None
+
+
+def spmv_set_compensation_threshold(h: Handle, tau: int):
+    """Rows of the row-split product longer than tau are summed with compensation under
+    SPMV_ACC_SEGMENT (see spmv.h)."""
+    _check(_lib.spmv_set_compensation_threshold(h.ptr, int(tau)), "spmv_set_compensation_threshold")
 
 
 def spmv_tune(h: Handle, vec_dtype="f64", accum=SPMV_ACC_DEFAULT, hb=False, stream=None) -> dict:

@@ -591,6 +591,17 @@ spmv_status spmv_mul_batch(int count, const spmv_handle *hs, int k, const void *
     return mul_batch(count, (spmv_matrix *const *)hs, k, X, Y, vec_dt, accum, (cudaStream_t)stream);
 }
 
+spmv_status spmv_set_compensation_threshold(spmv_handle h, int64_t tau) {
+    g_err.clear();
+    SPMV_TRY(check_handle(h));
+    if (tau < 0) {
+        set_error("spmv_set_compensation_threshold: tau must be >= 0");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    h->comp_tau = tau;
+    return SPMV_OK;
+}
+
 spmv_status spmv_destroy(spmv_handle h) {
     if (!h) return SPMV_OK;
     cudaError_t e = cudaDeviceSynchronize();

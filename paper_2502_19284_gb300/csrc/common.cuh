@@ -174,6 +174,9 @@ struct spmv_matrix {
     int32_t *bin_rows = nullptr;
     int64_t bin_count[8] = {0};
     int64_t max_row_len = 0;
+    // compensation threshold of the row-split product under SPMV_ACC_SEGMENT: rows whose length
+    // class reaches beyond comp_tau entries are summed with compensation
+    int64_t comp_tau = SPMV_COMP_TAU_DEFAULT;
 
     // merge-path partition and carries
     bool has_merge = false;

@@ -1004,7 +1004,38 @@ struct ClassTable {
 constexpr int RS_ROWS_PER_WARP = 4;
 __host__ __device__ constexpr int rs_rows_per_group(int G) { return G == 32 ? RS_ROWS_PER_WARP : 1; }
 
-template <typename VT, typename XT, typename AT, int G>
+// Row-split accumulators: RsPlain sums in AT (one fma per nonzero, butterfly of plain
+// additions); RsComp keeps an FP32 sum with its compensation (the FMA error of every product
+// and the TwoSum error of every addition, Neumaier style) through the lane sums and the
+// butterfly, rounded once at the end.
+template <typename AT>
+struct RsPlain {
+    AT v;
+    __device__ __forceinline__ void zero() { v = AT(0); }
+    __device__ __forceinline__ void mad(AT a, AT x) { v = v + a * x; }
+    __device__ __forceinline__ void add(const RsPlain &o) { v = v + o.v; }
+    __device__ __forceinline__ RsPlain xor_shfl(int o, int w) const {
+        RsPlain r;
+        r.v = __shfl_xor_sync(0xffffffffu, v, o, w);
+        return r;
+    }
+    template <typename XT> __device__ __forceinline__ XT out() const { return XT(v); }
+};
+struct RsComp {
+    float s, c;
+    __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
+    __device__ __forceinline__ void mad(float a, float x) { df_fma(a, 0.f, x, 0.f, s, c); }
+    __device__ __forceinline__ void add(const RsComp &o) { df_add(s, c, o.s, o.c); }
+    __device__ __forceinline__ RsComp xor_shfl(int o, int w) const {
+        RsComp r;
+        r.s = __shfl_xor_sync(0xffffffffu, s, o, w);
+        r.c = __shfl_xor_sync(0xffffffffu, c, o, w);
+        return r;
+    }
+    template <typename XT> __device__ __forceinline__ XT out() const { return XT(__fadd_rn(s, c)); }
+};
+
+template <typename VT, typename XT, typename AT, typename Acc, int G>
 __device__ __forceinline__ void rowsplit_group(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                                                const VT *__restrict__ val, const XT *__restrict__ x,
                                                XT *__restrict__ y, const int32_t *__restrict__ rows, int64_t count,
@@ -1024,7 +1055,8 @@ __device__ __forceinline__ void rowsplit_group(const int32_t *__restrict__ row_p
     }
 #pragma unroll
     for (int i = 0; i < RPG; ++i) {
-        AT acc = AT(0);
+        Acc acc;
+        acc.zero();
         for (int32_t kb = k0[i]; kb < k1[i]; kb += U * G) {
             int32_t c[U];
             AT a[U];
@@ -1036,22 +1068,23 @@ __device__ __forceinline__ void rowsplit_group(const int32_t *__restrict__ row_p
             }
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (c[u] >= 0) acc = acc + a[u] * ld_x<XT, AT>(x, c[u]);
+                if (c[u] >= 0) acc.mad(a[u], ld_x<XT, AT>(x, c[u]));
         }
 #pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) acc = acc + __shfl_xor_sync(0xffffffffu, acc, o, G);
-        if (row[i] >= 0 && lane == 0) y[row[i]] = XT(acc);
+        for (int o = G / 2; o > 0; o >>= 1) acc.add(acc.xor_shfl(o, G));
+        if (row[i] >= 0 && lane == 0) y[row[i]] = acc.template out<XT>();
     }
 }
 
-template <typename VT, typename XT, typename AT>
+template <typename VT, typename XT, typename AT, typename Acc>
 __device__ __forceinline__ void rowsplit_cta(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                                              const VT *__restrict__ val, const XT *__restrict__ x,
                                              XT *__restrict__ y, int32_t row) {
     constexpr int U = 8;   // independent loads in flight per thread
-    __shared__ AT red[RS_BLOCK / 32];
+    __shared__ Acc red[RS_BLOCK / 32];
     const int32_t k0 = __ldg(row_ptr + row), k1 = __ldg(row_ptr + row + 1);
-    AT acc = AT(0);
+    Acc acc;
+    acc.zero();
     for (int32_t kb = k0; kb < k1; kb += U * RS_BLOCK) {
         int32_t c[U];
         AT a[U];
@@ -1066,26 +1099,44 @@ __device__ __forceinline__ void rowsplit_cta(const int32_t *__restrict__ row_ptr
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int32_t k = kb + u * RS_BLOCK + threadIdx.x;
-            if (k < k1) acc = acc + a[u] * ld_x<XT, AT>(x, c[u]);
+            if (k < k1) acc.mad(a[u], ld_x<XT, AT>(x, c[u]));
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc = acc + __shfl_xor_sync(0xffffffffu, acc, o);
+    for (int o = 16; o > 0; o >>= 1) acc.add(acc.xor_shfl(o, 32));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        AT s = AT(0);
-        for (int w = 0; w < RS_BLOCK / 32; ++w) s = s + red[w];
-        y[row] = XT(s);
+        Acc s = red[0];
+        for (int w = 1; w < RS_BLOCK / 32; ++w) s.add(red[w]);
+        y[row] = s.template out<XT>();
     }
     __syncthreads();   // red[] is free for the CTA's next row
 }
 
-template <typename VT, typename XT, typename AT>
+template <typename VT, typename XT, typename AT, typename Acc>
+__device__ __forceinline__ void rowsplit_class(int c, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                                               const VT *__restrict__ val, const XT *__restrict__ x, XT *__restrict__ y,
+                                               const int32_t *__restrict__ rows, int64_t count, int64_t lb) {
+    switch (c) {
+        case 0: rowsplit_group<VT, XT, AT, Acc, 1>(row_ptr, col, val, x, y, rows, count, lb); break;
+        case 1: rowsplit_group<VT, XT, AT, Acc, 2>(row_ptr, col, val, x, y, rows, count, lb); break;
+        case 2: rowsplit_group<VT, XT, AT, Acc, 4>(row_ptr, col, val, x, y, rows, count, lb); break;
+        case 3: rowsplit_group<VT, XT, AT, Acc, 8>(row_ptr, col, val, x, y, rows, count, lb); break;
+        case 4: rowsplit_group<VT, XT, AT, Acc, 16>(row_ptr, col, val, x, y, rows, count, lb); break;
+        case 5: rowsplit_group<VT, XT, AT, Acc, 32>(row_ptr, col, val, x, y, rows, count, lb); break;
+        default: rowsplit_cta<VT, XT, AT, Acc>(row_ptr, col, val, x, y, rows[lb]); break;
+    }
+}
+
+// COMP: the classes from comp_from on (rows that can be longer than the compensation
+// threshold) accumulate with RsComp, the others plainly.
+template <typename VT, typename XT, typename AT, bool COMP>
 __global__ __launch_bounds__(RS_BLOCK) void k_rowsplit(const int32_t *__restrict__ row_ptr,
                                                        const int32_t *__restrict__ col, const VT *__restrict__ val,
                                                        const XT *__restrict__ x, XT *__restrict__ y,
-                                                       const int32_t *__restrict__ bin_rows, ClassTable ct) {
+                                                       const int32_t *__restrict__ bin_rows, ClassTable ct,
+                                                       int comp_from) {
     const int64_t nblocks = ct.blk_begin[NUM_ROW_CLASSES];
     for (int64_t b = blockIdx.x; b < nblocks; b += gridDim.x) {   // persistent over the class blocks
         int c = 0;
@@ -1093,20 +1144,20 @@ __global__ __launch_bounds__(RS_BLOCK) void k_rowsplit(const int32_t *__restrict
         const int64_t lb = b - ct.blk_begin[c];
         const int32_t *rows = bin_rows + ct.begin[c];
         const int64_t count = ct.begin[c + 1] - ct.begin[c];
-        switch (c) {
-            case 0: rowsplit_group<VT, XT, AT, 1>(row_ptr, col, val, x, y, rows, count, lb); break;
-            case 1: rowsplit_group<VT, XT, AT, 2>(row_ptr, col, val, x, y, rows, count, lb); break;
-            case 2: rowsplit_group<VT, XT, AT, 4>(row_ptr, col, val, x, y, rows, count, lb); break;
-            case 3: rowsplit_group<VT, XT, AT, 8>(row_ptr, col, val, x, y, rows, count, lb); break;
-            case 4: rowsplit_group<VT, XT, AT, 16>(row_ptr, col, val, x, y, rows, count, lb); break;
-            case 5: rowsplit_group<VT, XT, AT, 32>(row_ptr, col, val, x, y, rows, count, lb); break;
-            default: rowsplit_cta<VT, XT, AT>(row_ptr, col, val, x, y, rows[lb]); break;
+        if constexpr (COMP) {
+            if (c >= comp_from) {
+                rowsplit_class<VT, XT, AT, RsComp>(c, row_ptr, col, val, x, y, rows, count, lb);
+                continue;
+            }
         }
+        rowsplit_class<VT, XT, AT, RsPlain<AT>>(c, row_ptr, col, val, x, y, rows, count, lb);
     }
 }
 
+// comp_from < 0: plain accumulation everywhere; else compensated from that length class on
+// (only with FP32 accumulation).
 template <typename VT, typename XT, typename AT>
-spmv_status launch_rowsplit(const spmv_matrix *h, const void *x, void *y, cudaStream_t s) {
+spmv_status launch_rowsplit(const spmv_matrix *h, const void *x, void *y, cudaStream_t s, int comp_from = -1) {
     ClassTable ct;
     ct.begin[0] = 0;
     ct.blk_begin[0] = 0;
@@ -1118,9 +1169,20 @@ spmv_status launch_rowsplit(const spmv_matrix *h, const void *x, void *y, cudaSt
     }
     const int64_t blocks = ct.blk_begin[NUM_ROW_CLASSES];
     if (blocks == 0) return SPMV_OK;
-    const unsigned grid = (unsigned)std::min<int64_t>(blocks, persistent_grid((const void *)k_rowsplit<VT, XT, AT>, RS_BLOCK, 0, blocks * MW_WARPS));
-    SPMV_LAUNCH("k_rowsplit", s, (k_rowsplit<VT, XT, AT><<<grid, RS_BLOCK, 0, s>>>(h->row_ptr, h->col, (const VT *)h->val,
-                                                                 (const XT *)x, (XT *)y, h->bin_rows, ct)));
+    if constexpr (std::is_same<AT, float>::value) {
+        if (comp_from >= 0) {
+            const unsigned grid = (unsigned)std::min<int64_t>(
+                blocks, persistent_grid((const void *)k_rowsplit<VT, XT, AT, true>, RS_BLOCK, 0, blocks * MW_WARPS));
+            SPMV_LAUNCH("k_rowsplit", s, (k_rowsplit<VT, XT, AT, true><<<grid, RS_BLOCK, 0, s>>>(
+                                             h->row_ptr, h->col, (const VT *)h->val, (const XT *)x, (XT *)y,
+                                             h->bin_rows, ct, comp_from)));
+            SPMV_LAUNCH_CHECK("rowsplit spmv");
+            return SPMV_OK;
+        }
+    }
+    const unsigned grid = (unsigned)std::min<int64_t>(blocks, persistent_grid((const void *)k_rowsplit<VT, XT, AT, false>, RS_BLOCK, 0, blocks * MW_WARPS));
+    SPMV_LAUNCH("k_rowsplit", s, (k_rowsplit<VT, XT, AT, false><<<grid, RS_BLOCK, 0, s>>>(h->row_ptr, h->col, (const VT *)h->val,
+                                                                 (const XT *)x, (XT *)y, h->bin_rows, ct, -1)));
     SPMV_LAUNCH_CHECK("rowsplit spmv");
     return SPMV_OK;
 }
@@ -1285,6 +1347,17 @@ spmv_status dispatch(Algo a, const spmv_matrix *h, const void *x, void *y, spmv_
         if (dt == SPMV_PATTERN) return run_algo<Pattern, double, double>(a, h, x, y, allow_df, s);
         if (dt == SPMV_F32) return run_algo<float, double, double>(a, h, x, y, allow_df, s);
         goto unsupported;
+    }
+    if (vdt == SPMV_F32 && a == ROWSPLIT && (acc == SPMV_ACC_COMPENSATED || acc == SPMV_ACC_SEGMENT)) {
+        // compensated from the first length class whose rows can be longer than the threshold
+        int from = 0;
+        if (acc == SPMV_ACC_SEGMENT) {
+            static const int64_t cmax[NUM_ROW_CLASSES - 1] = {2, 4, 8, 16, 32, 2048};
+            while (from < NUM_ROW_CLASSES - 1 && cmax[from] <= h->comp_tau) ++from;
+        }
+        if (dt == SPMV_F32) return launch_rowsplit<float, float, float>(h, x, y, s, from);
+        if (dt == SPMV_BF16) return launch_rowsplit<__nv_bfloat16, float, float>(h, x, y, s, from);
+        if (dt == SPMV_PATTERN) return launch_rowsplit<Pattern, float, float>(h, x, y, s, from);
     }
     if (vdt == SPMV_F32 && acc == SPMV_ACC_COMPENSATED && a == MERGE) {
         if (dt == SPMV_F32) return launch_merge_comp<float, CompAcc>(h, x, y, s);

@@ -72,7 +72,8 @@ def test_precision_modes(sp, kind):
             xd = torch.from_numpy(x32).to(DEV)
             for algo, modes in (("merge", (sp.SPMV_ACC_F32, sp.SPMV_ACC_COMPENSATED, sp.SPMV_ACC_SEGMENT,
                                            sp.SPMV_ACC_F64)),
-                                ("rowsplit", (sp.SPMV_ACC_F32, sp.SPMV_ACC_F64)),
+                                ("rowsplit", (sp.SPMV_ACC_F32, sp.SPMV_ACC_F64, sp.SPMV_ACC_SEGMENT,
+                                              sp.SPMV_ACC_COMPENSATED)),
                                 ("hb", (sp.SPMV_ACC_F32, sp.SPMV_ACC_SEGMENT, sp.SPMV_ACC_COMPENSATED))):
                 sp.spmv_convert(h, algo)
                 for acc in modes:
@@ -93,16 +94,16 @@ def test_precision_modes(sp, kind):
                         bound = g * scale + U * np.abs(ref)
                     elif acc == sp.SPMV_ACC_COMPENSATED:
                         bound = 8 * L * U * U * scale + U * np.abs(ref) + 2.0 ** -140
+                    elif algo == "rowsplit":   # SEGMENT: rows whose class reaches beyond tau compensated
+                        g = (L + 1) * U / (1 - (L + 1) * U)
+                        cmax = np.array([2, 4, 8, 16, 32, 2048, np.inf])
+                        comp = cmax[np.searchsorted(cmax, L)] > sp.SPMV_COMP_TAU_DEFAULT
+                        bound = np.where(comp, 8 * L * U * U * scale, g * scale) + U * np.abs(ref) + 2.0 ** -140
                     elif acc == sp.SPMV_ACC_SEGMENT:   # <= 7 FP32 terms per lane, TwoSum joins
                         bound = (8 * U / (1 - 8 * U) + 8 * L * U * U) * scale + U * np.abs(ref) + 2.0 ** -140
                     else:
                         bound = U * np.abs(ref) + 1e-14 * scale
                     assert (err <= bound).all(), (name, algo, acc, float(np.max(err - bound)))
-            if kind == "f32":
-                with pytest.raises(sp.SpmvError):
-                    sp.spmv_convert(h, "rowsplit")
-                    sp.spmv_mul(h, xd, torch.empty(m, dtype=torch.float32, device=DEV),
-                                accum=sp.SPMV_ACC_COMPENSATED)
 
 
 def test_compensation_reduces_error(sp):
@@ -149,3 +150,44 @@ def test_pagerank_matches_oracle(sp, scale):
         sp.spmv_pagerank(h, x2, 0.5, 3)                        # new graph for new arguments
         torch.cuda.synchronize()
         np.testing.assert_allclose(x2.cpu().numpy(), oracle.pagerank(rp, co, 0.5, 3), rtol=1e-11, atol=1e-16)
+
+
+def test_compensation_threshold_sweep(sp):
+    """Row-split SPMV_ACC_SEGMENT with tau: rows longer than tau (by length class) follow the
+    compensated bound, the rest the FP32 bound; tau = 0 equals SPMV_ACC_COMPENSATED bit for
+    bit; a negative tau is rejected."""
+    n = 1 << 13
+    rows, cols = synth.zipf_rows(n, 1.5, 1 << 12, 0.05, seed=75)
+    vals = synth.values(rows, cols, 76).astype(np.float32)
+    x32 = synth.vector(n, 77).astype(np.float32)
+    rp, co, vo = oracle.coo_to_csr(n, n, rows, cols, vals.astype(np.float64))
+    x64 = x32.astype(np.float64)
+    ref = oracle.csr_spmv(rp, co, vo, x64)
+    scale = oracle.csr_absmul(rp, co, vo, x64)
+    L = np.diff(rp).astype(np.float64)
+    h = sp.spmv_create_coo(n, n, torch.from_numpy(rows).to(DEV), torch.from_numpy(cols).to(DEV),
+                           torch.from_numpy(vals).to(DEV))
+    sp.spmv_convert(h, "rowsplit")
+    xd = torch.from_numpy(x32).to(DEV)
+
+    def run(acc):
+        y = torch.full((n,), float("nan"), dtype=torch.float32, device=DEV)
+        sp.spmv_mul(h, xd, y, accum=acc)
+        torch.cuda.synchronize()
+        return y.cpu().numpy().astype(np.float64)
+
+    comp = run(sp.SPMV_ACC_COMPENSATED)
+    cmax = np.array([2, 4, 8, 16, 32, 2048, np.inf])
+    cls = np.searchsorted(cmax, L)                 # length class of every row
+    for tau in (0, 2, 8, 32, 2048, 1 << 30):
+        sp.spmv_set_compensation_threshold(h, tau)
+        y = run(sp.SPMV_ACC_SEGMENT)
+        compensated = cmax[cls] > tau
+        g = (L + 1) * U / (1 - (L + 1) * U)
+        bound = np.where(compensated, 8 * L * U * U * scale, g * scale) + U * np.abs(ref) + 2.0 ** -140
+        assert (np.abs(y - ref) <= bound).all(), tau
+        if tau == 0:
+            np.testing.assert_array_equal(y, comp)
+    with pytest.raises(sp.SpmvError):
+        sp.spmv_set_compensation_threshold(h, -1)
+    sp.spmv_destroy(h)
