@@ -39,7 +39,8 @@ typedef enum {
     SPMV_ERR_UNSUPPORTED = 5,   /* size/format/dtype combination not provided            */
     SPMV_ERR_CUDA = 6,          /* a CUDA runtime call failed; see spmv_last_error()     */
     SPMV_ERR_TIMEOUT = 7,       /* a bounded device wait gave up                         */
-    SPMV_ERR_NOT_CONVERTED = 8  /* spmv_mul before any spmv_convert                      */
+    SPMV_ERR_NOT_CONVERTED = 8, /* spmv_mul before any spmv_convert                      */
+    SPMV_ERR_IO = 9             /* a file could not be opened, written or read back whole */
 } spmv_status;
 
 /* Element types.  SPMV_PATTERN: no stored values, every nonzero is 1 (data == NULL). */
@@ -242,6 +243,45 @@ spmv_status spmv_tune(spmv_handle h, spmv_dtype vec_dt, uint32_t accum, uint32_t
  */
 #define SPMV_COMP_TAU_DEFAULT 0
 spmv_status spmv_set_compensation_threshold(spmv_handle h, int64_t tau);
+
+/* ---------------------------------------------------------------- iterative use */
+
+/*
+ * spmv_cg -- conjugate gradients (Hestenes and Stiefel) for A x = b with a symmetric positive
+ * definite A: the repeated products on one converted matrix over which the paper's
+ * break-even count amortises a conversion (Sections 6.2 and 7).
+ *   h           converted handle (square; FP64, FP32 or pattern values); every iteration runs one
+ *               spmv_mul with FP64 vectors in the handle's active format (SPMV_ACC_DEFAULT).
+ *   b           device, n doubles; x: device, n doubles (overwritten; x0 = 0).
+ *   tol         stop when the recursive residual ||r|| <= tol ||b||; max_iters: iteration cap.
+ *   iters_out, resid_out   may be NULL: iterations run and the final ||r||.
+ * Dot products are deterministic (fixed partial sums and order); the scalars stay on the
+ * device and the residual is read back every 8 iterations, so up to 7 iterations may run past
+ * the threshold.  Allocates scratch (3 n doubles), synchronises `stream` at those read-backs.
+ * SPMV_ERR_INVALID_ARG (NULL, non-square, tol < 0), SPMV_ERR_NOT_CONVERTED, SPMV_ERR_UNSUPPORTED
+ * (bfloat16 values).
+ */
+spmv_status spmv_cg(spmv_handle h, const double *b, double *x, double tol, int max_iters, void *stream,
+                    int *iters_out, double *resid_out);
+
+/* ---------------------------------------------------------------- storage */
+
+/*
+ * spmv_save / spmv_load -- keep converted formats on disk so that a later run skips the
+ * conversion (the paper's future work: storing several formats of a matrix, Section 8).
+ * spmv_save writes the handle's CRS arrays and, when built, its Hilbert-ordered blocked arrays
+ * and staged blocked layout, with its active format and a checksum of every array; it copies
+ * through a pinned host buffer on `stream` and synchronises it.  spmv_load reads such a file
+ * into a new handle (*out), verifies the checksum before any kernel reads the arrays, rebuilds
+ * the cheap derived tables (the HB chunk table, the staged layout's split between the loading
+ * device's SMs) and makes the saved format active again (its other tables, e.g. the merge-path
+ * partition, come from the CRS arrays as a conversion would build them).  The file format is
+ * this library's own (host byte order; see csrc/store.cu).  Errors: SPMV_ERR_INVALID_ARG (NULL
+ * argument, not a file of this library), SPMV_ERR_NOT_CONVERTED (save before any conversion),
+ * SPMV_ERR_IO (open, write or read failed, truncated or damaged file), SPMV_ERR_OOM.
+ */
+spmv_status spmv_save(spmv_handle h, const char *path, void *stream);
+spmv_status spmv_load(const char *path, void *stream, spmv_handle *out);
 
 /* ---------------------------------------------------------------- inspection */
 

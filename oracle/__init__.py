@@ -122,6 +122,7 @@ def _declare(lib):
         "oracle_round_bf16": (u16, [dbl]),
         "oracle_bf16_to_double": (dbl, [u16]),
         "oracle_pagerank": (i32, [i64, p, p, dbl, i32, p]),
+        "oracle_cg": (i32, [i64, p, p, p, p, dbl, i32, p, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -355,3 +356,16 @@ def pagerank(row_ptr, col, damping=0.85, iters=20, lib=None):
     if st != OK:
         raise OracleError(st, "pagerank")
     return x
+
+
+def cg(row_ptr, col, val, b, tol=1e-10, max_iters=1000, lib=None):
+    """Conjugate gradients from x0 = 0 (see oracle.c).  Returns (x, iterations, ||r||)."""
+    lib = lib or load()
+    rp, co, vo, bb = _i32(row_ptr), _i32(col), _f64(val), _f64(b)
+    n = rp.size - 1
+    x = np.empty(n)
+    res = ctypes.c_double(0.0)
+    it = lib.oracle_cg(n, _p(rp), _p(co), _p(vo), _p(bb), float(tol), int(max_iters), _p(x), ctypes.byref(res))
+    if it < 0:
+        raise OracleError(ERR_OOM, "oracle_cg")
+    return x, it, res.value

@@ -31,6 +31,8 @@
  *   oracle_round_f32, oracle_round_bf16  storage rounding to nearest-even, directly from double
  *   oracle_pagerank        Section 1 names PageRank as an SpMV application; the iteration
  *                          written out: x <- d (P x + dangling/n) + (1-d)/n, P = A D^{-1}
+ *   oracle_cg              conjugate gradients (Hestenes and Stiefel, 1952) on repeated
+ *                          Algorithm 1 products, the iterative use of Sections 6.2 and 7
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -511,4 +513,43 @@ int oracle_pagerank(int64_t n, const int32_t *row_ptr, const int32_t *col_ind, d
     }
     free(deg); free(z); free(y);
     return OK;
+}
+
+/* ---------------------------------------------------------------- conjugate gradients */
+
+/*
+ * Conjugate gradients (Hestenes and Stiefel, 1952) for a symmetric positive definite A in
+ * CRS form, x0 = 0, every product by Algorithm 1 (oracle_csr_spmv), every dot product a
+ * left-to-right FP64 sum.  Iterates while the recursive residual norm exceeds tol * ||b|| and
+ * fewer than max_iters iterations ran.  Returns the iteration count; *resid = ||r||.
+ */
+int oracle_cg(int64_t n, const int32_t *row_ptr, const int32_t *col_ind, const double *data, const double *b,
+              double tol, int max_iters, double *x, double *resid) {
+    double *r = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *p = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *q = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!r || !p || !q) { free(r); free(p); free(q); return -1; }
+    double rho = 0.0;
+    for (int64_t i = 0; i < n; ++i) { x[i] = 0.0; r[i] = b[i]; p[i] = b[i]; rho = rho + r[i] * r[i]; }
+    const double stop = tol * sqrt(rho);
+    int it = 0;
+    while (it < max_iters && sqrt(rho) > stop) {
+        oracle_csr_spmv(n, row_ptr, col_ind, data, p, q);
+        double pq = 0.0;
+        for (int64_t i = 0; i < n; ++i) pq = pq + p[i] * q[i];
+        const double alpha = pq != 0.0 ? rho / pq : 0.0;
+        double rho1 = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            x[i] = x[i] + alpha * p[i];
+            r[i] = r[i] - alpha * q[i];
+            rho1 = rho1 + r[i] * r[i];
+        }
+        const double beta = rho != 0.0 ? rho1 / rho : 0.0;
+        for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+        rho = rho1;
+        ++it;
+    }
+    if (resid) *resid = sqrt(rho);
+    free(r); free(p); free(q);
+    return it;
 }

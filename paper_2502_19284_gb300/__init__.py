@@ -24,7 +24,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 # ------------------------------------------------------------------ constants (spmv.h)
 SPMV_OK, SPMV_ERR_INVALID_ARG, SPMV_ERR_INDEX_RANGE, SPMV_ERR_DUPLICATE, SPMV_ERR_OOM, \
-    SPMV_ERR_UNSUPPORTED, SPMV_ERR_CUDA, SPMV_ERR_TIMEOUT, SPMV_ERR_NOT_CONVERTED = range(9)
+    SPMV_ERR_UNSUPPORTED, SPMV_ERR_CUDA, SPMV_ERR_TIMEOUT, SPMV_ERR_NOT_CONVERTED, SPMV_ERR_IO = range(10)
 SPMV_F64, SPMV_F32, SPMV_BF16, SPMV_PATTERN = range(4)
 SPMV_FMT_CSR_ROWSPLIT, SPMV_FMT_CSR_MERGE, SPMV_FMT_HB, SPMV_FMT_AUTO = range(4)
 SPMV_DEVICE_PTRS = 0x1
@@ -94,6 +94,9 @@ _SIG = {
     "spmv_pagerank": [_p, ctypes.c_double, _i32, _p, _p],
     "spmv_tune": [_p, _i32, _u32, _u32, ctypes.POINTER(spmv_tune_result), _p],
     "spmv_set_compensation_threshold": [_p, ctypes.c_int64],
+    "spmv_save": [_p, ctypes.c_char_p, _p],
+    "spmv_cg": [_p, _p, _p, ctypes.c_double, _i32, _p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)],
+    "spmv_load": [ctypes.c_char_p, _p, ctypes.POINTER(ctypes.c_void_p)],
     "spmv_server_create": [ctypes.POINTER(spmv_server_opts), ctypes.POINTER(_p)],
     "spmv_server_add": [_p, _p, ctypes.POINTER(ctypes.c_int32)],
     "spmv_server_submit": [_p, ctypes.POINTER(spmv_request), ctypes.POINTER(ctypes.c_int64)],
@@ -337,6 +340,28 @@ def _host_values(dt, nnz):
     if dt == SPMV_BF16:
         return np.empty(max(nnz, 1), np.uint16)
     return None
+
+
+def spmv_cg(h: Handle, b, x, tol=1e-10, max_iters=1000, stream=None):
+    """Conjugate gradients A x = b on device float64 tensors (x overwritten, x0 = 0); returns
+    (iterations, final recursive residual norm)."""
+    it = ctypes.c_int(0)
+    res = ctypes.c_double(0.0)
+    _check(_lib.spmv_cg(h.ptr, _addr(b), _addr(x), float(tol), int(max_iters), _stream(stream), ctypes.byref(it),
+                        ctypes.byref(res)), "spmv_cg")
+    return it.value, res.value
+
+
+def spmv_save(h: Handle, path: str, stream=None):
+    """Write the handle's converted formats to `path` (see spmv.h)."""
+    _check(_lib.spmv_save(h.ptr, os.fsencode(path), _stream(stream)), "spmv_save")
+
+
+def spmv_load(path: str, stream=None) -> Handle:
+    """A new handle from a file written by spmv_save (formats restored, no conversion)."""
+    out = ctypes.c_void_p()
+    _check(_lib.spmv_load(os.fsencode(path), _stream(stream), ctypes.byref(out)), "spmv_load")
+    return Handle(out.value)
 
 
 def spmv_set_compensation_threshold(h: Handle, tau: int):

@@ -235,6 +235,7 @@ const char *spmv_status_string(spmv_status s) {
         case SPMV_ERR_CUDA: return "SPMV_ERR_CUDA";
         case SPMV_ERR_TIMEOUT: return "SPMV_ERR_TIMEOUT";
         case SPMV_ERR_NOT_CONVERTED: return "SPMV_ERR_NOT_CONVERTED";
+        case SPMV_ERR_IO: return "SPMV_ERR_IO";
     }
     return "SPMV_ERR_UNKNOWN";
 }

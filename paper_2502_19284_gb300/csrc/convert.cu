@@ -939,6 +939,20 @@ spmv_status build_merge(spmv_matrix *h, int tile_items, cudaStream_t s) {
     return SPMV_OK;
 }
 
+spmv_status hb_chunk_table(spmv_matrix *h, cudaStream_t s) {
+    const int64_t nchunks = (h->nnz + HB_CHUNK - 1) / HB_CHUNK;
+    DevBuf chk(s);
+    SPMV_TRY(chk.alloc((size_t)(nchunks + 1) * 4, "hb chunk blocks"));
+    if (h->nnz > 0) {
+        SPMV_LAUNCH("k_hb_chunks", s, (k_hb_chunks<<<grid_for(nchunks + 1), CB, 0, s>>>(h->blk_ptr, h->nblk, h->nnz,
+                                                                                     nchunks, chk.as<int32_t>())));
+        SPMV_LAUNCH_CHECK("hb chunks");
+    }
+    if (h->hb_chunk_blk) dev_free_async(h->hb_chunk_blk, s);
+    h->hb_chunk_blk = (int32_t *)chk.release();
+    return SPMV_OK;
+}
+
 spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s) {
     const int64_t m = h->m, n = h->n, nnz = h->nnz;
     const int es = elem_size(h->dt);

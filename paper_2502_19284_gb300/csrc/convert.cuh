@@ -59,6 +59,10 @@ spmv_status mul_hb(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt,
 // Staged-x blocked layout and product (stage.cu), built from the CRS arrays with slices of
 // 2^lb columns; free_stage releases it in stream order.
 spmv_status build_stage(spmv_matrix *h, int lb, cudaStream_t s);
+// Recompute the CTA split of the staged layout for the current device (after a load).
+spmv_status stage_resplit(spmv_matrix *h, cudaStream_t s);
+// (Re)build the HB chunk table from blk_ptr (after a load).
+spmv_status hb_chunk_table(spmv_matrix *h, cudaStream_t s);
 void free_stage(spmv_matrix *h, cudaStream_t s);
 spmv_status mul_stage(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s);
 // x -> float pairs in h->xsplit, with the window flag h->xsplit_flag reset and set (spmv.cu).

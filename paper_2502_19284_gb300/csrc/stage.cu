@@ -667,6 +667,26 @@ spmv_status st_fill_launch(const uint64_t *Ks, const uint32_t *Ps, const spmv_ma
     return SPMV_OK;
 }
 
+int st_sms();
+
+// First tile of every CTA (one CTA per SM of the current device): equal shares of the
+// prefix-summed tile costs.
+spmv_status st_split(const int4 *hp, int64_t ntiles, DevBuf *part, int *G, cudaStream_t s) {
+    *G = st_sms();
+    SPMV_TRY(part->alloc((size_t)(*G + 1) * 4, "stage CTA split"));
+    DevBuf cost(s), pcost(s), ctmp(s);
+    SPMV_TRY(cost.alloc((size_t)(ntiles + 1) * 4, "stage tile costs"));
+    SPMV_TRY(pcost.alloc((size_t)(ntiles + 1) * 4, "stage tile costs"));
+    SPMV_TRY(ctmp.alloc(scan_temp_bytes(ntiles + 1), "stage tile costs"));
+    SPMV_LAUNCH("k_st_cost", s, (k_st_cost<<<st_grid(ntiles + 1), ST_CB, 0, s>>>(hp, ntiles, cost.as<uint32_t>())));
+    SPMV_LAUNCH_CHECK("stage tile costs");
+    SPMV_TRY(exclusive_scan_u32(cost.as<uint32_t>(), pcost.as<uint32_t>(), ntiles + 1, ctmp.p, s));
+    SPMV_LAUNCH("k_st_parts", s, (k_st_parts<<<st_grid(*G + 1), ST_CB, 0, s>>>(pcost.as<uint32_t>(), ntiles, *G,
+                                                                              part->as<int32_t>())));
+    SPMV_LAUNCH_CHECK("stage CTA split");
+    return SPMV_OK;
+}
+
 int st_sms() {
     int dev = 0, n = 1;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
@@ -892,18 +912,7 @@ spmv_status build_stage(spmv_matrix *h, int lb, cudaStream_t s) {
         SPMV_LAUNCH("k_st_meta", s, (k_st_meta<<<st_grid(ntiles * 32), ST_CB, 0, s>>>(w, hp, ntiles, lb,
                                                                                     lmeta.as<uint2>())));
         SPMV_LAUNCH_CHECK("stage lane headers");
-        G = st_sms();
-        SPMV_TRY(part.alloc((size_t)(G + 1) * 4, "stage CTA split"));
-        DevBuf cost(s), pcost(s), ctmp(s);
-        SPMV_TRY(cost.alloc((size_t)(ntiles + 1) * 4, "stage tile costs"));
-        SPMV_TRY(pcost.alloc((size_t)(ntiles + 1) * 4, "stage tile costs"));
-        SPMV_TRY(ctmp.alloc(scan_temp_bytes(ntiles + 1), "stage tile costs"));
-        SPMV_LAUNCH("k_st_cost", s, (k_st_cost<<<st_grid(ntiles + 1), ST_CB, 0, s>>>(hp, ntiles, cost.as<uint32_t>())));
-        SPMV_LAUNCH_CHECK("stage tile costs");
-        SPMV_TRY(exclusive_scan_u32(cost.as<uint32_t>(), pcost.as<uint32_t>(), ntiles + 1, ctmp.p, s));
-        SPMV_LAUNCH("k_st_parts", s, (k_st_parts<<<st_grid(G + 1), ST_CB, 0, s>>>(pcost.as<uint32_t>(), ntiles, G,
-                                                                                 part.as<int32_t>())));
-        SPMV_LAUNCH_CHECK("stage CTA split");
+        SPMV_TRY(st_split(hp, ntiles, &part, &G, s));
         SPMV_CUDA_TRY(cudaStreamSynchronize(s));   // the temporaries are freed in stream order next
     }
     h->st_slice_tile = (uint32_t *)stile.release();
@@ -920,6 +929,18 @@ spmv_status build_stage(spmv_matrix *h, int lb, cudaStream_t s) {
     h->stage_bytes = ntiles * (16 + 256 + ST_TILE * (4 + (int64_t)vs)) + (nsl + 1) * 4 + (G + 1) * 4;
     h->bytes += h->stage_bytes;
     h->has_stage = true;
+    return SPMV_OK;
+}
+
+spmv_status stage_resplit(spmv_matrix *h, cudaStream_t s) {
+    if (!h->has_stage || h->stage_tiles == 0) return SPMV_OK;
+    DevBuf part(s);
+    int G = 0;
+    SPMV_TRY(st_split(h->st_hdr, h->stage_tiles, &part, &G, s));
+    if (h->st_part) dev_free_async(h->st_part, s);
+    h->bytes += (int64_t)(G - h->stage_parts) * 4;
+    h->st_part = (int32_t *)part.release();
+    h->stage_parts = G;
     return SPMV_OK;
 }
 

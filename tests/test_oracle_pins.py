@@ -593,3 +593,54 @@ def test_planted_absmul_row_overrun_fails_brute_force(orc):
     D = _dense(m, n, rp, co, vo)
     want = np.abs(D) @ np.abs(x)
     assert np.array_equal(good, want) and not np.array_equal(bad, want)
+
+
+# ------------------------------------------------------------------ conjugate gradients
+
+def _spd(n, nnz, seed):
+    """B + B^T + D with D the row sums of |B + B^T| plus one: strictly diagonally dominant with a
+    positive diagonal, hence symmetric positive definite (triplets, duplicates summed)."""
+    r, c = synth.random_coo(n, n, nnz, seed)
+    v = synth.values(r, c, seed)
+    rows = np.concatenate([r, c]).astype(np.int32)
+    cols = np.concatenate([c, r]).astype(np.int32)
+    vals = np.concatenate([v, v])
+    dense = np.zeros((n, n))
+    np.add.at(dense, (rows, cols), vals)
+    d = np.abs(dense).sum(axis=1) + 1.0
+    rows = np.concatenate([rows, np.arange(n, dtype=np.int32)])
+    cols = np.concatenate([cols, np.arange(n, dtype=np.int32)])
+    vals = np.concatenate([vals, d])
+    return rows, cols, vals, dense + np.diag(d)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_cg_matches_dense_solve(orc, seed):
+    """CG on a small SPD matrix reaches the dense solution (numpy.linalg.solve) and stops
+    within n iterations (exact arithmetic would terminate in at most n)."""
+    n = 40
+    rows, cols, vals, D = _spd(n, 120, 300 + seed)
+    rp, co, vo = oracle.coo_to_csr(n, n, rows, cols, vals, 0, orc)
+    b = synth.vector(n, 301 + seed)
+    x, it, res = oracle.cg(rp, co, vo, b, tol=1e-13, max_iters=4 * n, lib=orc)
+    xs = np.linalg.solve(D, b)
+    assert it <= n
+    assert np.max(np.abs(x - xs)) <= 1e-10 * np.max(np.abs(xs))
+    assert np.linalg.norm(b - D @ x) <= 1e-11 * np.linalg.norm(b)
+
+
+def test_planted_cg_sign_error_fails_the_dense_solve(orc):
+    """CG with the residual update sign flipped (r += alpha q) does not reach the solution."""
+    n = 30
+    rows, cols, vals, D = _spd(n, 90, 310)
+    b = synth.vector(n, 311)
+    x = np.zeros(n); r = b.copy(); p = b.copy(); rho = r @ r
+    for _ in range(2 * n):
+        q = D @ p
+        alpha = rho / (p @ q)
+        x = x + alpha * p
+        r = r + alpha * q                     # planted mistake
+        rho1 = r @ r
+        p = r + (rho1 / rho) * p
+        rho = rho1
+    assert not np.allclose(x, np.linalg.solve(D, b), rtol=1e-6)
