@@ -514,6 +514,71 @@ def batched_leg(sp, torch, dev, synth, np, cfg):
     return out
 
 
+# ------------------------------------------------------------------ iterative leg
+
+def iterative_leg(sp, torch, dev, synth, np):
+    """Conjugate gradients on one resident matrix: B + B^T + diag(row sums of |B + B^T| + 1)
+    from R-MAT scale 20 (edge factor 8, FP64, symmetric positive definite), solved to 1e-8 in
+    the merge-path and in the staged blocked format.  Reports the conversion, the solve, the
+    iterations and the conversion amortised over them (Sections 6.2 and 7), and for the blocked
+    format the time to load the converted matrix from disk instead (spmv_save / spmv_load)."""
+    import tempfile
+    scale, ef, seed = 20, 8, 4242
+    n = 1 << scale
+    r, c = synth.gpu_rmat_raw(scale, ef, seed=seed, device=dev)
+    v = synth.gpu_values(r, c, seed=seed)
+    rows = torch.cat([r, c, torch.arange(n, dtype=torch.int32, device=dev)])
+    cols = torch.cat([c, r, torch.arange(n, dtype=torch.int32, device=dev)])
+    d = torch.zeros(n, dtype=torch.float64, device=dev)
+    d.index_add_(0, torch.cat([r, c]).long(), torch.cat([v, v]).abs())
+    vals = torch.cat([v, v, d + 1.0])
+    del r, c, v, d
+    b = torch.from_numpy(synth.vector(n, seed + 1)).to(dev)
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    out = {"matrix": f"R-MAT scale {scale}, edge factor {ef}, made SPD (B + B^T + diagonal), FP64",
+           "tol": 1e-8, "formats": []}
+    for fmt in ("merge", "hb"):
+        torch.cuda.synchronize()
+        e = [ev() for _ in range(4)]
+        e[0].record()
+        h = sp.spmv_create_coo(n, n, rows, cols, vals)
+        e[1].record()
+        sp.spmv_convert(h, fmt)
+        e[2].record()
+        it, res = sp.spmv_cg(h, b, x, tol=1e-8, max_iters=500)
+        e[3].record()
+        torch.cuda.synchronize()
+        y = torch.empty(n, dtype=torch.float64, device=dev)
+        p0, p1 = ev(), ev()
+        p0.record()
+        for _ in range(10):
+            sp.spmv_mul(h, b, y)
+        p1.record()
+        torch.cuda.synchronize()
+        conv = e[0].elapsed_time(e[2])
+        solve = e[2].elapsed_time(e[3])
+        entry = {"format": fmt, "nnz": sp.spmv_info(h)["nnz"], "convert_ms": round(conv, 3),
+                 "cg_iterations": it, "cg_residual": res, "solve_ms": round(solve, 3),
+                 "ms_per_iteration": round(solve / max(it, 1), 4), "product_ms": round(p0.elapsed_time(p1) / 10, 4),
+                 "convert_per_iteration_ms": round(conv / max(it, 1), 4)}
+        if fmt == "hb":
+            with tempfile.TemporaryDirectory() as tmp:
+                path = os.path.join(tmp, "a.spmv")
+                t0 = time.perf_counter()
+                sp.spmv_save(h, path)
+                t1 = time.perf_counter()
+                g = sp.spmv_load(path)
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                entry.update(save_s=round(t1 - t0, 3), load_s=round(t2 - t1, 3),
+                             file_bytes=os.path.getsize(path))
+                sp.spmv_destroy(g)
+        out["formats"].append(entry)
+        sp.spmv_destroy(h)
+    return out
+
+
 # ------------------------------------------------------------------ precision leg
 
 def precision_leg(sp, torch, dev, synth, np):
@@ -627,6 +692,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-iterative", action="store_true")
     ap.add_argument("--batched-small", action="store_true", help="64 matrices, scales 10-18")
     args = ap.parse_args()
 
@@ -861,6 +927,7 @@ def main():
     batched = None if args.no_batched else batched_leg(sp, torch, dev, synth, np,
                                                          BATCH_SMALL if args.batched_small else BATCH)
     precision = None if args.no_precision else precision_leg(sp, torch, dev, synth, np)
+    iterative = None if args.no_iterative else iterative_leg(sp, torch, dev, synth, np)
 
     if world > 1:
         dist.destroy_process_group()
@@ -904,6 +971,7 @@ def main():
         "serving": serving,
         "batched": batched,
         "precision": precision,
+        "iterative": iterative,
         "cpu_baseline": cpu,
         "wall_s_timed": round(wall_s, 3),
     }

@@ -67,9 +67,14 @@ typedef enum {
 #define SPMV_DUP_SUM 0x0u       /* duplicates are added, in input order (default)       */
 #define SPMV_DUP_ERROR 0x2u     /* duplicates are rejected with SPMV_ERR_DUPLICATE       */
 
-/* Order of nonzeros inside an HB block. */
-#define SPMV_INNER_HILBERT 0    /* Hilbert order (BCOHCH, Section 4.2)                  */
+/* Order of nonzeros inside a block of the blocked format. */
+#define SPMV_INNER_HILBERT 0    /* Hilbert order (BCOHCH, Section 4.2; CSBH, Section 4.1) */
 #define SPMV_INNER_ROWMAJOR 1   /* row-wise (BCOHC, Section 4.2)                        */
+#define SPMV_INNER_ZMORTON 2    /* Z-Morton order (CSB, Section 3.1)                     */
+
+/* Order of the blocks of the blocked format. */
+#define SPMV_BLOCK_HILBERT 0    /* Hilbert order of the blocks (BCOHC/BCOHCH, Section 4.2) */
+#define SPMV_BLOCK_ROWMAJOR 1   /* block rows in turn (CSB/CSBH, Sections 3.1 and 4.1)     */
 
 /* Product of the HB format. */
 #define SPMV_HB_STAGED 0        /* block column by block column, x slice staged on chip   */
@@ -80,6 +85,7 @@ typedef struct {
     int32_t inner_order;  /* SPMV_INNER_*                                                */
     int32_t tile;         /* CSR_MERGE: path items per CTA tile; 0 = library default     */
     int32_t hb_product;   /* HB: SPMV_HB_STAGED (default) or SPMV_HB_CHUNKED             */
+    int32_t block_order;  /* HB: SPMV_BLOCK_HILBERT (default) or SPMV_BLOCK_ROWMAJOR       */
 } spmv_convert_opts;
 
 /*
@@ -133,6 +139,9 @@ spmv_status spmv_create_coo(int64_t m, int64_t n, int64_t nnz, const int32_t *ro
  *   HB: Hilbert key h(r, c) on the 2^K grid (K = ceil(log2 max(m, n))), radix sort on h
  *   (or on (h >> 2 log2_beta, r, c) for SPMV_INNER_ROWMAJOR), block segmentation,
  *   packed indices ((r mod beta) << 16 | (c mod beta)).  Requires beta <= 2^16.  With
+ *   block_order = SPMV_BLOCK_ROWMAJOR the blocks follow each other block row by block row
+ *   (CSB, Section 3.1, with SPMV_INNER_ZMORTON; CSBH, Section 4.1, with SPMV_INNER_HILBERT,
+ *   the block's own curve), sorted on (br * 2^(K - log2_beta) + bc, in-block key).  With
  *   hb_product = SPMV_HB_STAGED (the default) the conversion also lays the blocks out for
  *   the staged product (Sections 3.1, 3.2: the x slice of a block column held on chip):
  *   the entries of every block column (a slice of beta columns) in CRS order, in warp tiles
@@ -295,7 +304,7 @@ typedef struct {
     int64_t nblk;           /* non-empty HB blocks                                       */
     int64_t merge_tiles;    /* CSR_MERGE tiles                                           */
     int32_t merge_tile_items;
-    int32_t pad_;
+    int32_t hb_orders;      /* 16 x block order + inner order of the blocked arrays      */
     int64_t device_bytes;   /* device memory held by the handle                          */
 } spmv_info_t;
 

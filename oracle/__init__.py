@@ -114,6 +114,7 @@ def _declare(lib):
         "oracle_grid_order": (i32, [i64, i64]),
         "oracle_log2_beta": (i32, [i64, i64, i64]),
         "oracle_csr_to_hb": (i32, [i64, i64, p, p, p, i32, i32, p, p, p, p, p, p]),
+        "oracle_csr_to_csb": (i32, [i64, i64, p, p, p, i32, i32, p, p, p, p, p, p]),
         "oracle_hb_spmv": (None, [i64, i64, i32, p, p, p, p, p, p, p]),
         "oracle_merge_path_walk": (None, [i64, p, i64, p, i64, p, p]),
         "oracle_merge_path_search": (None, [i64, i64, p, i64, p, p]),
@@ -264,8 +265,10 @@ def log2_beta(n, x_bytes=8, slice_budget_bytes=200 * 1024, lib=None):
     return int((lib or load()).oracle_log2_beta(n, x_bytes, slice_budget_bytes))
 
 
-def csr_to_hb(m, n, row_ptr, col, val, log2beta, inner_order=0, lib=None):
-    """CRS -> Hilbert-ordered blocked format.  Returns dict of arrays."""
+def csr_to_hb(m, n, row_ptr, col, val, log2beta, inner_order=0, lib=None, block_order=0):
+    """CRS -> blocked format: Hilbert block order (block_order 0; inner_order 0 Hilbert, 1
+    row-major) or row-major block order (block_order 1, CSB / CSBH; inner_order 0 the block's
+    own Hilbert curve, 1 row-major, 2 Z-Morton).  Returns dict of arrays."""
     lib = lib or load()
     row_ptr, col, val = _i32(row_ptr), _i32(col), _f64(val)
     nnz = int(row_ptr[m])
@@ -275,8 +278,9 @@ def csr_to_hb(m, n, row_ptr, col, val, log2beta, inner_order=0, lib=None):
     br = np.empty(max(nnz, 1), np.int32)
     bc = np.empty(max(nnz, 1), np.int32)
     nb = ctypes.c_int64(0)
-    st = lib.oracle_csr_to_hb(m, n, _p(row_ptr), _p(col), _p(val), log2beta, inner_order, _p(idx), _p(vo),
-                              _p(bp), _p(br), _p(bc), ctypes.byref(nb))
+    fn = lib.oracle_csr_to_csb if block_order == 1 else lib.oracle_csr_to_hb
+    st = fn(m, n, _p(row_ptr), _p(col), _p(val), log2beta, inner_order, _p(idx), _p(vo),
+            _p(bp), _p(br), _p(bc), ctypes.byref(nb))
     if st != OK:
         raise OracleError(st, "csr_to_hb")
     k = nb.value

@@ -21,7 +21,9 @@
  *   oracle_log2_beta       Eq. 2 (CSB block size bound) + Section 3.1 constraints
  *   oracle_csr_to_hb       Section 4.2 (BCOHC / BCOHCH): nonzeros sorted on the Hilbert
  *                          curve, stored per beta x beta block as packed 16+16-bit triplets
- *   oracle_hb_spmv         block-by-block product over the structure above
+ *   oracle_csr_to_csb      Sections 3.1 and 4.1 (CSB / CSBH): row-major block order, Z-Morton
+ *                          (or the block's own Hilbert curve) inside every block
+ *   oracle_hb_spmv         block-by-block product over the structures above
  *   oracle_merge_path_search, oracle_merge_spmv
  *                          Section 3.3 and the merge-path figure: diagonal split of the
  *                          (row ends x nonzero indices) path; ties consume a row end first;
@@ -317,6 +319,56 @@ int oracle_csr_to_hb(int64_t m, int64_t n, const int32_t *row_ptr, const int32_t
     qsort(e, (size_t)nnz, sizeof(hb_ent), cmp_hb);
     int64_t nb = 0;
     uint64_t mask = ((uint64_t)1 << log2beta) - 1;
+    for (int64_t t = 0; t < nnz; ++t) {
+        uint64_t blk = e[t].key >> (2 * log2beta);
+        if (t == 0 || blk != (e[t - 1].key >> (2 * log2beta))) {
+            blk_ptr[nb] = (int32_t)t;
+            blk_row[nb] = (int32_t)(e[t].row >> log2beta);
+            blk_col[nb] = (int32_t)(e[t].col >> log2beta);
+            ++nb;
+        }
+        idx[t] = (uint32_t)((((uint64_t)e[t].row & mask) << 16) | ((uint64_t)e[t].col & mask));
+        if (data && val_out) val_out[t] = data[e[t].src];
+    }
+    blk_ptr[nb] = (int32_t)nnz;
+    *nblk_out = nb;
+    free(e);
+    return OK;
+}
+
+/*
+ * CRS -> compressed sparse blocks (Section 3.1, CSB, and Section 4.1, CSBH): the beta x beta
+ * blocks in row-major block order (block rows top to bottom, left to right inside a block
+ * row) and, inside every block, the nonzeros in Z-Morton order (inner_order 2: the row bit
+ * above the column bit at every level, the Z-Morton figure), in the Hilbert order of the
+ * block's own curve (inner_order 0, CSBH) or row by row (inner_order 1).  Same output arrays
+ * as oracle_csr_to_hb.
+ */
+int oracle_csr_to_csb(int64_t m, int64_t n, const int32_t *row_ptr, const int32_t *col_ind, const double *data,
+                      int log2beta, int inner_order, uint32_t *idx, double *val_out, int32_t *blk_ptr,
+                      int32_t *blk_row, int32_t *blk_col, int64_t *nblk_out) {
+    if (log2beta < 1 || log2beta > 16 || inner_order < 0 || inner_order > 2) return ERR_INVALID_ARG;
+    int K = oracle_grid_order(m, n);
+    if (log2beta > K) log2beta = K;
+    int64_t nnz = row_ptr[m];
+    hb_ent *e = (hb_ent *)malloc(sizeof(hb_ent) * (size_t)(nnz > 0 ? nnz : 1));
+    if (!e) return ERR_OOM;
+    const int64_t bcols = (int64_t)1 << (K - log2beta);   /* blocks per block row */
+    const uint64_t mask = ((uint64_t)1 << log2beta) - 1;
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int64_t j = col_ind[k];
+            uint64_t blk = (uint64_t)((i >> log2beta) * bcols + (j >> log2beta));
+            int64_t ri = i & (int64_t)mask, cj = j & (int64_t)mask;
+            uint64_t inner;
+            if (inner_order == 2) inner = oracle_zmorton_index(log2beta, ri, cj);
+            else if (inner_order == 0) inner = oracle_hilbert_index(log2beta, ri, cj);
+            else inner = ((uint64_t)ri << log2beta) | (uint64_t)cj;
+            e[k].key = (blk << (2 * log2beta)) | inner;
+            e[k].row = (int32_t)i; e[k].col = (int32_t)j; e[k].src = k;
+        }
+    qsort(e, (size_t)nnz, sizeof(hb_ent), cmp_hb);
+    int64_t nb = 0;
     for (int64_t t = 0; t < nnz; ++t) {
         uint64_t blk = e[t].key >> (2 * log2beta);
         if (t == 0 || blk != (e[t - 1].key >> (2 * log2beta))) {

@@ -30,7 +30,8 @@ SPMV_FMT_CSR_ROWSPLIT, SPMV_FMT_CSR_MERGE, SPMV_FMT_HB, SPMV_FMT_AUTO = range(4)
 SPMV_DEVICE_PTRS = 0x1
 SPMV_DUP_SUM = 0x0
 SPMV_DUP_ERROR = 0x2
-SPMV_INNER_HILBERT, SPMV_INNER_ROWMAJOR = 0, 1
+SPMV_INNER_HILBERT, SPMV_INNER_ROWMAJOR, SPMV_INNER_ZMORTON = 0, 1, 2
+SPMV_BLOCK_HILBERT, SPMV_BLOCK_ROWMAJOR = 0, 1
 SPMV_HB_STAGED, SPMV_HB_CHUNKED = 0, 1
 SPMV_COMP_TAU_DEFAULT = 0   # include/spmv.h
 SPMV_ACC_DEFAULT, SPMV_ACC_F32, SPMV_ACC_F64, SPMV_ACC_COMPENSATED, SPMV_ACC_SEGMENT = range(5)
@@ -41,14 +42,14 @@ ELEM_SIZE = {SPMV_F64: 8, SPMV_F32: 4, SPMV_BF16: 2, SPMV_PATTERN: 0}
 
 class spmv_convert_opts(ctypes.Structure):
     _fields_ = [("log2_beta", ctypes.c_int32), ("inner_order", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("hb_product", ctypes.c_int32)]
+                ("hb_product", ctypes.c_int32), ("block_order", ctypes.c_int32)]
 
 
 class spmv_info_t(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("format", ctypes.c_int32),
                 ("dtype", ctypes.c_int32), ("log2_beta", ctypes.c_int32), ("grid_order", ctypes.c_int32),
                 ("nblk", ctypes.c_int64), ("merge_tiles", ctypes.c_int64), ("merge_tile_items", ctypes.c_int32),
-                ("pad_", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+                ("hb_orders", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
 
 
 class spmv_tune_result(ctypes.Structure):
@@ -206,10 +207,14 @@ def spmv_create_coo(m, n, row_ind, col_ind, data=None, dtype=None, flags=SPMV_DU
 
 
 def spmv_convert(h: Handle, fmt="merge", log2_beta=0, inner_order=SPMV_INNER_HILBERT, tile=0,
-                 hb_product=SPMV_HB_STAGED, stream=None):
-    """Build a storage format (Section 5.1) and make it the active one."""
+                 hb_product=SPMV_HB_STAGED, block_order=SPMV_BLOCK_HILBERT, stream=None):
+    """Build a storage format (Section 5.1) and make it the active one ("csb": the blocked
+    format with row-major block order and Z-Morton inner order, Section 3.1)."""
+    if fmt == "csb":
+        fmt, block_order = "hb", SPMV_BLOCK_ROWMAJOR
+        inner_order = SPMV_INNER_ZMORTON if inner_order == SPMV_INNER_HILBERT else inner_order
     f = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
-    opts = spmv_convert_opts(log2_beta, inner_order, tile, hb_product)
+    opts = spmv_convert_opts(log2_beta, inner_order, tile, hb_product, block_order)
     _check(_lib.spmv_convert(h.ptr, f, ctypes.byref(opts), _stream(stream)), "spmv_convert")
 
 

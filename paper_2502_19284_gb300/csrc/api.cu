@@ -372,7 +372,7 @@ spmv_status spmv_convert(spmv_handle h, spmv_format f, const spmv_convert_opts *
     SPMV_TRY(check_handle(h));
     forget_batch_plans(h);
     cudaStream_t s = (cudaStream_t)stream;
-    spmv_convert_opts o = {0, SPMV_INNER_HILBERT, 0, SPMV_HB_STAGED};
+    spmv_convert_opts o = {0, SPMV_INNER_HILBERT, 0, SPMV_HB_STAGED, SPMV_BLOCK_HILBERT};
     if (opt) o = *opt;
     if (f == SPMV_FMT_AUTO) {
         // Row-length statistics decide: very long rows favour the merge path (it splits
@@ -385,8 +385,13 @@ spmv_status spmv_convert(spmv_handle h, spmv_format f, const spmv_convert_opts *
         set_error("spmv_convert: unknown format");
         return SPMV_ERR_INVALID_ARG;
     }
-    if (o.inner_order != SPMV_INNER_HILBERT && o.inner_order != SPMV_INNER_ROWMAJOR) {
+    if (o.inner_order != SPMV_INNER_HILBERT && o.inner_order != SPMV_INNER_ROWMAJOR &&
+        o.inner_order != SPMV_INNER_ZMORTON) {
         set_error("spmv_convert: unknown inner order");
+        return SPMV_ERR_INVALID_ARG;
+    }
+    if (o.block_order != SPMV_BLOCK_HILBERT && o.block_order != SPMV_BLOCK_ROWMAJOR) {
+        set_error("spmv_convert: unknown block order");
         return SPMV_ERR_INVALID_ARG;
     }
     if (o.log2_beta < 0 || o.log2_beta > 16) {
@@ -409,7 +414,8 @@ spmv_status spmv_convert(spmv_handle h, spmv_format f, const spmv_convert_opts *
         int lb = o.log2_beta ? o.log2_beta : default_log2_beta(h->n, h->dt == SPMV_F64 ? 8 : 4);
         const int K = bits_for(std::max<int64_t>(std::max(h->m, h->n), 2));
         if (lb > K) lb = K;
-        if (!h->has_hb || h->log2beta != lb || h->inner != o.inner_order) SPMV_TRY(build_hb(h, lb, o.inner_order, s));
+        if (!h->has_hb || h->log2beta != lb || h->inner != o.inner_order || h->block_order != o.block_order)
+            SPMV_TRY(build_hb(h, lb, o.inner_order, s, o.block_order));
         if (o.hb_product == SPMV_HB_STAGED && (!h->has_stage || h->stage_lb != lb)) SPMV_TRY(build_stage(h, lb, s));
         h->hb_chunked = o.hb_product == SPMV_HB_CHUNKED;
     }
@@ -627,6 +633,7 @@ spmv_status spmv_info(spmv_handle h, spmv_info_t *out) {
     out->nblk = h->nblk;
     out->merge_tiles = h->tiles;
     out->merge_tile_items = h->tile_items;
+    out->hb_orders = h->has_hb ? 16 * h->block_order + h->inner : 0;
     out->device_bytes = h->bytes;
     return SPMV_OK;
 }

@@ -202,7 +202,7 @@ struct spmv_matrix {
 
     // Hilbert-ordered blocked format
     bool has_hb = false;
-    int32_t log2beta = 0, grid_K = 0, inner = 0;
+    int32_t log2beta = 0, grid_K = 0, inner = 0, block_order = 0;
     int64_t nblk = 0;
     uint32_t *hb_idx = nullptr;
     void *hb_val = nullptr;

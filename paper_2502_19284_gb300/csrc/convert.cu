@@ -603,6 +603,101 @@ __global__ void k_hb_blocks(const uint64_t *__restrict__ keys, const uint32_t *_
     }
 }
 
+// ---------------------------------------------------------------- other block orders
+// Keys of the block orders and inner orders besides the Hilbert-ordered HB above: blocks in
+// row-major order (CSB and CSBH, Sections 3.1 and 4.1) or in Hilbert order with a Z-Morton
+// inner order.  key = (block key << 2 lb) | in-block key, where the block key is the block's
+// Hilbert index on the (K - lb)-order block grid or br * 2^(K - lb) + bc, and the in-block key
+// is the Z-Morton index (row bit above the column bit at every level), the Hilbert index of
+// the block's own curve of order lb, or the row-major cell index.
+
+__device__ __forceinline__ uint32_t zm_spread(uint32_t v) {   // bits of v to the even positions
+    v &= 0xFFFFu;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+__device__ __forceinline__ uint32_t zm_gather(uint32_t v) {   // the even bits of v, packed
+    v &= 0x55555555u;
+    v = (v | (v >> 1)) & 0x33333333u;
+    v = (v | (v >> 2)) & 0x0F0F0F0Fu;
+    v = (v | (v >> 4)) & 0x00FF00FFu;
+    v = (v | (v >> 8)) & 0x0000FFFFu;
+    return v;
+}
+
+__device__ __forceinline__ uint64_t blk_key(uint32_t r, uint32_t c, int K, int lb, int border, int inner,
+                                            const uint16_t *fwd4) {
+    const uint32_t br = r >> lb, bc = c >> lb, mask = (1u << lb) - 1u, ri = r & mask, ci = c & mask;
+    const uint64_t bk = border == SPMV_BLOCK_HILBERT ? hilbert_key4(K - lb, br, bc, fwd4)
+                                                     : ((uint64_t)br << (K - lb)) | bc;
+    uint64_t ik;
+    if (inner == SPMV_INNER_ZMORTON) ik = ((uint64_t)zm_spread(ri) << 1) | zm_spread(ci);
+    else if (inner == SPMV_INNER_HILBERT) ik = hilbert_key4(lb, ri, ci, fwd4);
+    else ik = ((uint64_t)ri << lb) | ci;
+    return (bk << (2 * lb)) | ik;
+}
+
+__device__ __forceinline__ void blk_cell(uint64_t key, int K, int lb, int border, int inner, uint32_t *br,
+                                         uint32_t *bc, uint32_t *ri, uint32_t *ci) {
+    const uint64_t bk = key >> (2 * lb), ik = key & ((1ull << (2 * lb)) - 1ull);
+    if (border == SPMV_BLOCK_HILBERT) {
+        hilbert_cell1(K - lb, bk, br, bc);
+    } else {
+        *br = (uint32_t)(bk >> (K - lb));
+        *bc = (uint32_t)(bk & ((1ull << (K - lb)) - 1ull));
+    }
+    if (inner == SPMV_INNER_ZMORTON) {
+        *ri = zm_gather((uint32_t)(ik >> 1));
+        *ci = zm_gather((uint32_t)ik);
+    } else if (inner == SPMV_INNER_HILBERT) {
+        hilbert_cell1(lb, ik, ri, ci);
+    } else {
+        *ri = (uint32_t)(ik >> lb);
+        *ci = (uint32_t)(ik & ((1ull << lb) - 1ull));
+    }
+}
+
+// One thread per CRS entry; its row by bisection of row_ptr.
+__global__ void k_blk_keys(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int64_t m,
+                           int64_t nnz, int K, int lb, int border, int inner, uint64_t *__restrict__ keys,
+                           uint32_t *__restrict__ perm) {
+    __shared__ __align__(16) uint16_t s_fwd4[1024];
+    hilbert_stage(s_fwd4, g_hilbert4.fwd);
+    __syncthreads();
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nnz) return;
+    const int64_t r = row_of(row_ptr, 0, m - 1, k);
+    keys[k] = blk_key((uint32_t)r, (uint32_t)col[k], K, lb, border, inner, s_fwd4);
+    perm[k] = (uint32_t)k;
+}
+
+__global__ void k_blk_fill(const uint64_t *__restrict__ keys, int64_t nnz, int K, int lb, int border, int inner,
+                           uint32_t *__restrict__ idx, uint32_t *__restrict__ head) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nnz) return;
+    uint32_t br, bc, ri, ci;
+    blk_cell(keys[t], K, lb, border, inner, &br, &bc, &ri, &ci);
+    idx[t] = (ri << 16) | ci;
+    head[t] = (t == 0 || (keys[t - 1] >> (2 * lb)) != (keys[t] >> (2 * lb))) ? 1u : 0u;
+}
+
+__global__ void k_blk_blocks(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ head,
+                             const uint32_t *__restrict__ bid, int64_t nnz, int K, int lb, int border, int inner,
+                             int32_t *__restrict__ blk_ptr, int32_t *__restrict__ blk_row,
+                             int32_t *__restrict__ blk_col) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nnz || !head[t]) return;
+    uint32_t br, bc, ri, ci;
+    blk_cell(keys[t], K, lb, border, inner, &br, &bc, &ri, &ci);
+    const uint32_t b = bid[t];
+    blk_ptr[b] = (int32_t)t;
+    blk_row[b] = (int32_t)br;
+    blk_col[b] = (int32_t)bc;
+}
+
 __global__ void k_hilbert_keys(int K, int64_t n, const int32_t *__restrict__ rows, const int32_t *__restrict__ cols,
                                uint64_t *__restrict__ keys) {
     __shared__ __align__(16) uint16_t s_fwd4[1024], s_inv4[1024];
@@ -953,7 +1048,7 @@ spmv_status hb_chunk_table(spmv_matrix *h, cudaStream_t s) {
     return SPMV_OK;
 }
 
-spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s) {
+spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s, int border) {
     const int64_t m = h->m, n = h->n, nnz = h->nnz;
     const int es = elem_size(h->dt);
     const int K = bits_for(std::max<int64_t>(std::max(m, n), 2));
@@ -971,23 +1066,35 @@ spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s) {
         SPMV_TRY(tmp.alloc(std::max(radix_temp_bytes(nnz), scan_temp_bytes(nnz)), "hb sort temp"));
         SPMV_TRY(idx.alloc((size_t)nnz * 4, "hb idx"));
         if (es) SPMV_TRY(val.alloc((size_t)nnz * es, "hb values"));
-        const int64_t ktiles = (nnz + HB_KEY_TILE - 1) / HB_KEY_TILE;
-        DevBuf trow(s);
-        SPMV_TRY(trow.alloc((size_t)(ktiles + 1) * 8, "hb key tile rows"));
-        SPMV_LAUNCH("k_tile_rows", s, (k_tile_rows<<<grid_for(ktiles + 1), CB, 0, s>>>(h->row_ptr, m, nnz, ktiles,
-                                                                                     trow.as<int64_t>())));
-        SPMV_LAUNCH_CHECK("hb key tile rows");
-        SPMV_LAUNCH("k_hb_keys", s, (k_hb_keys<<<(unsigned)ktiles, CB, 0, s>>>(h->row_ptr, h->col, m, nnz,
-                                                                             trow.as<int64_t>(), K, log2b, inner,
-                                                                             keys.as<uint64_t>(), perm.as<uint32_t>())));
-        SPMV_LAUNCH_CHECK("hb keys");
+        const bool fast = border == SPMV_BLOCK_HILBERT && inner != SPMV_INNER_ZMORTON;   // the HB path
+        if (fast) {
+            const int64_t ktiles = (nnz + HB_KEY_TILE - 1) / HB_KEY_TILE;
+            DevBuf trow(s);
+            SPMV_TRY(trow.alloc((size_t)(ktiles + 1) * 8, "hb key tile rows"));
+            SPMV_LAUNCH("k_tile_rows", s, (k_tile_rows<<<grid_for(ktiles + 1), CB, 0, s>>>(h->row_ptr, m, nnz, ktiles,
+                                                                                         trow.as<int64_t>())));
+            SPMV_LAUNCH_CHECK("hb key tile rows");
+            SPMV_LAUNCH("k_hb_keys", s, (k_hb_keys<<<(unsigned)ktiles, CB, 0, s>>>(h->row_ptr, h->col, m, nnz,
+                                                                                 trow.as<int64_t>(), K, log2b, inner,
+                                                                                 keys.as<uint64_t>(), perm.as<uint32_t>())));
+            SPMV_LAUNCH_CHECK("hb keys");
+        } else {
+            SPMV_LAUNCH("k_blk_keys", s, (k_blk_keys<<<grid_for(nnz), CB, 0, s>>>(h->row_ptr, h->col, m, nnz, K, log2b,
+                                                                                border, inner, keys.as<uint64_t>(),
+                                                                                perm.as<uint32_t>())));
+            SPMV_LAUNCH_CHECK("blocked keys");
+        }
         bool alt = false;
         SPMV_TRY(sort_begin(h, s));
         SPMV_TRY(radix_sort_pairs(keys.as<uint64_t>(), keys_alt.as<uint64_t>(), perm.as<uint32_t>(),
                                   perm_alt.as<uint32_t>(), nnz, 0, 2 * K, tmp.p, s, &alt, h->status_dev + 1));
         uint64_t *Ks = alt ? keys_alt.as<uint64_t>() : keys.as<uint64_t>();
         uint32_t *Ps = alt ? perm_alt.as<uint32_t>() : perm.as<uint32_t>();
-        SPMV_LAUNCH("k_hb_fill", s, (k_hb_fill<<<grid_for((nnz + HB_FILL_U - 1) / HB_FILL_U), CB, 0, s>>>(Ks, nnz, K, log2b, inner, idx.as<uint32_t>(), head.as<uint32_t>())));
+        if (fast)
+            SPMV_LAUNCH("k_hb_fill", s, (k_hb_fill<<<grid_for((nnz + HB_FILL_U - 1) / HB_FILL_U), CB, 0, s>>>(Ks, nnz, K, log2b, inner, idx.as<uint32_t>(), head.as<uint32_t>())));
+        else
+            SPMV_LAUNCH("k_blk_fill", s, (k_blk_fill<<<grid_for(nnz), CB, 0, s>>>(Ks, nnz, K, log2b, border, inner,
+                                                                                idx.as<uint32_t>(), head.as<uint32_t>())));
         SPMV_LAUNCH_CHECK("hb fill");
         if (es) SPMV_TRY(gather_values(h->val, h->dt, Ps, nnz, val.p, s));
         SPMV_TRY(exclusive_scan_u32(head.as<uint32_t>(), bid.as<uint32_t>(), nnz, tmp.p, s));
@@ -1001,8 +1108,13 @@ spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s) {
         SPMV_TRY(bptr.alloc((size_t)(nblk + 1) * 4, "hb blk_ptr"));
         SPMV_TRY(brow.alloc((size_t)nblk * 4, "hb blk_row"));
         SPMV_TRY(bcol.alloc((size_t)nblk * 4, "hb blk_col"));
-        SPMV_LAUNCH("k_hb_blocks", s, (k_hb_blocks<<<grid_for((nnz + 3) / 4), CB, 0, s>>>(Ks, head.as<uint32_t>(), bid.as<uint32_t>(), nnz, K, log2b, inner,
-                                                 bptr.as<int32_t>(), brow.as<int32_t>(), bcol.as<int32_t>())));
+        if (fast)
+            SPMV_LAUNCH("k_hb_blocks", s, (k_hb_blocks<<<grid_for((nnz + 3) / 4), CB, 0, s>>>(Ks, head.as<uint32_t>(), bid.as<uint32_t>(), nnz, K, log2b, inner,
+                                                     bptr.as<int32_t>(), brow.as<int32_t>(), bcol.as<int32_t>())));
+        else
+            SPMV_LAUNCH("k_blk_blocks", s, (k_blk_blocks<<<grid_for(nnz), CB, 0, s>>>(Ks, head.as<uint32_t>(), bid.as<uint32_t>(), nnz, K,
+                                                                                    log2b, border, inner, bptr.as<int32_t>(),
+                                                                                    brow.as<int32_t>(), bcol.as<int32_t>())));
         SPMV_LAUNCH_CHECK("hb blocks");
         *h->status_host = (uint32_t)nnz;   // pinned staging slot for the tail entry
         SPMV_CUDA_TRY(cudaMemcpyAsync(bptr.as<int32_t>() + nblk, h->status_host, 4, cudaMemcpyHostToDevice, s));
@@ -1034,6 +1146,7 @@ spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s) {
     h->log2beta = log2b;
     h->grid_K = K;
     h->inner = inner;
+    h->block_order = border;
     h->has_hb = true;
     h->bytes += nnz * (4 + es) + nblk * 12 + 4 + (nchunks + 1) * 4;
     return SPMV_OK;

@@ -46,7 +46,7 @@ spmv_status launch_validate(const int32_t *row, const int32_t *col, int64_t nnz,
 spmv_status build_csr(spmv_matrix *h, cudaStream_t s);
 spmv_status build_bins(spmv_matrix *h, cudaStream_t s);
 spmv_status build_merge(spmv_matrix *h, int tile_items, cudaStream_t s);
-spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s);
+spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s, int border = SPMV_BLOCK_HILBERT);
 // FP64 matrices: check the double-float window of the stored values and allocate the
 // x-split scratch (n float pairs + a flag word).
 spmv_status build_df(spmv_matrix *h, cudaStream_t s);

@@ -9,7 +9,7 @@
 //   8-byte magic "SPMVGB01", uint32 version, uint32 section flags (1 CRS, 2 HB, 4 staged),
 //   int64 m, n, nnz, int32 dtype, int32 active format, int32 hb_chunked, int32 reserved;
 //   CRS: row_ptr (m+1 int32), col (nnz int32), values (nnz x element size);
-//   HB: int32 log2beta, grid K, inner order, reserved; int64 nblk; packed indices (nnz uint32),
+//   HB: int32 log2beta, grid K, inner order, block order; int64 nblk; packed indices (nnz uint32),
 //       values, blk_ptr (nblk+1), blk_row (nblk), blk_col (nblk) (int32);
 //   staged: int32 lb, kind; int64 slices, tiles; tile headers (16 B each), words (256 x 4 B per
 //       tile), values (256 per tile), first tile per slice (slices+1 uint32), lane headers
@@ -138,7 +138,7 @@ spmv_status spmv_save(spmv_handle h, const char *path, void *stream) {
     SPMV_TRY(put(f, h->col, (size_t)h->nnz * 4, stage.p, s, path, hs));
     if (es) SPMV_TRY(put(f, h->val, (size_t)h->nnz * es, stage.p, s, path, hs));
     if (h->has_hb) {
-        ok = wr(f, h->log2beta) && wr(f, h->grid_K) && wr(f, h->inner) && wr(f, reserved) && wr(f, h->nblk);
+        ok = wr(f, h->log2beta) && wr(f, h->grid_K) && wr(f, h->inner) && wr(f, h->block_order) && wr(f, h->nblk);
         if (!ok) return io_error("spmv_save: write failed", path);
         SPMV_TRY(put(f, h->hb_idx, (size_t)h->nnz * 4, stage.p, s, path, hs));
         if (es) SPMV_TRY(put(f, h->hb_val, (size_t)h->nnz * es, stage.p, s, path, hs));
@@ -215,7 +215,7 @@ spmv_status spmv_load(const char *path, void *stream, spmv_handle *out) {
         int32_t lb = 0, K = 0, inner = 0, r2 = 0;
         int64_t nblk = 0;
         if (!(rd(f, lb) && rd(f, K) && rd(f, inner) && rd(f, r2) && rd(f, nblk)) || nblk < 0 || nblk > nnz ||
-            lb < 1 || lb > 16)
+            lb < 1 || lb > 16 || inner < 0 || inner > 2 || r2 < 0 || r2 > 1)
             return io_error("spmv_load: damaged blocked section", path);
         SPMV_TRY(get(f, &p, (size_t)nnz * 4, 0, stage.p, s, "hb idx", path, hs));
         h->hb_idx = (uint32_t *)p;
@@ -233,6 +233,7 @@ spmv_status spmv_load(const char *path, void *stream, spmv_handle *out) {
         h->log2beta = lb;
         h->grid_K = K;
         h->inner = inner;
+        h->block_order = r2;
         h->has_hb = true;
         h->bytes += nnz * (4 + es) + nblk * 12 + 4;
     }
@@ -275,7 +276,7 @@ spmv_status spmv_load(const char *path, void *stream, spmv_handle *out) {
     // the active format: its derived tables are cheap to rebuild from the stored arrays
     if (fmt >= 0) {
         spmv_convert_opts o = {h->has_hb ? h->log2beta : 0, h->has_hb ? h->inner : 0, 0,
-                               hbc ? SPMV_HB_CHUNKED : SPMV_HB_STAGED};
+                               hbc ? SPMV_HB_CHUNKED : SPMV_HB_STAGED, h->has_hb ? h->block_order : 0};
         SPMV_TRY(spmv_convert(h, (spmv_format)fmt, &o, stream));
     }
     guard.h = nullptr;
