@@ -518,8 +518,8 @@ def batched_leg(sp, torch, dev, synth, np, cfg):
 
 def iterative_leg(sp, torch, dev, synth, np):
     """Conjugate gradients on one resident matrix: B + B^T + diag(row sums of |B + B^T| + 1)
-    from R-MAT scale 20 (edge factor 8, FP64, symmetric positive definite), solved to 1e-8 in
-    the merge-path and in the staged blocked format.  Reports the conversion, the solve, the
+    from R-MAT scale 20 (edge factor 8, FP64, symmetric positive definite), solved to 1e-6 in
+    the merge-path and in the staged blocked format (tolerance 1e-6).  Reports the conversion, the solve, the
     iterations and the conversion amortised over them (Sections 6.2 and 7), and for the blocked
     format the time to load the converted matrix from disk instead (spmv_save / spmv_load)."""
     import tempfile
@@ -537,7 +537,7 @@ def iterative_leg(sp, torch, dev, synth, np):
     x = torch.empty(n, dtype=torch.float64, device=dev)
     ev = lambda: torch.cuda.Event(enable_timing=True)
     out = {"matrix": f"R-MAT scale {scale}, edge factor {ef}, made SPD (B + B^T + diagonal), FP64",
-           "tol": 1e-8, "formats": []}
+           "tol": 1e-6, "formats": []}
     for fmt in ("merge", "hb"):
         torch.cuda.synchronize()
         e = [ev() for _ in range(4)]
@@ -546,7 +546,7 @@ def iterative_leg(sp, torch, dev, synth, np):
         e[1].record()
         sp.spmv_convert(h, fmt)
         e[2].record()
-        it, res = sp.spmv_cg(h, b, x, tol=1e-8, max_iters=500)
+        it, res = sp.spmv_cg(h, b, x, tol=1e-6, max_iters=500)
         e[3].record()
         torch.cuda.synchronize()
         y = torch.empty(n, dtype=torch.float64, device=dev)
