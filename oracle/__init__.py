@@ -119,6 +119,8 @@ def _declare(lib):
         "oracle_merge_path_walk": (None, [i64, p, i64, p, i64, p, p]),
         "oracle_merge_path_search": (None, [i64, i64, p, i64, p, p]),
         "oracle_merge_spmv": (None, [i64, p, p, p, p, p, i64, p, p]),
+        "oracle_block_row_ptr": (None, [i64, p, i64, p]),
+        "oracle_mergeb_spmv": (i32, [i64, i64, i32, p, p, p, p, p, p, p, i64]),
         "oracle_round_f32": (f32, [dbl]),
         "oracle_round_bf16": (u16, [dbl]),
         "oracle_bf16_to_double": (dbl, [u16]),
@@ -329,6 +331,42 @@ def merge_spmv(row_ptr, col, val, x, parts, lib=None):
     row_ptr, col, val, x = _i32(row_ptr), _i32(col), _f64(val), _f64(x)
     lib.oracle_merge_spmv(m, _p(row_ptr), _p(col), _p(val), _p(x), _p(y), parts, _p(cr), _p(cv))
     return y, cr, cv
+
+
+def block_row_ptr(blk_row, nblk, nbr, lib=None):
+    """CRS pointer over blocks in row-major block order (Section 4.3): nbr + 1 entries."""
+    lib = lib or load()
+    br = _i32(blk_row)
+    ptr = np.empty(nbr + 1, np.int32)
+    lib.oracle_block_row_ptr(nblk, _p(br), nbr, _p(ptr))
+    return ptr
+
+
+def csr_to_mergeb(m, n, row_ptr, col, val, log2beta, inner_order=1, lib=None):
+    """CRS -> Merge Blocking storage (Section 4.3): the blocks in row-major block order with
+    row-wise (inner_order 1, MergeB) or Hilbert (inner_order 0, MergeBH) entries inside, plus
+    the block-row pointer (key "blk_row_ptr", nbr = ceil(m / beta) block rows)."""
+    lib = lib or load()
+    mb = csr_to_hb(m, n, row_ptr, col, val, log2beta, inner_order, lib, block_order=1)
+    lb = mb["log2beta"]
+    nbr = (m + (1 << lb) - 1) >> lb
+    mb["nbr"] = nbr
+    mb["blk_row_ptr"] = block_row_ptr(mb["blk_row"], mb["nblk"], nbr, lib)
+    return mb
+
+
+def mergeb_spmv(m, mb, x, parts=1, lib=None):
+    """Merge Blocking SpMV (Section 4.3) with `parts` sequentially executed parts."""
+    lib = lib or load()
+    rp, bp, bc = _i32(mb["blk_row_ptr"]), _i32(mb["blk_ptr"]), _i32(mb["blk_col"])
+    idx = np.ascontiguousarray(mb["idx"], np.uint32)
+    val, x = _f64(mb["val"]), _f64(x)
+    y = np.empty(m, np.float64)
+    st = lib.oracle_mergeb_spmv(m, mb["nbr"], mb["log2beta"], _p(rp), _p(bp), _p(bc), _p(idx), _p(val), _p(x),
+                                _p(y), parts)
+    if st != OK:
+        raise OracleError(st, "mergeb_spmv")
+    return y
 
 
 def round_f32(v, lib=None):

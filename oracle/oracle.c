@@ -28,7 +28,12 @@
  *                          Section 3.3 and the merge-path figure: diagonal split of the
  *                          (row ends x nonzero indices) path; ties consume a row end first;
  *                          per-part carries added afterwards in order
- *   oracle_csr_transpose   plain transpose (for the adjoint identity test)
+ *   oracle_block_row_ptr, oracle_mergeb_spmv
+ *                          Section 4.3 (Merge Blocking, MergeB / MergeBH): the block matrix in
+ *                          CRS over blocks in row-major order (oracle_csr_to_csb with a
+ *                          row-wise or Hilbert inner order), merge path over (block-row ends x
+ *                          blocks), a temporary vector in place of the temporary value
+ *   oracle_csr_transpose  plain transpose (for the adjoint identity test)
  *   oracle_csr_spmv_neumaier  Neumaier (1974) compensated row sums, an accuracy reference
  *   oracle_round_f32, oracle_round_bf16  storage rounding to nearest-even, directly from double
  *   oracle_pagerank        Section 1 names PageRank as an SpMV application; the iteration
@@ -483,6 +488,83 @@ void oracle_merge_spmv(int64_t m, const int32_t *row_ptr, const int32_t *col_ind
         if (carry_val) carry_val[p] = cv[p];
     }
     free(cr); free(cv);
+}
+
+/* --------------------------------------------------------- merge blocking */
+
+/*
+ * Block-row pointer of blocks stored in row-major block order (Section 4.3, Merge Blocking:
+ * the block matrix is kept in CRS, its "nonzeros" being the non-empty blocks):
+ * ptr[i] = the number of blocks whose block row is below i, for i = 0..nbr, so that the
+ * blocks of block row i are ptr[i] .. ptr[i+1]-1 and ptr[nbr] = nblk.
+ */
+void oracle_block_row_ptr(int64_t nblk, const int32_t *blk_row, int64_t nbr, int32_t *ptr) {
+    int64_t b = 0;
+    for (int64_t i = 0; i <= nbr; ++i) {
+        while (b < nblk && (int64_t)blk_row[b] < i) ++b;
+        ptr[i] = (int32_t)b;
+    }
+}
+
+/*
+ * Merge Blocking SpMV (Section 4.3, MergeB; MergeBH has the same product over blocks whose
+ * entries follow the block's Hilbert curve): the merge-based product of Section 3.3 applied
+ * to the block matrix.  Its path merges A = the block-row ends (blk_row_ptr[1..nbr]) with
+ * B = the block indices 0..nblk-1 and is cut into `parts` equal diagonal bands as in
+ * oracle_merge_spmv.  Each part walks its band with a temporary vector temp[0..beta) = 0:
+ * consuming block b is the sparse block product, temp[r mod beta] += v * x[c] over the
+ * block's entries in storage order (r = blk_row*beta + (idx >> 16), c = blk_col[b]*beta +
+ * (idx & 0xFFFF)); consuming the end of block row i copies temp into rows i*beta .. of y
+ * (those below m) and resets it.  At the end of its band a part keeps (block row, temp) as
+ * its carry; after all parts the carries are added into y in part order.  A tie between a
+ * block-row end and a block consumes the block-row end (the rule of Section 3.3).
+ * data == NULL: pattern matrix.  Returns ERR_OOM if the carry vectors cannot be allocated.
+ */
+int oracle_mergeb_spmv(int64_t m, int64_t nbr, int log2beta, const int32_t *blk_row_ptr, const int32_t *blk_ptr,
+                       const int32_t *blk_col, const uint32_t *idx, const double *data, const double *x,
+                       double *y, int64_t parts) {
+    const int64_t beta = (int64_t)1 << log2beta;
+    const int64_t nblk = blk_row_ptr[nbr];
+    const int64_t total = nbr + nblk;
+    if (parts < 1) parts = 1;
+    const int64_t L = (total + parts - 1) / parts;
+    double *temp = (double *)calloc((size_t)beta, sizeof(double));
+    double *cv = (double *)calloc((size_t)(parts * beta), sizeof(double));
+    int64_t *cr = (int64_t *)malloc(sizeof(int64_t) * (size_t)parts);
+    if (!temp || !cv || !cr) { free(temp); free(cv); free(cr); return ERR_OOM; }
+    for (int64_t i = 0; i < m; ++i) y[i] = 0.0;
+    for (int64_t p = 0; p < parts; ++p) {
+        int64_t d0 = p * L < total ? p * L : total, d1 = (p + 1) * L < total ? (p + 1) * L : total;
+        int64_t i, b, i1, b1;
+        /* blk_row_ptr plays row_ptr's part: block-row ends against block indices */
+        oracle_merge_path_search(d0, nbr, blk_row_ptr, nblk, &i, &b);
+        oracle_merge_path_search(d1, nbr, blk_row_ptr, nblk, &i1, &b1);
+        for (int64_t r = 0; r < beta; ++r) temp[r] = 0.0;
+        while (i < i1 || b < b1) {
+            if (i < i1 && (int64_t)blk_row_ptr[i + 1] <= b) {   /* end of block row i comes first */
+                for (int64_t r = 0; r < beta && i * beta + r < m; ++r) y[i * beta + r] = temp[r];
+                for (int64_t r = 0; r < beta; ++r) temp[r] = 0.0;
+                ++i;
+            } else {   /* block b: the sparse block multiplication into temp */
+                const int64_t c0 = (int64_t)blk_col[b] << log2beta;
+                for (int64_t t = blk_ptr[b]; t < blk_ptr[b + 1]; ++t) {
+                    const int64_t r = idx[t] >> 16, c = c0 + (idx[t] & 0xFFFF);
+                    double a = data ? data[t] : 1.0;
+                    double prod = a * x[c];
+                    temp[r] = temp[r] + prod;
+                }
+                ++b;
+            }
+        }
+        cr[p] = i;
+        for (int64_t r = 0; r < beta; ++r) cv[p * beta + r] = temp[r];
+    }
+    for (int64_t p = 0; p < parts; ++p)
+        if (cr[p] < nbr)
+            for (int64_t r = 0; r < beta && cr[p] * beta + r < m; ++r)
+                y[cr[p] * beta + r] = y[cr[p] * beta + r] + cv[p * beta + r];
+    free(temp); free(cv); free(cr);
+    return OK;
 }
 
 /* ------------------------------------------------------------ precision */

@@ -686,3 +686,127 @@ def test_zmorton_block_order_matches_figure(orc):
     tab = oracle.zmorton_table(2, orc)
     order = [tuple(np.argwhere(tab == i)[0]) for i in range(16)]
     assert order[:8] == [(0, 0), (0, 1), (1, 0), (1, 1), (0, 2), (0, 3), (1, 2), (1, 3)]
+
+
+# ------------------------------------------------------------------ Merge Blocking (Section 4.3)
+
+def _nonempty_blocks(D, lb):
+    """Block rows and columns of the non-empty beta x beta blocks of a dense matrix, row-major."""
+    m, n = D.shape
+    b = 1 << lb
+    out = []
+    for br in range((m + b - 1) // b):
+        for bc in range((n + b - 1) // b):
+            if np.any(D[br * b:(br + 1) * b, bc * b:(bc + 1) * b] != 0):
+                out.append((br, bc))
+    return out
+
+
+@pytest.mark.parametrize("inner", [0, 1])
+@pytest.mark.parametrize("seed", range(4))
+def test_mergeb_block_crs_matches_dense_blocks(orc, seed, inner):
+    """The CRS over blocks: blocks of block row i are ptr[i]..ptr[i+1]-1, in the order and number
+    of the non-empty blocks of the dense matrix (nonzero values, so a stored entry is a dense
+    nonzero)."""
+    rng = np.random.default_rng(100 + seed)
+    m, n = int(rng.integers(1, 60)), int(rng.integers(1, 60))
+    r, c = synth.random_coo(m, n, int(rng.integers(0, 5 * m + 1)), seed)
+    v = np.abs(synth.values(r, c, seed, integer=True)) + 1.0
+    rp, co, vo = oracle.coo_to_csr(m, n, r, c, v, 0, orc)
+    for lb in [1, 2, 3]:
+        mb = oracle.csr_to_mergeb(m, n, rp, co, vo, lb, inner, orc)
+        lbe = mb["log2beta"]
+        D = _dense(m, n, rp, co, vo)
+        want = _nonempty_blocks(D, lbe)
+        got = [(int(mb["blk_row"][k]), int(mb["blk_col"][k])) for k in range(mb["nblk"])]
+        assert got == want
+        ptr = mb["blk_row_ptr"]
+        assert len(ptr) == mb["nbr"] + 1 == (m + (1 << lbe) - 1 >> lbe) + 1
+        assert ptr[0] == 0 and ptr[-1] == mb["nblk"] and (np.diff(ptr) >= 0).all()
+        for i in range(mb["nbr"]):
+            assert ptr[i + 1] - ptr[i] == sum(1 for br, _ in want if br == i)
+            assert all(int(mb["blk_row"][k]) == i for k in range(ptr[i], ptr[i + 1]))
+
+
+@pytest.mark.parametrize("inner", [0, 1])
+@pytest.mark.parametrize("parts", [1, 2, 3, 7, 64, 100000])
+def test_mergeb_spmv_integer_equals_dense(orc, parts, inner):
+    """Integer data: every part count (down to one path item per part) gives D @ x exactly;
+    carries of block rows split over several parts are added back."""
+    rows, cols = synth.rmat(8, 8, seed=5)
+    m = n = 1 << 8
+    vals = synth.values(rows, cols, 5, integer=True)
+    rp, co, vo = oracle.coo_to_csr(m, n, rows, cols, vals, 0, orc)
+    x = synth.vector(n, 6, integer=True)
+    D = _dense(m, n, rp, co, vo)
+    for lb in [2, 4, 6]:
+        mb = oracle.csr_to_mergeb(m, n, rp, co, vo, lb, inner, orc)
+        np.testing.assert_array_equal(oracle.mergeb_spmv(m, mb, x, parts, orc), D @ x)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 40), (40, 1), (37, 53), (53, 37), (3, 300)])
+def test_mergeb_spmv_ragged_shapes(orc, shape):
+    """Non-square, partial last block row and column, a single row, pattern data."""
+    m, n = shape
+    rp, co, vo = _random_csr(m, n, 3 * max(m, n), 8, integer=True)
+    x = synth.vector(n, 9, integer=True)
+    D = _dense(m, n, rp, co, vo)
+    for lb in [1, 3, 5]:
+        for inner in (0, 1):
+            mb = oracle.csr_to_mergeb(m, n, rp, co, vo, lb, inner, orc)
+            for parts in (1, 4, 29):
+                np.testing.assert_array_equal(oracle.mergeb_spmv(m, mb, x, parts, orc), D @ x)
+            pat = dict(mb, val=None)
+            np.testing.assert_array_equal(oracle.mergeb_spmv(m, pat, x, 3, orc), _dense(m, n, rp, co, None) @ x)
+
+
+def test_mergeb_spmv_float_within_summation_order(orc):
+    rows, cols = synth.rmat(9, 8, seed=3)
+    m = n = 1 << 9
+    vals = synth.values(rows, cols, 3)
+    rp, co, vo = oracle.coo_to_csr(m, n, rows, cols, vals, 0, orc)
+    x = synth.vector(n, 4)
+    ref = oracle.csr_spmv(rp, co, vo, x, orc)
+    scale = oracle.csr_absmul(rp, co, vo, x, orc)
+    for inner in (0, 1):
+        mb = oracle.csr_to_mergeb(m, n, rp, co, vo, 5, inner, orc)
+        y = oracle.mergeb_spmv(m, mb, x, 13, orc)
+        assert (np.abs(y - ref) <= 1e-13 * scale).all()
+
+
+def test_planted_mergeb_carry_overwrite_fails_dense(orc):
+    """Writing a part's carry over y instead of adding it (a plausible slip in the fix-up)
+    breaks the dense product as soon as a block row is split between parts."""
+    rows, cols = synth.rmat(8, 8, seed=5)
+    m = n = 1 << 8
+    vals = synth.values(rows, cols, 5, integer=True)
+    rp, co, vo = oracle.coo_to_csr(m, n, rows, cols, vals, 0, orc)
+    x = synth.vector(n, 6, integer=True)
+    mb = oracle.csr_to_mergeb(m, n, rp, co, vo, 5, 1, orc)
+    beta, nbr, parts = 1 << mb["log2beta"], mb["nbr"], 7
+    # the same walk as the oracle, written here with the carry stored instead of added
+    ptr, bp, bc, idx, val = mb["blk_row_ptr"], mb["blk_ptr"], mb["blk_col"], mb["idx"], mb["val"]
+    total = nbr + mb["nblk"]
+    L = -(-total // parts)
+    y = np.zeros(m)
+    carries = []
+    for p in range(parts):
+        i, b = oracle.merge_path_search(min(p * L, total), ptr, orc)
+        i1, b1 = oracle.merge_path_search(min((p + 1) * L, total), ptr, orc)
+        temp = np.zeros(beta)
+        while i < i1 or b < b1:
+            if i < i1 and ptr[i + 1] <= b:
+                y[i * beta:min(m, (i + 1) * beta)] = temp[:min(m, (i + 1) * beta) - i * beta]
+                temp[:] = 0
+                i += 1
+            else:
+                for t in range(bp[b], bp[b + 1]):
+                    temp[int(idx[t]) >> 16] += val[t] * x[(int(bc[b]) << mb["log2beta"]) + (int(idx[t]) & 0xFFFF)]
+                b += 1
+        carries.append((i, temp.copy()))
+    for i, temp in carries:
+        if i < nbr:
+            y[i * beta:min(m, (i + 1) * beta)] = temp[:min(m, (i + 1) * beta) - i * beta]   # planted
+    D = _dense(m, n, rp, co, vo)
+    np.testing.assert_array_equal(oracle.mergeb_spmv(m, mb, x, parts, orc), D @ x)
+    assert not np.array_equal(y, D @ x)
