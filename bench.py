@@ -579,6 +579,66 @@ def iterative_leg(sp, torch, dev, synth, np):
     return out
 
 
+# ------------------------------------------------------------------ Merge Blocking leg
+
+def blocking_leg(sp, torch, dev, m, n, r_d, c_d, v_d, x_d, flush, reps=10):
+    """Merge Blocking (Section 4.3) on the step's workload, outside the timed step: the
+    conversion CSR -> MergeB (row-wise inside blocks) and CSR -> MergeBH (Hilbert inside
+    blocks) at beta = 2^14, each a full rebuild from the CRS arrays (median of 3), and each
+    product (L2 flushed before every call; median of `reps`), with its main kernel's device
+    time from the library's trace against the blocked format's compulsory bytes.  Returns the
+    figures and the two products' y for the oracle errors."""
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    h = sp.spmv_create_coo(m, n, r_d, c_d, v_d)
+    sp.spmv_convert(h, "rowsplit")
+    out, ys = {}, {}
+    conv = {"mergeb": [], "mergebh": []}
+    for _ in range(3):
+        for fmt in ("mergeb", "mergebh"):
+            torch.cuda.synchronize()
+            e0, e1 = ev(), ev()
+            e0.record()
+            sp.spmv_convert(h, fmt, log2_beta=14)
+            e1.record()
+            torch.cuda.synchronize()
+            conv[fmt].append(e0.elapsed_time(e1))
+    for fmt in ("mergeb", "mergebh"):
+        sp.spmv_convert(h, fmt, log2_beta=14)
+        info = sp.spmv_info(h)
+        nnz, nblk = info["nnz"], info["nblk"]
+        y = torch.empty(m, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            sp.spmv_mul(h, x_d, y)
+        torch.cuda.synchronize()
+        sp.spmv_trace_enable(True)
+        t = []
+        for _ in range(reps):
+            flush.fill_(1)
+            e0, e1 = ev(), ev()
+            e0.record()
+            sp.spmv_mul(h, x_d, y)
+            e1.record()
+            t.append((e0, e1))
+        torch.cuda.synchronize()
+        trace = sp.spmv_trace_read()
+        sp.spmv_trace_enable(False)
+        ms = statistics.median(a.elapsed_time(b) for a, b in t)
+        kb = nnz * 12 + nblk * 12 + n * 8 + m * 8
+        cnt, kms = trace.get("k_mergeb", (0, 0.0))
+        kdur = kms / cnt if cnt else None
+        out[fmt] = {"convert_ms": round(statistics.median(conv[fmt]), 3), "product_ms": round(ms, 4),
+                    "gbs": round(kb / (ms * 1e-3) / 1e9, 1), "gflops": round(2 * nnz / (ms * 1e-3) / 1e9, 1),
+                    "kernel_ms": None if kdur is None else round(kdur, 4),
+                    "kernel_gbs": None if kdur is None else round(kb / (kdur * 1e-3) / 1e9, 1),
+                    "compulsory_bytes": kb, "nblk": nblk, "block_rows": info["block_rows"],
+                    "warp_tiles": info["mergeb_tiles"]}
+        ys[fmt] = y
+    sp.spmv_destroy(h)
+    out["what"] = ("Merge Blocking at beta 2^14: merge path over (block-row ends, entries) in warp tiles of 256 "
+                   "items, run sums reduced into y; native FP64 accumulation")
+    return out, ys
+
+
 # ------------------------------------------------------------------ precision leg
 
 def precision_leg(sp, torch, dev, synth, np):
@@ -693,6 +753,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-iterative", action="store_true")
+    ap.add_argument("--no-blocking", action="store_true", help="skip the Merge Blocking leg")
     ap.add_argument("--batched-small", action="store_true", help="64 matrices, scales 10-18")
     args = ap.parse_args()
 
@@ -910,6 +971,15 @@ def main():
                     "h2d_bytes_per_step": nnz_in * 16 + 4 * n * 8, "d2h_bytes_per_step": 4 * m * 8}
         del hr, hc, hv, hys
 
+    # ---- Merge Blocking (Section 4.3) on the same workload, outside the timed step
+    blocking, ys_mb = (None, {}) if args.no_blocking else blocking_leg(sp, torch, dev, m, n, r_d, c_d, v_d, x_d,
+                                                                       flush)
+    if blocking:
+        for fmt in ("mergeb", "mergebh"):
+            kg = blocking[fmt]["kernel_gbs"]
+            blocking[fmt]["kernel_frac_of_peak"] = None if kg is None else round(kg / peak, 4)
+            blocking[fmt]["frac_of_peak"] = round(blocking[fmt]["gbs"] / peak, 4)
+
     # ---- errors of every product against the oracle, CPU baselines (rank 0)
     errors = None
     cpu = None
@@ -918,6 +988,9 @@ def main():
         errors = {st: rel_err(ys[st].cpu().numpy(), ref.y, ref.scale) for st in PRODUCTS}
         for st in PRODUCTS:
             rows_out[st]["max_err"] = errors[st]
+        for fmt, y in ys_mb.items():
+            errors[fmt] = rel_err(y.cpu().numpy(), ref.y, ref.scale)
+            blocking[fmt]["max_err"] = errors[fmt]
         if world == 1 and not args.no_cpu_baseline:
             cpu = cpu_baselines(ref)
         del ref
@@ -968,6 +1041,7 @@ def main():
         "kernel_shares": shares,
         "break_even": break_even,
         "errors_vs_oracle": errors,
+        "merge_blocking": blocking,
         "serving": serving,
         "batched": batched,
         "precision": precision,

@@ -54,12 +54,18 @@ typedef enum { SPMV_F64 = 0, SPMV_F32 = 1, SPMV_BF16 = 2, SPMV_PATTERN = 3 } spm
  *   HB            Hilbert-ordered blocked format (Sections 3.1, 4.2: BCOHC/BCOHCH
  *                 storage -- beta x beta blocks, packed 16+16-bit in-block indices,
  *                 nonzeros and blocks in Hilbert-curve order).
- *   AUTO          the library picks one from the matrix's row-length statistics.   */
+ *   AUTO          the library picks one from the matrix's row-length statistics.
+ *   MERGEB        Merge Blocking (Section 4.3): beta x beta blocks in row-major block
+ *                 order held as a CRS over the blocks, packed 16+16-bit in-block indices,
+ *                 entries row-wise inside a block (MergeB, inner_order =
+ *                 SPMV_INNER_ROWMAJOR) or along the block's Hilbert curve (MergeBH,
+ *                 SPMV_INNER_HILBERT); merge-path product over (block-row ends, entries). */
 typedef enum {
     SPMV_FMT_CSR_ROWSPLIT = 0,
     SPMV_FMT_CSR_MERGE = 1,
     SPMV_FMT_HB = 2,
-    SPMV_FMT_AUTO = 3
+    SPMV_FMT_AUTO = 3,
+    SPMV_FMT_MERGEB = 4
 } spmv_format;
 
 /* spmv_create_coo flags */
@@ -151,6 +157,17 @@ spmv_status spmv_create_coo(int64_t m, int64_t n, int64_t nnz, const int32_t *ro
  *   adds row sums into y with reductions (y is zeroed first; the order of the additions
  *   across runs is not fixed).  SPMV_HB_CHUNKED keeps the Hilbert-ordered product that
  *   gathers x per nonzero.
+ *   MERGEB: the blocked arrays in row-major block order (as HB with block_order =
+ *   SPMV_BLOCK_ROWMAJOR; log2_beta and inner_order as for HB, inner_order ROWMAJOR = MergeB,
+ *   HILBERT = MergeBH, ZMORTON accepted), the CRS pointer over the blocks and the merge-path
+ *   split point of every warp lane: the path of Section 3.3 over A = the block-row ends and
+ *   B = the entries of the blocks, cut into warp tiles of 256 items, 8 per lane.  With a
+ *   row-wise inner order the sort runs on the block key only (the CRS order already orders
+ *   a block's entries row-wise), the conversion the paper finds cheapest (Section 6.2).  The
+ *   product adds each lane's run sums of one row into y with reductions (y is zeroed first;
+ *   the order of the additions across runs is not fixed); FP64 vectors accumulate in FP64,
+ *   FP32 vectors in plain or compensated FP32.  The blocked arrays are shared with HB: a
+ *   later HB conversion with another block order rebuilds them (and drops the MERGEB tables).
  * opt may be NULL (defaults).  The CRS arrays are kept once built, so a later
  * conversion to another CSR algorithm or to HB reuses them.  The converted format
  * becomes the one spmv_mul uses.  Synchronises `stream` (status read-backs).  Errors:
@@ -198,7 +215,7 @@ spmv_status spmv_wait(spmv_handle h, void *stream);
  * copied per call.  Per column, the result is bitwise the one spmv_mul gives for the
  * same accumulation on the merge path (FP64 vectors accumulate in native FP64 here, so
  * SPMV_ACC_DEFAULT matches spmv_mul with SPMV_ACC_F64).  With k = 1, a handle whose active
- * format is row-split or blocked (spmv_convert, or chosen by spmv_tune) runs that format's
+ * format is row-split, HB or MERGEB (spmv_convert, or chosen by spmv_tune) runs that format's
  * product after the persistent launch instead, with spmv_mul's result.  Calls with the same batch shape share scratch
  * and must be ordered.  Not capturable into a caller's graph (the pointer table is
  * uploaded from pageable memory).  A handle's plans are dropped when it is converted
@@ -306,6 +323,8 @@ typedef struct {
     int32_t merge_tile_items;
     int32_t hb_orders;      /* 16 x block order + inner order of the blocked arrays      */
     int64_t device_bytes;   /* device memory held by the handle                          */
+    int64_t block_rows;     /* MERGEB: block rows nbr = ceil(m / beta) (0 if not built)  */
+    int64_t mergeb_tiles;   /* MERGEB: warp tiles of 256 path items                      */
 } spmv_info_t;
 
 spmv_status spmv_info(spmv_handle h, spmv_info_t *out);
@@ -329,6 +348,17 @@ spmv_status spmv_export_hb(spmv_handle h, uint32_t *idx, void *data, int32_t *bl
  * nz_start[t] nonzeros are consumed before the tile (tiles+1 entries each).
  */
 spmv_status spmv_export_merge_partition(spmv_handle h, int32_t *row_start, int32_t *nz_start);
+
+/*
+ * spmv_export_mergeb -- copy the MERGEB tables to host buffers: blk_row_ptr (block_rows + 1
+ * entries: the first block of every block row), and for every lane g = 0 .. 32 *
+ * mergeb_tiles - 1 of the warp tiles the merge-path split point of its first item (path
+ * diagonal 8 g, clamped to the path length): lane_entry[g] entries and, implicitly,
+ * 8 g - lane_entry[g] block-row ends consumed before it; lane_block[g] the block holding
+ * entry lane_entry[g] (nblk when every entry is consumed).  Sizes from spmv_info; any
+ * pointer may be NULL.  SPMV_ERR_NOT_CONVERTED if the tables are not built.
+ */
+spmv_status spmv_export_mergeb(spmv_handle h, int32_t *blk_row_ptr, int32_t *lane_entry, int32_t *lane_block);
 
 /* Text of the last error raised on the calling host thread ("" if none). */
 const char *spmv_last_error(void);

@@ -26,7 +26,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 SPMV_OK, SPMV_ERR_INVALID_ARG, SPMV_ERR_INDEX_RANGE, SPMV_ERR_DUPLICATE, SPMV_ERR_OOM, \
     SPMV_ERR_UNSUPPORTED, SPMV_ERR_CUDA, SPMV_ERR_TIMEOUT, SPMV_ERR_NOT_CONVERTED, SPMV_ERR_IO = range(10)
 SPMV_F64, SPMV_F32, SPMV_BF16, SPMV_PATTERN = range(4)
-SPMV_FMT_CSR_ROWSPLIT, SPMV_FMT_CSR_MERGE, SPMV_FMT_HB, SPMV_FMT_AUTO = range(4)
+SPMV_FMT_CSR_ROWSPLIT, SPMV_FMT_CSR_MERGE, SPMV_FMT_HB, SPMV_FMT_AUTO, SPMV_FMT_MERGEB = range(5)
 SPMV_DEVICE_PTRS = 0x1
 SPMV_DUP_SUM = 0x0
 SPMV_DUP_ERROR = 0x2
@@ -36,7 +36,8 @@ SPMV_HB_STAGED, SPMV_HB_CHUNKED = 0, 1
 SPMV_COMP_TAU_DEFAULT = 0   # include/spmv.h
 SPMV_ACC_DEFAULT, SPMV_ACC_F32, SPMV_ACC_F64, SPMV_ACC_COMPENSATED, SPMV_ACC_SEGMENT = range(5)
 
-FORMATS = {"rowsplit": SPMV_FMT_CSR_ROWSPLIT, "merge": SPMV_FMT_CSR_MERGE, "hb": SPMV_FMT_HB, "auto": SPMV_FMT_AUTO}
+FORMATS = {"rowsplit": SPMV_FMT_CSR_ROWSPLIT, "merge": SPMV_FMT_CSR_MERGE, "hb": SPMV_FMT_HB, "auto": SPMV_FMT_AUTO,
+           "mergeb": SPMV_FMT_MERGEB}
 ELEM_SIZE = {SPMV_F64: 8, SPMV_F32: 4, SPMV_BF16: 2, SPMV_PATTERN: 0}
 
 
@@ -49,7 +50,8 @@ class spmv_info_t(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("format", ctypes.c_int32),
                 ("dtype", ctypes.c_int32), ("log2_beta", ctypes.c_int32), ("grid_order", ctypes.c_int32),
                 ("nblk", ctypes.c_int64), ("merge_tiles", ctypes.c_int64), ("merge_tile_items", ctypes.c_int32),
-                ("hb_orders", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+                ("hb_orders", ctypes.c_int32), ("device_bytes", ctypes.c_int64), ("block_rows", ctypes.c_int64),
+                ("mergeb_tiles", ctypes.c_int64)]
 
 
 class spmv_tune_result(ctypes.Structure):
@@ -90,6 +92,7 @@ _SIG = {
     "spmv_export_csr": [_p, _p, _p, _p],
     "spmv_export_hb": [_p, _p, _p, _p, _p, _p],
     "spmv_export_merge_partition": [_p, _p, _p],
+    "spmv_export_mergeb": [_p, _p, _p, _p],
     "spmv_hilbert_keys": [_i32, _i64, _p, _p, _p, _p],
     "spmv_mul_csr_merge_noalloc": [_i64, _i64, _i64, _p, _p, _p, _p, _p, _p],
     "spmv_pagerank": [_p, ctypes.c_double, _i32, _p, _p],
@@ -209,7 +212,11 @@ def spmv_create_coo(m, n, row_ind, col_ind, data=None, dtype=None, flags=SPMV_DU
 def spmv_convert(h: Handle, fmt="merge", log2_beta=0, inner_order=SPMV_INNER_HILBERT, tile=0,
                  hb_product=SPMV_HB_STAGED, block_order=SPMV_BLOCK_HILBERT, stream=None):
     """Build a storage format (Section 5.1) and make it the active one ("csb": the blocked
-    format with row-major block order and Z-Morton inner order, Section 3.1)."""
+    format with row-major block order and Z-Morton inner order, Section 3.1; "mergeb" and
+    "mergebh": Merge Blocking with row-wise or Hilbert entries inside the blocks, Section 4.3)."""
+    if fmt in ("mergeb", "mergebh"):
+        inner_order = SPMV_INNER_ROWMAJOR if fmt == "mergeb" else SPMV_INNER_HILBERT
+        fmt = "mergeb"
     if fmt == "csb":
         fmt, block_order = "hb", SPMV_BLOCK_ROWMAJOR
         inner_order = SPMV_INNER_ZMORTON if inner_order == SPMV_INNER_HILBERT else inner_order
@@ -284,6 +291,20 @@ def spmv_export_merge_partition(h: Handle):
     ns = np.empty(tiles + 1, np.int32)
     _check(_lib.spmv_export_merge_partition(h.ptr, _addr(rs), _addr(ns)), "spmv_export_merge_partition")
     return rs, ns
+
+
+def spmv_export_mergeb(h: Handle) -> dict:
+    """Merge Blocking tables: the CRS pointer over blocks and every lane's split point (entry and
+    block at its first path item), plus the blocked arrays (spmv_export_hb)."""
+    inf = spmv_info(h)
+    nbr, tiles = inf["block_rows"], inf["mergeb_tiles"]
+    rp = np.empty(nbr + 1, np.int32)
+    le = np.empty(max(tiles * 32, 1), np.int32)
+    lb = np.empty(max(tiles * 32, 1), np.int32)
+    _check(_lib.spmv_export_mergeb(h.ptr, _addr(rp), _addr(le), _addr(lb)), "spmv_export_mergeb")
+    out = spmv_export_hb(h)
+    out.update({"blk_row_ptr": rp, "nbr": nbr, "lane_entry": le[:tiles * 32], "lane_block": lb[:tiles * 32]})
+    return out
 
 
 def spmv_hilbert_keys(K, rows, cols, keys, stream=None):

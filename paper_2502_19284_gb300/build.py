@@ -13,7 +13,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libspmv.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-UNITS = ["primitives", "convert", "spmv", "stage", "store", "cg", "pagerank", "batch", "serve", "api"]
+UNITS = ["primitives", "convert", "spmv", "stage", "mergeb", "store", "cg", "pagerank", "batch", "serve", "api"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -200,7 +200,7 @@ void release_slot(uint32_t *p) {
 void free_all(spmv_matrix *h) {
     void *ptrs[] = {h->coo_row, h->coo_col, h->coo_val, h->row_ptr, h->col, h->val, h->bin_rows,
                     h->part_row, h->part_nz, h->carry_row, h->carry_val, h->merge_desc, h->hb_idx, h->hb_val,
-                    h->blk_ptr, h->blk_row, h->blk_col, h->hb_chunk_blk, h->st_hdr, h->st_words, h->st_vals, h->st_slice_tile, h->st_lmeta, h->st_part, h->xsplit, h->xsplit_flag, h->slot_desc, h->slot_col, h->slot_val2, h->slot_val, h->fix_len, h->fix_long,
+                    h->blk_ptr, h->blk_row, h->blk_col, h->hb_chunk_blk, h->st_hdr, h->st_words, h->st_vals, h->st_slice_tile, h->st_lmeta, h->st_part, h->xsplit, h->xsplit_flag, h->slot_desc, h->slot_col, h->slot_val2, h->slot_val, h->fix_len, h->fix_long, h->mb_row_ptr, h->mb_desc,
                     h->pr_inv, h->pr_z, h->pr_z2, h->pr_y, h->pr_part, h->status_dev};
     if (h->pr_graph) cudaGraphExecDestroy((cudaGraphExec_t)h->pr_graph);
     for (void *p : ptrs) dev_free(p);
@@ -381,7 +381,7 @@ spmv_status spmv_convert(spmv_handle h, spmv_format f, const spmv_convert_opts *
         if (!h->has_bins) SPMV_TRY(build_bins(h, s));
         f = (h->max_row_len > 4096 || h->nnz > ((int64_t)1 << 20)) ? SPMV_FMT_CSR_MERGE : SPMV_FMT_CSR_ROWSPLIT;
     }
-    if ((int)f < 0 || (int)f > 2) {
+    if ((int)f < 0 || ((int)f > 2 && f != SPMV_FMT_MERGEB)) {
         set_error("spmv_convert: unknown format");
         return SPMV_ERR_INVALID_ARG;
     }
@@ -419,6 +419,14 @@ spmv_status spmv_convert(spmv_handle h, spmv_format f, const spmv_convert_opts *
         if (o.hb_product == SPMV_HB_STAGED && (!h->has_stage || h->stage_lb != lb)) SPMV_TRY(build_stage(h, lb, s));
         h->hb_chunked = o.hb_product == SPMV_HB_CHUNKED;
     }
+    if (f == SPMV_FMT_MERGEB) {
+        int lb = o.log2_beta ? o.log2_beta : default_log2_beta(h->n, h->dt == SPMV_F64 ? 8 : 4);
+        const int K = bits_for(std::max<int64_t>(std::max(h->m, h->n), 2));
+        if (lb > K) lb = K;
+        if (!h->has_hb || h->log2beta != lb || h->inner != o.inner_order || h->block_order != SPMV_BLOCK_ROWMAJOR)
+            SPMV_TRY(build_hb(h, lb, o.inner_order, s, SPMV_BLOCK_ROWMAJOR));
+        if (!h->has_mergeb) SPMV_TRY(build_mergeb(h, s));
+    }
     SPMV_CUDA_TRY(cudaStreamSynchronize(s));
     h->format = (int32_t)f;
     return SPMV_OK;
@@ -444,6 +452,7 @@ spmv_status spmv_mul(spmv_handle h, const void *x, void *y, spmv_dtype vec_dt, u
         case SPMV_FMT_CSR_MERGE: return mul_merge(h, x, y, vec_dt, accum, s);
         case SPMV_FMT_CSR_ROWSPLIT: return mul_rowsplit(h, x, y, vec_dt, accum, s);
         case SPMV_FMT_HB: return mul_hb(h, x, y, vec_dt, accum, s);
+        case SPMV_FMT_MERGEB: return mul_mergeb(h, x, y, vec_dt, accum, s);
     }
     set_error("spmv_mul: bad format");
     return SPMV_ERR_INVALID_ARG;
@@ -576,7 +585,8 @@ spmv_status spmv_mul_batch(int count, const spmv_handle *hs, int k, const void *
         std::vector<void *> my;
         std::vector<int> own;
         for (int i = 0; i < count; ++i) {
-            if (hs[i]->format == SPMV_FMT_CSR_ROWSPLIT || hs[i]->format == SPMV_FMT_HB) {
+            if (hs[i]->format == SPMV_FMT_CSR_ROWSPLIT || hs[i]->format == SPMV_FMT_HB ||
+                hs[i]->format == SPMV_FMT_MERGEB) {
                 own.push_back(i);
             } else {
                 mh.push_back(hs[i]);
@@ -590,6 +600,7 @@ spmv_status spmv_mul_batch(int count, const spmv_handle *hs, int k, const void *
             for (int i : own) {
                 if (hs[i]->m == 0) continue;
                 if (hs[i]->format == SPMV_FMT_HB) SPMV_TRY(mul_hb(hs[i], X[i], Y[i], vec_dt, accum, s));
+                else if (hs[i]->format == SPMV_FMT_MERGEB) SPMV_TRY(mul_mergeb(hs[i], X[i], Y[i], vec_dt, accum, s));
                 else SPMV_TRY(mul_rowsplit(hs[i], X[i], Y[i], vec_dt, accum, s));
             }
             return SPMV_OK;
@@ -635,6 +646,8 @@ spmv_status spmv_info(spmv_handle h, spmv_info_t *out) {
     out->merge_tile_items = h->tile_items;
     out->hb_orders = h->has_hb ? 16 * h->block_order + h->inner : 0;
     out->device_bytes = h->bytes;
+    out->block_rows = h->mb_nbr;
+    out->mergeb_tiles = h->mb_tiles;
     return SPMV_OK;
 }
 
@@ -666,6 +679,26 @@ spmv_status spmv_export_hb(spmv_handle h, uint32_t *idx, void *data, int32_t *bl
     if (blk_ptr) SPMV_CUDA_TRY(cudaMemcpy(blk_ptr, h->blk_ptr, (size_t)(h->nblk + 1) * 4, cudaMemcpyDeviceToHost));
     if (blk_row && h->nblk) SPMV_CUDA_TRY(cudaMemcpy(blk_row, h->blk_row, (size_t)h->nblk * 4, cudaMemcpyDeviceToHost));
     if (blk_col && h->nblk) SPMV_CUDA_TRY(cudaMemcpy(blk_col, h->blk_col, (size_t)h->nblk * 4, cudaMemcpyDeviceToHost));
+    return SPMV_OK;
+}
+
+spmv_status spmv_export_mergeb(spmv_handle h, int32_t *blk_row_ptr, int32_t *lane_entry, int32_t *lane_block) {
+    SPMV_TRY(check_handle(h));
+    if (!h->has_mergeb) {
+        set_error("spmv_export_mergeb: no Merge Blocking tables (convert to MERGEB first)");
+        return SPMV_ERR_NOT_CONVERTED;
+    }
+    SPMV_CUDA_TRY(cudaDeviceSynchronize());
+    if (blk_row_ptr)
+        SPMV_CUDA_TRY(cudaMemcpy(blk_row_ptr, h->mb_row_ptr, (size_t)(h->mb_nbr + 1) * 4, cudaMemcpyDeviceToHost));
+    if ((lane_entry || lane_block) && h->mb_tiles > 0) {
+        std::vector<int2> d((size_t)h->mb_tiles * 32);
+        SPMV_CUDA_TRY(cudaMemcpy(d.data(), h->mb_desc, d.size() * sizeof(int2), cudaMemcpyDeviceToHost));
+        for (size_t g = 0; g < d.size(); ++g) {
+            if (lane_entry) lane_entry[g] = d[g].x;
+            if (lane_block) lane_block[g] = d[g].y;
+        }
+    }
     return SPMV_OK;
 }
 

@@ -224,6 +224,14 @@ struct spmv_matrix {
     int32_t stage_parts = 0;
     bool hb_chunked = false;          // the HB product walks the Hilbert-ordered chunks instead
 
+    // Merge Blocking (mergeb.cu), over the blocked arrays in row-major block order: the CRS
+    // pointer over the blocks (first block of every block row) and the merge-path split point
+    // (entry, block) of every lane's first item of the warp tiles
+    bool has_mergeb = false;
+    int32_t *mb_row_ptr = nullptr;
+    int2 *mb_desc = nullptr;
+    int64_t mb_nbr = 0, mb_tiles = 0;
+
     // FP64 through double-float arithmetic (df64.cuh): set when every stored value lies in
     // the double-float window; x is split into float pairs per product (scratch below)
     bool df_checked = false, df_ok = false;

@@ -1086,8 +1086,12 @@ spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s, int b
         }
         bool alt = false;
         SPMV_TRY(sort_begin(h, s));
+        // A row-wise inner order is the CRS order restricted to a block, and the keys are made in
+        // CRS order: a stable sort on the block key alone (bits 2 lb and up) yields the same order
+        // as a sort on the whole key.
+        const int begin_bit = inner == SPMV_INNER_ROWMAJOR ? 2 * log2b : 0;
         SPMV_TRY(radix_sort_pairs(keys.as<uint64_t>(), keys_alt.as<uint64_t>(), perm.as<uint32_t>(),
-                                  perm_alt.as<uint32_t>(), nnz, 0, 2 * K, tmp.p, s, &alt, h->status_dev + 1));
+                                  perm_alt.as<uint32_t>(), nnz, begin_bit, 2 * K, tmp.p, s, &alt, h->status_dev + 1));
         uint64_t *Ks = alt ? keys_alt.as<uint64_t>() : keys.as<uint64_t>();
         uint32_t *Ps = alt ? perm_alt.as<uint32_t>() : perm.as<uint32_t>();
         if (fast)
@@ -1131,6 +1135,7 @@ spmv_status build_hb(spmv_matrix *h, int log2b, int inner, cudaStream_t s, int b
                                                                                      nchunks, chk.as<int32_t>())));
         SPMV_LAUNCH_CHECK("hb chunks");
     }
+    free_mergeb(h, s);   // its tables index the blocked arrays being replaced
     if (h->has_hb) {
         dev_free_async(h->hb_idx, s); dev_free_async(h->hb_val, s); dev_free_async(h->blk_ptr, s);
         dev_free_async(h->blk_row, s); dev_free_async(h->blk_col, s); dev_free_async(h->hb_chunk_blk, s);

@@ -65,6 +65,11 @@ spmv_status stage_resplit(spmv_matrix *h, cudaStream_t s);
 spmv_status hb_chunk_table(spmv_matrix *h, cudaStream_t s);
 void free_stage(spmv_matrix *h, cudaStream_t s);
 spmv_status mul_stage(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s);
+// Merge Blocking (mergeb.cu): block-row pointer and lane split points over the blocked arrays
+// (which must be in row-major block order); free_mergeb releases them in stream order.
+spmv_status build_mergeb(spmv_matrix *h, cudaStream_t s);
+void free_mergeb(spmv_matrix *h, cudaStream_t s);
+spmv_status mul_mergeb(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s);
 // x -> float pairs in h->xsplit, with the window flag h->xsplit_flag reset and set (spmv.cu).
 spmv_status split_x(const spmv_matrix *h, const double *x, cudaStream_t s);
 // Bounded-wait check: one warp waits `polls` polls on an mbarrier nothing arrives at and sets

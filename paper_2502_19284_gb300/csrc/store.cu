@@ -3,7 +3,7 @@
 // when built, the Hilbert-ordered blocked arrays and the staged blocked layout; spmv_load
 // restores them into a new handle whose conversions to those formats then cost only the cheap
 // derived tables (merge partition, row bins, the HB chunk table, the CTA split of the staged
-// layout for the loading device).
+// layout for the loading device, the Merge Blocking block-row pointer and lane split points).
 //
 // File layout (host byte order; every array as stored on the device, without padding):
 //   8-byte magic "SPMVGB01", uint32 version, uint32 section flags (1 CRS, 2 HB, 4 staged),
@@ -181,7 +181,7 @@ spmv_status spmv_load(const char *path, void *stream, spmv_handle *out) {
               rd(f, dt) && rd(f, fmt) && rd(f, hbc) && rd(f, reserved);
     if (!ok || memcmp(magic, MAGIC, 8) != 0 || version != VERSION || !(sections & 1u) || m < 0 || n < 0 || nnz < 0 ||
         m >= ((int64_t)1 << 31) || n >= ((int64_t)1 << 31) || nnz >= ((int64_t)1 << 31) || dt < 0 || dt > 3 ||
-        fmt < -1 || fmt > 2) {
+        fmt < -1 || (fmt > 2 && fmt != SPMV_FMT_MERGEB)) {
         set_error(std::string("spmv_load: not a matrix file of this library (or a damaged header): ") + path);
         return SPMV_ERR_INVALID_ARG;
     }
