@@ -209,17 +209,21 @@ def spmv_create_coo(m, n, row_ind, col_ind, data=None, dtype=None, flags=SPMV_DU
     return Handle(out.value)
 
 
-def spmv_convert(h: Handle, fmt="merge", log2_beta=0, inner_order=SPMV_INNER_HILBERT, tile=0,
+_INNER_DEFAULT = {"csb": SPMV_INNER_ZMORTON, "mergeb": SPMV_INNER_ROWMAJOR, "mergebh": SPMV_INNER_HILBERT}
+
+
+def spmv_convert(h: Handle, fmt="merge", log2_beta=0, inner_order=None, tile=0,
                  hb_product=SPMV_HB_STAGED, block_order=SPMV_BLOCK_HILBERT, stream=None):
     """Build a storage format (Section 5.1) and make it the active one ("csb": the blocked
     format with row-major block order and Z-Morton inner order, Section 3.1; "mergeb" and
-    "mergebh": Merge Blocking with row-wise or Hilbert entries inside the blocks, Section 4.3)."""
-    if fmt in ("mergeb", "mergebh"):
-        inner_order = SPMV_INNER_ROWMAJOR if fmt == "mergeb" else SPMV_INNER_HILBERT
+    "mergebh": Merge Blocking with row-wise or Hilbert entries inside the blocks, Section 4.3).
+    inner_order None: the format's own inner order (Hilbert for "hb")."""
+    if inner_order is None:
+        inner_order = _INNER_DEFAULT.get(fmt, SPMV_INNER_HILBERT) if isinstance(fmt, str) else SPMV_INNER_HILBERT
+    if fmt == "mergebh":
         fmt = "mergeb"
     if fmt == "csb":
         fmt, block_order = "hb", SPMV_BLOCK_ROWMAJOR
-        inner_order = SPMV_INNER_ZMORTON if inner_order == SPMV_INNER_HILBERT else inner_order
     f = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
     opts = spmv_convert_opts(log2_beta, inner_order, tile, hb_product, block_order)
     _check(_lib.spmv_convert(h.ptr, f, ctypes.byref(opts), _stream(stream)), "spmv_convert")
