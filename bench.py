@@ -264,7 +264,7 @@ def cpu_baselines(ref, reps_oracle=3, reps_par=10):
 
 SERVE = dict(n_matrices=64, scales=(14, 24), edge_factor=16, budget=150 << 30, slots=8, max_batch=64,
              rates=(1000.0, 5000.0, 10000.0, 20000.0, 50000.0), requests=2000, pagerank_frac=0.2, pagerank_iters=20,
-             damping=0.85, check_scale=18)
+             damping=0.85, check_scale=18, staged_pagerank_scale=22)
 
 
 def serving_leg(sp, torch, dev, synth, np):
@@ -272,7 +272,10 @@ def serving_leg(sp, torch, dev, synth, np):
     on a resident set of R-MAT matrices, through the serving loop, against the same trace on
     the plain one-at-a-time FP64 path (FP64 copies of the matrices, one synchronous call per
     request in arrival order).  Latency = completion - arrival.  Edges are drawn on the GPU
-    (synth's twin of the host generator), duplicates summed at ingestion."""
+    (synth's twin of the host generator), duplicates summed at ingestion.  Served matrices of
+    scale 22 and up are also converted to the staged blocked layout (beta 2^14, active format
+    HB): their PageRank requests run on the staged product, their SpMV requests on the batched
+    merge path like the others."""
     cfg = SERVE
     rng = np.random.Generator(np.random.PCG64(77))
     scales = rng.integers(cfg["scales"][0], cfg["scales"][1] + 1, size=cfg["n_matrices"])
@@ -284,6 +287,8 @@ def serving_leg(sp, torch, dev, synth, np):
         rd, cd = synth.gpu_rmat_raw(int(sc), cfg["edge_factor"], seed=1000 + i, device=dev)
         a = sp.spmv_create_coo(n, n, rd, cd, synth.gpu_values(rd, cd, seed=1000 + i, f32=True))
         sp.spmv_convert(a, "merge")
+        if sc >= cfg["staged_pagerank_scale"]:   # PageRank on the staged blocked product
+            sp.spmv_convert(a, "hb", log2_beta=14)
         b = sp.spmv_create_coo(n, n, rd, cd, synth.gpu_values(rd, cd, seed=1000 + i))
         sp.spmv_convert(b, "auto")
         del rd, cd
@@ -309,6 +314,8 @@ def serving_leg(sp, torch, dev, synth, np):
                       "mix": f"{1 - cfg['pagerank_frac']:.0%} SpMV / {cfg['pagerank_frac']:.0%} PageRank-"
                              f"{cfg['pagerank_iters']}", "budget_bytes": cfg["budget"], "slots": cfg["slots"],
                       "max_batch": cfg["max_batch"], "requests_per_rate": cfg["requests"],
+                      "pagerank_product": (f"staged blocked (HB, beta 2^14) for scales >= {cfg['staged_pagerank_scale']}, "
+                                           "merge path below"),
                       "resident_bytes": srv.stats()["resident_bytes"]},
            "rates": []}
     # accuracy of a served FP32 product against the oracle (the matrix of scale closest to

@@ -383,9 +383,14 @@ spmv_status spmv_hilbert_keys(int K, int64_t n, const int32_t *rows, const int32
  *   damping     in [0, 1] (0.85 is customary);  iters: number of iterations, 0..10000.
  *   x           device array of n doubles; receives the final vector (it is also the
  *               working vector of the iteration).
- * Builds the CRS arrays and the merge-path partition if needed.  The iterations are
- * captured into a CUDA graph on the first call for a given (x, iters, damping) and the
- * graph is replayed on `stream` (asynchronously) by this and later calls.
+ * Builds the CRS arrays and the merge-path partition if needed.  The product of every
+ * iteration is the pattern merge-path product, or, when the handle's active format is HB
+ * with the staged product, the staged blocked pattern product (x read in slices, which pays
+ * once x no longer fits in L2; its summation order is not fixed, so its results agree within
+ * FP64 rounding but are not bitwise reproducible).  The iterations are captured into a CUDA
+ * graph on the first call for a given (x, iters, damping, product) and the graph is replayed
+ * on `stream` (asynchronously) by this and later calls; a conversion that replaces the staged
+ * layout drops the graph.
  */
 spmv_status spmv_pagerank(spmv_handle h, double damping, int iters, double *x, void *stream);
 
@@ -403,7 +408,8 @@ spmv_status spmv_pagerank(spmv_handle h, double damping, int iters, double *x, v
  * memory free up.  Every SpMV result is bitwise the spmv_mul result with the same
  * accumulation on the merge path (FP64 vectors accumulate in native FP64, as with
  * SPMV_ACC_F64), and every PageRank result the spmv_pagerank result, whatever else is in
- * flight.
+ * flight (bitwise for matrices whose active format is not HB; HB matrices run PageRank on the
+ * staged product, whose summation order is not fixed).
  *
  * Memory: the budget covers the resident matrices (their spmv_info bytes at spmv_server_add,
  * plus the PageRank scratch of a matrix from its first PageRank request on) and, per admitted

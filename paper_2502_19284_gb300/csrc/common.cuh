@@ -245,6 +245,7 @@ struct spmv_matrix {
     const double *pr_graph_x = nullptr;
     int pr_graph_iters = 0;
     double pr_graph_damping = 0.0;
+    bool pr_graph_staged = false;     // the graph runs the staged blocked product
 
     uint32_t *status_dev = nullptr;   // device status word
     uint32_t *status_host = nullptr;  // pinned read-back slot

@@ -80,6 +80,12 @@ spmv_status test_wait(long long polls, uint32_t *status, cudaStream_t s);
 spmv_status mul_merge_pattern_split(const spmv_matrix *h, const double *x, const float2 *x2, const uint32_t *xflag,
                                     double *y, cudaStream_t s);
 spmv_status pagerank(spmv_matrix *h, double damping, int iters, double *x, cudaStream_t s);
+// Drop the captured PageRank graph (its kernels hold pointers into tables being replaced).
+void pagerank_forget(spmv_matrix *h);
+// Pattern product (values taken as 1) y = A x through the staged blocked layout, with x split
+// into float pairs in x2 (*xflag non-zero: native FP64 on x); y is zeroed first (stage.cu).
+spmv_status mul_stage_pattern_split(const spmv_matrix *h, const double *x, const float2 *x2, const uint32_t *xflag,
+                                    double *y, cudaStream_t s);
 spmv_status mul_csr_merge_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col,
                                   const double *data, const double *x, double *y, cudaStream_t s);
 // Batched multi-RHS merge-path products (batch.cu); plans that name a handle are dropped

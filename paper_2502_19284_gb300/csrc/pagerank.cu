@@ -3,7 +3,10 @@
 //   out-degree of column j = number of stored entries in column j (values ignored),
 //   x0 = 1/n, and per iteration, with dangling = sum of x_j over columns of out-degree 0,
 //   x_i <- d * ( (A z)_i + dangling / n ) + (1 - d) / n,   z_j = x_j / outdeg_j (0 if dangling).
-// Each iteration is three fused kernels around the pattern merge-path product:
+// Each iteration is three fused kernels around the pattern product -- the merge-path product,
+// or, when the handle's active format is HB with the staged product, the staged blocked
+// product (x slices read once per CTA by bulk copies instead of gathered per nonzero, which
+// matters once the split x no longer fits in L2; its summation order is not fixed):
 //   prep    z = x * (1/outdeg), split into float pairs for the double-float product, and
 //           per-block partial sums of the dangling mass (fixed order: deterministic);
 //   dsum    one block adds the partials in a fixed tree order;
@@ -111,7 +114,12 @@ spmv_status pr_buffers(spmv_matrix *h, cudaStream_t s) {
     return SPMV_OK;
 }
 
+bool pr_staged(const spmv_matrix *h) {
+    return h->format == SPMV_FMT_HB && h->has_stage && !h->hb_chunked && h->stage_tiles > 0;
+}
+
 spmv_status pr_enqueue(spmv_matrix *h, double damping, int iters, double *x, cudaStream_t s) {
+    const bool staged = pr_staged(h);
     const int64_t n = h->n;
     double *total = h->pr_part + PR_PARTS;
     uint32_t *flag = (uint32_t *)(h->pr_part + PR_PARTS + 1);
@@ -124,7 +132,8 @@ spmv_status pr_enqueue(spmv_matrix *h, double damping, int iters, double *x, cud
         SPMV_LAUNCH_CHECK("pagerank prep");
         SPMV_LAUNCH("k_pr_dsum", s, (k_pr_dsum<<<1, PR_PARTS, 0, s>>>(h->pr_part, total)));
         SPMV_LAUNCH_CHECK("pagerank dangling sum");
-        SPMV_TRY(mul_merge_pattern_split(h, h->pr_z, h->pr_z2, flag, h->pr_y, s));
+        if (staged) SPMV_TRY(mul_stage_pattern_split(h, h->pr_z, h->pr_z2, flag, h->pr_y, s));
+        else SPMV_TRY(mul_merge_pattern_split(h, h->pr_z, h->pr_z2, flag, h->pr_y, s));
         SPMV_LAUNCH("k_pr_update", s, (k_pr_update<<<blocks_for(n), 256, 0, s>>>(h->pr_y, total, damping, n, x)));
         SPMV_LAUNCH_CHECK("pagerank update");
     }
@@ -135,8 +144,9 @@ spmv_status pr_enqueue(spmv_matrix *h, double damping, int iters, double *x, cud
 
 spmv_status pagerank(spmv_matrix *h, double damping, int iters, double *x, cudaStream_t s) {
     SPMV_TRY(pr_buffers(h, s));
-    // one graph per (x, iterations, damping); re-captured when any of them changes
-    if (!h->pr_graph || h->pr_graph_x != x || h->pr_graph_iters != iters || h->pr_graph_damping != damping) {
+    // one graph per (x, iterations, damping, product); re-captured when any of them changes
+    if (!h->pr_graph || h->pr_graph_x != x || h->pr_graph_iters != iters || h->pr_graph_damping != damping ||
+        h->pr_graph_staged != pr_staged(h)) {
         if (h->pr_graph) {
             cudaGraphExecDestroy((cudaGraphExec_t)h->pr_graph);
             h->pr_graph = nullptr;
@@ -160,9 +170,16 @@ spmv_status pagerank(spmv_matrix *h, double damping, int iters, double *x, cudaS
         h->pr_graph_x = x;
         h->pr_graph_iters = iters;
         h->pr_graph_damping = damping;
+        h->pr_graph_staged = pr_staged(h);
     }
     SPMV_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)h->pr_graph, s));
     return SPMV_OK;
+}
+
+void pagerank_forget(spmv_matrix *h) {
+    if (!h->pr_graph) return;
+    cudaGraphExecDestroy((cudaGraphExec_t)h->pr_graph);
+    h->pr_graph = nullptr;
 }
 
 }  // namespace spmv

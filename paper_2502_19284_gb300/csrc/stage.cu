@@ -797,8 +797,25 @@ spmv_status st_mul_f32_acc(const spmv_matrix *h, const float *x, float *y, uint3
 
 }  // namespace
 
+spmv_status mul_stage_pattern_split(const spmv_matrix *h, const double *x, const float2 *x2, const uint32_t *xflag,
+                                    double *y, cudaStream_t s) {
+    SPMV_CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)h->m * 8, s));
+    if (!h->has_stage || h->stage_tiles == 0) return SPMV_OK;
+    bool stage_ok = false;
+    StArgs<Pattern, double> a = st_args<Pattern, double>(h, 8, x, y, &stage_ok);
+    constexpr size_t slots = st_slots_bytes<DfAcc>();
+    const size_t smem = slots + (stage_ok ? ((size_t)1 << h->stage_lb) * 8 : 0);
+    static DeviceOnce attr;
+    SPMV_TRY(attr([&] { return set_smem((const void *)k_hb_stage_f64<Pattern>, slots + ST_X_MAX); }));
+    SPMV_LAUNCH("k_hb_stage", s, (k_hb_stage_f64<Pattern><<<(unsigned)h->stage_parts, ST_NW * 32, smem, s>>>(
+                                      a, x, x2, xflag, 0)));
+    SPMV_LAUNCH_CHECK("staged blocked pattern spmv");
+    return SPMV_OK;
+}
+
 void free_stage(spmv_matrix *h, cudaStream_t s) {
     if (!h->has_stage) return;
+    pagerank_forget(h);   // a captured PageRank graph may point into the layout
     dev_free_async(h->st_hdr, s);
     dev_free_async(h->st_words, s);
     dev_free_async(h->st_vals, s);
@@ -934,6 +951,7 @@ spmv_status build_stage(spmv_matrix *h, int lb, cudaStream_t s) {
 
 spmv_status stage_resplit(spmv_matrix *h, cudaStream_t s) {
     if (!h->has_stage || h->stage_tiles == 0) return SPMV_OK;
+    pagerank_forget(h);   // the split array is replaced
     DevBuf part(s);
     int G = 0;
     SPMV_TRY(st_split(h->st_hdr, h->stage_tiles, &part, &G, s));

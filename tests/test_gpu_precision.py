@@ -152,6 +152,38 @@ def test_pagerank_matches_oracle(sp, scale):
         np.testing.assert_allclose(x2.cpu().numpy(), oracle.pagerank(rp, co, 0.5, 3), rtol=1e-11, atol=1e-16)
 
 
+@pytest.mark.parametrize("scale", [12, 17])
+def test_pagerank_staged_product_matches_oracle(sp, scale):
+    """A handle whose active format is HB (staged product) runs PageRank on the staged blocked
+    pattern product: within FP64 rounding of the oracle; a re-conversion that rebuilds the
+    staged layout (another block side) drops the captured graph and the result still holds; a
+    conversion to the merge path switches back to the bitwise-reproducible product."""
+    n = 1 << scale
+    rows, cols = synth.rmat(scale, 16, seed=91)
+    rp, co, _ = oracle.coo_to_csr(n, n, rows, cols, None)
+    ref = oracle.pagerank(rp, co, 0.85, 20)
+    vals = synth.values(rows, cols, 92)
+    h = sp.spmv_create_coo(n, n, torch.from_numpy(rows).to(DEV), torch.from_numpy(cols).to(DEV),
+                           torch.from_numpy(vals).to(DEV))
+    x = torch.full((n,), float("nan"), dtype=torch.float64, device=DEV)
+    for lb in (0, 9, 6):
+        sp.spmv_convert(h, "hb", log2_beta=lb)
+        sp.spmv_pagerank(h, x, 0.85, 20)
+        torch.cuda.synchronize()
+        a = x.cpu().numpy()
+        np.testing.assert_allclose(a, ref, rtol=1e-11, atol=1e-16)
+        assert abs(a.sum() - 1.0) < 1e-12
+    sp.spmv_convert(h, "merge")
+    sp.spmv_pagerank(h, x, 0.85, 20)
+    torch.cuda.synchronize()
+    b = x.cpu().numpy()
+    np.testing.assert_allclose(b, ref, rtol=1e-11, atol=1e-16)
+    sp.spmv_pagerank(h, x, 0.85, 20)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(x.cpu().numpy(), b)
+    sp.spmv_destroy(h)
+
+
 def test_compensation_threshold_sweep(sp):
     """Row-split SPMV_ACC_SEGMENT with tau: rows longer than tau (by length class) follow the
     compensated bound, the rest the FP32 bound; tau = 0 equals SPMV_ACC_COMPENSATED bit for
