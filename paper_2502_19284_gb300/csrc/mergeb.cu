@@ -35,6 +35,10 @@ namespace {
 constexpr int MB_IPT = 8;                        // path items per lane
 constexpr int MB_ITEMS = 32 * MB_IPT;            // path items per warp tile
 constexpr int MB_WARPS = 8;                      // warps (tiles) per CTA
+#ifndef MB_MINB_CFG
+#define MB_MINB_CFG 4
+#endif
+constexpr int MB_MINB = MB_MINB_CFG;             // resident CTAs per SM the registers are sized for
 constexpr int MB_PAD = MB_ITEMS + MB_ITEMS / 8;  // staging slots: one spare slot per 8
 constexpr int CB = 256;
 
@@ -98,7 +102,7 @@ __device__ __forceinline__ void mb_red(YT *p, const Acc &a) {
 
 // One warp tile per warp.  VT: stored value type (Pattern: none); XT/YT: vector types.
 template <typename Acc, typename VT, typename XT, typename YT>
-__global__ __launch_bounds__(MB_WARPS * 32) void k_mergeb(const int2 *__restrict__ desc,
+__global__ __launch_bounds__(MB_WARPS * 32, MB_MINB) void k_mergeb(const int2 *__restrict__ desc,
                                                           const int32_t *__restrict__ blk_ptr,
                                                           const int32_t *__restrict__ blk_row,
                                                           const int32_t *__restrict__ blk_col,
@@ -135,7 +139,7 @@ __global__ __launch_bounds__(MB_WARPS * 32) void k_mergeb(const int2 *__restrict
         rbase = (int64_t)blk_row[b] << lb;
         cbase = (int64_t)blk_col[b] << lb;
     }
-    int64_t row[MB_IPT];
+    int32_t row[MB_IPT];   // -1: no entry (rows < 2^31)
     Op av[MB_IPT], xv[MB_IPT];
 #pragma unroll
     for (int k = 0; k < MB_IPT; ++k) {
@@ -153,7 +157,7 @@ __global__ __launch_bounds__(MB_WARPS * 32) void k_mergeb(const int2 *__restrict
             const uint32_t w = s_w[warp][ps];
             const int64_t r = rbase + (w >> 16), c = cbase + (w & 0xFFFFu);
             if (r < m && c < n) {
-                row[k] = r;
+                row[k] = (int32_t)r;
                 xv[k] = ld_x<XT, Op>(x, c);
                 if constexpr (PAT) av[k] = Op(1);
                 else av[k] = sval<VT, Op>(s_v[warp], ps);
@@ -164,7 +168,7 @@ __global__ __launch_bounds__(MB_WARPS * 32) void k_mergeb(const int2 *__restrict
     }
     Acc acc;
     acc.zero();
-    int64_t cur = -1;
+    int32_t cur = -1;
 #pragma unroll
     for (int k = 0; k < MB_IPT; ++k) {
         if (row[k] < 0) continue;
