@@ -588,7 +588,7 @@ def iterative_leg(sp, torch, dev, synth, np):
 
 # ------------------------------------------------------------------ Merge Blocking leg
 
-def blocking_leg(sp, torch, dev, m, n, r_d, c_d, v_d, x_d, flush, reps=10):
+def blocking_leg(sp, torch, dev, m, n, r_d, c_d, v_d, x_d, flush, traffic_db, reps=10):
     """Merge Blocking (Section 4.3) on the step's workload, outside the timed step: the
     conversion CSR -> MergeB (row-wise inside blocks) and CSR -> MergeBH (Hilbert inside
     blocks) at beta = 2^14, each a full rebuild from the CRS arrays (median of 3), and each
@@ -633,7 +633,12 @@ def blocking_leg(sp, torch, dev, m, n, r_d, c_d, v_d, x_d, flush, reps=10):
         kb = nnz * 12 + nblk * 12 + n * 8 + m * 8
         cnt, kms = trace.get("k_mergeb", (0, 0.0))
         kdur = kms / cnt if cnt else None
+        t = traffic_db.get("k_mergeb")
+        traffic = None
+        if fmt == "mergeb" and t and t.get("source_sha") == source_sha(t.get("source"), t.get("from"), t.get("to")):
+            traffic = int(t["bytes_per_unit"] * nnz)   # ncu DRAM bytes (scale 21, MergeB) scaled to one launch
         out[fmt] = {"convert_ms": round(statistics.median(conv[fmt]), 3), "product_ms": round(ms, 4),
+                    "kernel_traffic": traffic,
                     "gbs": round(kb / (ms * 1e-3) / 1e9, 1), "gflops": round(2 * nnz / (ms * 1e-3) / 1e9, 1),
                     "kernel_ms": None if kdur is None else round(kdur, 4),
                     "kernel_gbs": None if kdur is None else round(kb / (kdur * 1e-3) / 1e9, 1),
@@ -980,7 +985,7 @@ def main():
 
     # ---- Merge Blocking (Section 4.3) on the same workload, outside the timed step
     blocking, ys_mb = (None, {}) if args.no_blocking else blocking_leg(sp, torch, dev, m, n, r_d, c_d, v_d, x_d,
-                                                                       flush)
+                                                                       flush, traffic_db)
     if blocking:
         for fmt in ("mergeb", "mergebh"):
             kg = blocking[fmt]["kernel_gbs"]
