@@ -19,10 +19,10 @@
 // Product.  One persistent CTA per SM takes a contiguous range of tiles.  For each slice in
 // its range with at least ST_STAGE_MIN tiles, the CTA copies the slice of x into shared
 // memory once (beta entries) and its warps read x from there; for the few tiles of sparse
-// slices x is gathered from global memory.  Each warp brings its tiles into shared memory
-// with 1-D bulk copies (TMA, two tiles in flight), decodes rows by a warp scan of the
-// deltas, forms the products, sums runs of equal rows inside a lane and across lanes (a
-// segmented scan), and adds each run's sum to y with one reduction (red.global.add);
+// slices x is gathered from global memory.  Each warp loads its tiles into registers with
+// 16-byte loads (later tiles prefetched into L2 a few turns ahead), decodes rows from the
+// deltas and the lane headers, forms the products, sums runs of equal rows inside a lane and
+// across lanes (a segmented scan), and adds each run's sum to y with one reduction (red.global.add);
 // y is zeroed first.  The run sums of a tile are staged in shared memory and reduced into y
 // 32 at a time, so that consecutive reductions touch consecutive rows.
 //
@@ -47,7 +47,7 @@ namespace {
 constexpr int ST_TILE = 256;                  // entries per warp tile
 constexpr int ST_IPT = ST_TILE / 32;          // entries per lane
 #ifndef ST_NW_CFG
-#define ST_NW_CFG 16
+#define ST_NW_CFG 20
 #endif
 #ifndef ST_PF_CFG
 #define ST_PF_CFG 3
@@ -254,17 +254,22 @@ __global__ void k_st_meta(const uint32_t *__restrict__ words, int4 *__restrict__
     if (lane == 0) hdr[t].w = (hd.w & 0xFF) | (total << 8);
 }
 
-// Cost of every tile for the split between CTAs, in units of one run sum (a shared-memory
-// round trip and a reduction in L2): ST_TILE_COST for the tile's 256 entries plus its run
-// sums, plus ST_STAGE_COST at the first tile of a slice whose x slice gets staged (the
-// weights that balanced the CTAs best on R-MAT scale 22); cost[ntiles] = 0.
+// Cost of every tile for the split between CTAs: ST_TILE_COST for the tile's 256 entries,
+// ST_RUN_COST per run sum (a shared-memory round trip and a reduction in L2), plus
+// ST_STAGE_COST at the first tile of a slice whose x slice gets staged.  The weights come from
+// per-CTA device times of R-MAT scales 20-22: a staging costs about 70 tiles, a run about 1/500
+// of a tile (a sweep around them gave the shortest kernel).  All weights are shifted right by
+// `sh` (chosen by the host) so that the prefix sum of the costs fits in 32 bits; cost[ntiles] = 0.
 #ifndef ST_TILE_COST_CFG
-#define ST_TILE_COST_CFG 256
+#define ST_TILE_COST_CFG 1024
+#endif
+#ifndef ST_RUN_COST_CFG
+#define ST_RUN_COST_CFG 2
 #endif
 #ifndef ST_STAGE_COST_CFG
-#define ST_STAGE_COST_CFG 8192
+#define ST_STAGE_COST_CFG 70000
 #endif
-__global__ void k_st_cost(const int4 *__restrict__ hdr, int64_t ntiles, uint32_t *__restrict__ cost) {
+__global__ void k_st_cost(const int4 *__restrict__ hdr, int64_t ntiles, int sh, uint32_t *__restrict__ cost) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t > ntiles) return;
     if (t == ntiles) {
@@ -272,7 +277,9 @@ __global__ void k_st_cost(const int4 *__restrict__ hdr, int64_t ntiles, uint32_t
         return;
     }
     const uint32_t w = (uint32_t)hdr[t].w;
-    cost[t] = (uint32_t)ST_TILE_COST_CFG + (w >> 8) + ((w & 2u) ? (uint32_t)ST_STAGE_COST_CFG : 0u);
+    const uint32_t c = (uint32_t)ST_TILE_COST_CFG + (w >> 8) * (uint32_t)ST_RUN_COST_CFG +
+                       ((w & 2u) ? (uint32_t)ST_STAGE_COST_CFG : 0u);
+    cost[t] = max(c >> sh, 1u);
 }
 
 // First tile of every CTA: equal shares of the prefix-summed cost.
@@ -582,8 +589,9 @@ struct StWalk {
 };
 
 // The CTA's tile range, slice by slice.  Acc/XS: accumulator and x type of the slices.  Each
-// warp takes the tiles t0 + warp, t0 + warp + ST_NW, ... in two register sets used in turn
-// (the next tile's loads are in flight while one is computed).
+// warp takes the tiles t0 + warp, t0 + warp + ST_NW, ... in one register set; the tiles a few
+// turns ahead are prefetched into L2.  (Two register sets, with the next tile's loads in flight
+// while one is computed, cap the CTA at 16 warps by registers; one set and 20 warps is faster.)
 template <typename Acc, typename SV, typename XS, typename YT>
 __device__ __forceinline__ void st_run(const StArgs<SV, YT> &a, const XS *__restrict__ xg, unsigned char *smem) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -621,25 +629,16 @@ __device__ __forceinline__ void st_run(const StArgs<SV, YT> &a, const XS *__rest
             else st_tile<false, false, Acc, SV, XS, YT>(T, xs, xg, a.lb, a.n, a.m, obuf, a.y, a.err);
         }
     };
-    StRegs<SV> A, B;
+    StRegs<SV> A;
     int64_t cp = t0 + warp;
     if (lane == 0)
-        for (int k = 2; k < 2 + ST_PF; ++k)
+        for (int k = 1; k < 1 + ST_PF; ++k)
             if (cp + k * ST_NW < t1) StRegs<SV>::prefetch(a, cp + k * ST_NW);
-    if (cp < t1) A.load(a, cp, lane);
-    auto pf = [&](int64_t t) {   // keep ST_PF tiles of this warp on their way into L2
-        const int64_t tp = t + (int64_t)(1 + ST_PF) * ST_NW;
-        if (lane == 0 && tp < t1) StRegs<SV>::prefetch(a, tp);
-    };
     while (cp < t1) {
-        if (cp + ST_NW < t1) B.load(a, cp + ST_NW, lane);
-        pf(cp);
+        A.load(a, cp, lane);
+        const int64_t tp = cp + (int64_t)(1 + ST_PF) * ST_NW;   // keep ST_PF tiles on their way into L2
+        if (lane == 0 && tp < t1) StRegs<SV>::prefetch(a, tp);
         tile(A, cp);
-        cp += ST_NW;
-        if (cp >= t1) break;
-        if (cp + ST_NW < t1) A.load(a, cp + ST_NW, lane);
-        pf(cp);
-        tile(B, cp);
         cp += ST_NW;
     }
     wk.advance(a, t1, xs, xg, &sbar);   // the barriers of the remaining staged segments
@@ -678,7 +677,12 @@ spmv_status st_split(const int4 *hp, int64_t ntiles, DevBuf *part, int *G, cudaS
     SPMV_TRY(cost.alloc((size_t)(ntiles + 1) * 4, "stage tile costs"));
     SPMV_TRY(pcost.alloc((size_t)(ntiles + 1) * 4, "stage tile costs"));
     SPMV_TRY(ctmp.alloc(scan_temp_bytes(ntiles + 1), "stage tile costs"));
-    SPMV_LAUNCH("k_st_cost", s, (k_st_cost<<<st_grid(ntiles + 1), ST_CB, 0, s>>>(hp, ntiles, cost.as<uint32_t>())));
+    // costs at most ntiles x (tile + 256 runs) + one staging per tile: shift them into 31 bits
+    const uint64_t bound = (uint64_t)ntiles * ((uint64_t)ST_TILE_COST_CFG + 256ull * ST_RUN_COST_CFG + ST_STAGE_COST_CFG);
+    int sh = 0;
+    while ((bound >> sh) >= (1ull << 31)) ++sh;
+    SPMV_LAUNCH("k_st_cost", s, (k_st_cost<<<st_grid(ntiles + 1), ST_CB, 0, s>>>(hp, ntiles, sh,
+                                                                              cost.as<uint32_t>())));
     SPMV_LAUNCH_CHECK("stage tile costs");
     SPMV_TRY(exclusive_scan_u32(cost.as<uint32_t>(), pcost.as<uint32_t>(), ntiles + 1, ctmp.p, s));
     SPMV_LAUNCH("k_st_parts", s, (k_st_parts<<<st_grid(*G + 1), ST_CB, 0, s>>>(pcost.as<uint32_t>(), ntiles, *G,
