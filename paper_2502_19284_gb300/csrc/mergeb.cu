@@ -18,9 +18,9 @@
 // over (block-row ends, entries), done once at the conversion.  The temporary vector is y
 // itself, kept in L2 while the warps walk a block row: a lane adds the sum of each run of its
 // entries in one row to y with one reduction (y is zeroed first), so the carries between
-// lanes and tiles need no fix-up pass.  A tile's entries reach shared memory by coalesced
-// loads; x is gathered from global memory.  Summation order across runs is not fixed (FP
-// results within tolerance, integer results exact).
+// lanes and tiles need no fix-up pass.  Persistent warps load the next tile's entries into
+// registers while they compute the current one; x is gathered from global memory.  Summation
+// order across runs is not fixed (FP results within tolerance, integer results exact).
 #include "common.cuh"
 #include "convert.cuh"
 #include "acc.cuh"
@@ -36,7 +36,7 @@ constexpr int MB_IPT = 8;                        // path items per lane
 constexpr int MB_ITEMS = 32 * MB_IPT;            // path items per warp tile
 constexpr int MB_WARPS = 8;                      // warps (tiles) per CTA
 #ifndef MB_MINB_CFG
-#define MB_MINB_CFG 4
+#define MB_MINB_CFG 2
 #endif
 constexpr int MB_MINB = MB_MINB_CFG;             // resident CTAs per SM the registers are sized for
 constexpr int MB_PAD = MB_ITEMS + MB_ITEMS / 8;  // staging slots: one spare slot per 8
@@ -85,6 +85,41 @@ __global__ void k_mb_desc(const int32_t *__restrict__ ptr, const int32_t *__rest
 
 // ---------------------------------------------------------------- product
 
+// Add a run sum to y with one reduction in L2 (compensated FP32 sums are rounded first).
+template <typename YT, typename Acc>
+__device__ __forceinline__ void mb_red(YT *p, const Acc &a) {
+    atomicAdd(p, a.template out<YT>());
+}
+
+// A warp tile's split points: this lane's (entry, block) and the entry where its items end,
+// the tile's first entry and its entry count.  Loaded raw first, finished (shuffles) later.
+struct MbRaw {
+    int2 dc;
+    int tail;   // lane 31: the first entry of the next tile (or nnz)
+};
+struct MbTile {
+    int2 dc;
+    int e1, te0, tn;
+};
+__device__ __forceinline__ MbRaw mb_load(const int2 *__restrict__ desc, int64_t t, int64_t ntiles, int64_t nnz,
+                                         int lane) {
+    MbRaw r;
+    r.dc = desc[t * 32 + lane];
+    r.tail = lane == 31 ? (t + 1 < ntiles ? desc[(t + 1) * 32].x : (int)nnz) : 0;
+    return r;
+}
+__device__ __forceinline__ MbTile mb_finish(const MbRaw &r, int lane) {
+    MbTile T;
+    T.dc = r.dc;
+    T.e1 = __shfl_down_sync(0xffffffffu, r.dc.x, 1);
+    if (lane == 31) T.e1 = r.tail;
+    T.te0 = __shfl_sync(0xffffffffu, r.dc.x, 0);
+    // at most MB_ITEMS entries by the merge-path split (clamped, so that a damaged table can
+    // never index past a staging slot)
+    T.tn = max(0, min(__shfl_sync(0xffffffffu, T.e1, 31) - T.te0, MB_ITEMS));
+    return T;
+}
+
 template <typename T>
 __device__ __forceinline__ T ld_stream(const T *p) {
     if constexpr (std::is_same<T, __nv_bfloat16>::value) {
@@ -94,13 +129,14 @@ __device__ __forceinline__ T ld_stream(const T *p) {
     }
 }
 
-// Add a run sum to y with one reduction in L2 (compensated FP32 sums are rounded first).
-template <typename YT, typename Acc>
-__device__ __forceinline__ void mb_red(YT *p, const Acc &a) {
-    atomicAdd(p, a.template out<YT>());
-}
-
-// One warp tile per warp.  VT: stored value type (Pattern: none); XT/YT: vector types.
+// Persistent warps over the tiles w, w + W, ... (W warps in the grid).  While a tile is
+// computed, the packed indices and values of the warp's next tile are already loaded into
+// registers (lane-strided, streaming loads that do not displace x from L1) and the split
+// points of the tile after it are on their way, so a tile's exposed latency is its x gathers;
+// a warp that stays resident also never waits for its reductions to drain between tiles.  The
+// tile's entries pass through the warp's shared slot (entry j at j + j / 8: a lane's 8
+// consecutive entries fall on distinct banks).  VT: stored value type (Pattern: none);
+// XT/YT: vector types.
 template <typename Acc, typename VT, typename XT, typename YT>
 __global__ __launch_bounds__(MB_WARPS * 32, MB_MINB) void k_mergeb(const int2 *__restrict__ desc,
                                                           const int32_t *__restrict__ blk_ptr,
@@ -117,75 +153,112 @@ __global__ __launch_bounds__(MB_WARPS * 32, MB_MINB) void k_mergeb(const int2 *_
     __shared__ uint32_t s_w[MB_WARPS][MB_PAD];
     __shared__ VS s_v[MB_WARPS][PAT ? 1 : MB_PAD];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t t = (int64_t)blockIdx.x * MB_WARPS + warp;
+    const int64_t W = (int64_t)gridDim.x * MB_WARPS;
+    int64_t t = (int64_t)blockIdx.x * MB_WARPS + warp;
     if (t >= ntiles) return;   // whole warps
-    const int2 dc = desc[t * 32 + lane];
-    int e1 = __shfl_down_sync(0xffffffffu, dc.x, 1);
-    if (lane == 31) e1 = t + 1 < ntiles ? desc[(t + 1) * 32].x : (int)nnz;
-    const int te0 = __shfl_sync(0xffffffffu, dc.x, 0);
-    // entries of the tile: at most MB_ITEMS by the merge-path split (clamped, so that a damaged
-    // table can never index past the staging slots)
-    const int tn = max(0, min(__shfl_sync(0xffffffffu, e1, 31) - te0, MB_ITEMS));
-    for (int j = lane; j < tn; j += 32) {
-        const int p = j + (j >> 3);
-        s_w[warp][p] = __ldcs(idx + te0 + j);
-        if constexpr (!PAT) s_v[warp][p] = ld_stream(val + te0 + j);
-    }
-    __syncwarp();
-    const int ne = max(0, min(e1 - dc.x, MB_IPT)), o0 = dc.x - te0;
-    int64_t b = dc.y, bend = 0, rbase = 0, cbase = 0;
-    if (ne > 0) {
-        bend = blk_ptr[b + 1];
-        rbase = (int64_t)blk_row[b] << lb;
-        cbase = (int64_t)blk_col[b] << lb;
-    }
-    int32_t row[MB_IPT];   // -1: no entry (rows < 2^31)
-    Op av[MB_IPT], xv[MB_IPT];
+    uint32_t pw[MB_IPT];
+    VS pv[MB_IPT];
+    auto fetch = [&](const MbTile &T) {   // the tile's entries, lane-strided, into registers
 #pragma unroll
-    for (int k = 0; k < MB_IPT; ++k) {
-        row[k] = -1;
-        av[k] = Op(0);
-        xv[k] = Op(0);
-        if (k < ne && o0 >= 0 && o0 + k < tn) {
-            if ((int64_t)dc.x + k >= bend && b + 1 < nblk) {   // the next block (blocks are never empty)
-                ++b;
-                bend = blk_ptr[b + 1];
-                rbase = (int64_t)blk_row[b] << lb;
-                cbase = (int64_t)blk_col[b] << lb;
-            }
-            const int p = o0 + k, ps = p + (p >> 3);
-            const uint32_t w = s_w[warp][ps];
-            const int64_t r = rbase + (w >> 16), c = cbase + (w & 0xFFFFu);
-            if (r < m && c < n) {
-                row[k] = (int32_t)r;
-                xv[k] = ld_x<XT, Op>(x, c);
-                if constexpr (PAT) av[k] = Op(1);
-                else av[k] = sval<VT, Op>(s_v[warp], ps);
-            } else {
-                atomicOr(err, ST_INDEX_RANGE);   // a corrupt structure: report, never write outside y
+        for (int k = 0; k < MB_IPT; ++k) {
+            const int j = lane + 32 * k;
+            if (j < T.tn) {
+                pw[k] = __ldcs(idx + T.te0 + j);
+                if constexpr (!PAT) pv[k] = ld_stream(val + T.te0 + j);
             }
         }
-    }
-    Acc acc;
-    acc.zero();
-    int32_t cur = -1;
+    };
+    MbTile cur = mb_finish(mb_load(desc, t, ntiles, nnz, lane), lane);
+    fetch(cur);
+    bool more = t + W < ntiles;
+    MbRaw rnext{};
+    if (more) rnext = mb_load(desc, t + W, ntiles, nnz, lane);
+    for (;;) {
 #pragma unroll
-    for (int k = 0; k < MB_IPT; ++k) {
-        if (row[k] < 0) continue;
-        if (row[k] != cur) {
-            if (cur >= 0) mb_red(y + cur, acc);
-            acc.zero();
-            cur = row[k];
+        for (int k = 0; k < MB_IPT; ++k) {
+            const int j = lane + 32 * k;
+            if (j < cur.tn) {
+                const int p = j + (j >> 3);
+                s_w[warp][p] = pw[k];
+                if constexpr (!PAT) s_v[warp][p] = pv[k];
+            }
         }
-        acc.mad(av[k], xv[k]);
+        __syncwarp();
+        MbTile nxt{};
+        if (more) {
+            nxt = mb_finish(rnext, lane);
+            fetch(nxt);                                   // in flight while this tile is computed
+            if (t + 2 * W < ntiles) rnext = mb_load(desc, t + 2 * W, ntiles, nnz, lane);
+        }
+        const int2 dc = cur.dc;
+        const int ne = max(0, min(cur.e1 - dc.x, MB_IPT)), o0 = dc.x - cur.te0;
+        int64_t b = dc.y, bend = 0, rbase = 0, cbase = 0;
+        if (ne > 0) {
+            bend = blk_ptr[b + 1];
+            rbase = (int64_t)blk_row[b] << lb;
+            cbase = (int64_t)blk_col[b] << lb;
+        }
+        int32_t row[MB_IPT];
+        Op av[MB_IPT], xv[MB_IPT];
+#pragma unroll
+        for (int k = 0; k < MB_IPT; ++k) {
+            row[k] = -1;
+            av[k] = Op(0);
+            xv[k] = Op(0);
+            if (k < ne && o0 >= 0 && o0 + k < cur.tn) {
+                if ((int64_t)dc.x + k >= bend && b + 1 < nblk) {
+                    ++b;
+                    bend = blk_ptr[b + 1];
+                    rbase = (int64_t)blk_row[b] << lb;
+                    cbase = (int64_t)blk_col[b] << lb;
+                }
+                const int p = o0 + k, ps = p + (p >> 3);
+                const uint32_t w = s_w[warp][ps];
+                const int64_t r = rbase + (w >> 16), c = cbase + (w & 0xFFFFu);
+                if (r < m && c < n) {
+                    row[k] = (int32_t)r;
+                    xv[k] = ld_x<XT, Op>(x, c);
+                    if constexpr (PAT) av[k] = Op(1);
+                    else av[k] = sval<VT, Op>(s_v[warp], ps);
+                } else {
+                    atomicOr(err, ST_INDEX_RANGE);
+                }
+            }
+        }
+        Acc acc;
+        acc.zero();
+        int32_t cr = -1;
+#pragma unroll
+        for (int k = 0; k < MB_IPT; ++k) {
+            if (row[k] < 0) continue;
+            if (row[k] != cr) {
+                if (cr >= 0) mb_red(y + cr, acc);
+                acc.zero();
+                cr = row[k];
+            }
+            acc.mad(av[k], xv[k]);
+        }
+        if (cr >= 0) mb_red(y + cr, acc);
+        __syncwarp();
+        if (!more) break;
+        t += W;
+        cur = nxt;
+        more = t + W < ntiles;
     }
-    if (cur >= 0) mb_red(y + cur, acc);
 }
 
 template <typename Acc, typename VT, typename XT, typename YT>
 spmv_status mb_launch(const spmv_matrix *h, const void *x, void *y, cudaStream_t s) {
-    const unsigned grid = (unsigned)((h->mb_tiles + MB_WARPS - 1) / MB_WARPS);
-    SPMV_LAUNCH("k_mergeb", s, (k_mergeb<Acc, VT, XT, YT><<<grid, MB_WARPS * 32, 0, s>>>(
+    constexpr size_t smem = 0;   // static slots
+    int dev = 0, sms = 1, per = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mergeb<Acc, VT, XT, YT>, MB_WARPS * 32, smem) !=
+            cudaSuccess)
+        return cuda_status(cudaGetLastError(), "merge blocking grid");
+    const int64_t tiles_ctas = (h->mb_tiles + MB_WARPS - 1) / MB_WARPS;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles_ctas, (int64_t)sms * std::max(per, 1)));
+    SPMV_LAUNCH("k_mergeb", s, (k_mergeb<Acc, VT, XT, YT><<<grid, MB_WARPS * 32, smem, s>>>(
                                    h->mb_desc, h->blk_ptr, h->blk_row, h->blk_col, h->hb_idx, (const VT *)h->hb_val,
                                    (const XT *)x, (YT *)y, h->nblk, h->nnz, h->mb_tiles, h->m, h->n, h->log2beta,
                                    h->status_dev + 3)));
