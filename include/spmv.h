@@ -231,9 +231,12 @@ spmv_status spmv_destroy(spmv_handle h);
  * spmv_tune -- autotuner: time one product y = A x in each candidate storage format of the
  * handle (Section 6.1 finds that the best method depends on the matrix; here it is
  * measured), and make the fastest the active format.  Candidates: row-split CRS and
- * merge-path CRS (built if missing, both cheap), and the Hilbert-blocked format with both of
+ * merge-path CRS (built if missing, both cheap), the Hilbert-blocked format with both of
  * its products (staged block columns and Hilbert-ordered chunks) if it is already built or
- * flags has SPMV_TUNE_HB (its conversion costs far more than a product).
+ * flags has SPMV_TUNE_HB (its conversion costs far more than a product), and Merge Blocking
+ * (MERGEB, row-wise inside the blocks) if its tables are built or flags has SPMV_TUNE_MERGEB
+ * (which rebuilds the blocked arrays in row-major block order when they are in another order;
+ * the HB products then run on those).
  *   vec_dt, accum   the product to time (as in spmv_mul).
  *   out             may be NULL; receives the chosen format (and HB product) and the median
  *                   time of one product per candidate in milliseconds (-1 where not tried).
@@ -242,11 +245,12 @@ spmv_status spmv_destroy(spmv_handle h);
  * with k = 1 runs a handle whose active format is row-split or blocked with that product,
  * after the persistent launch of the merge-path matrices of the batch.
  */
-enum { SPMV_TUNE_HB = 0x1 };
+enum { SPMV_TUNE_HB = 0x1, SPMV_TUNE_MERGEB = 0x2 };
 typedef struct {
-    int32_t chosen;     /* SPMV_FMT_CSR_ROWSPLIT, SPMV_FMT_CSR_MERGE or SPMV_FMT_HB */
+    int32_t chosen;     /* SPMV_FMT_CSR_ROWSPLIT, SPMV_FMT_CSR_MERGE, SPMV_FMT_HB or SPMV_FMT_MERGEB */
     int32_t reps;       /* timed products per candidate */
-    float ms[4];        /* median ms per product: [ROWSPLIT, MERGE, HB staged, HB chunked], -1 if not tried */
+    float ms[5];        /* median ms per product: [ROWSPLIT, MERGE, HB staged, HB chunked, MERGEB],
+                           -1 if not tried */
     int32_t hb_product; /* SPMV_HB_STAGED or SPMV_HB_CHUNKED when chosen is SPMV_FMT_HB */
     int32_t pad_;
 } spmv_tune_result;

@@ -55,11 +55,11 @@ class spmv_info_t(ctypes.Structure):
 
 
 class spmv_tune_result(ctypes.Structure):
-    _fields_ = [("chosen", ctypes.c_int32), ("reps", ctypes.c_int32), ("ms", ctypes.c_float * 4),
+    _fields_ = [("chosen", ctypes.c_int32), ("reps", ctypes.c_int32), ("ms", ctypes.c_float * 5),
                 ("hb_product", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
-SPMV_TUNE_HB = 0x1
+SPMV_TUNE_HB, SPMV_TUNE_MERGEB = 0x1, 0x2
 
 
 class spmv_server_opts(ctypes.Structure):
@@ -400,16 +400,18 @@ def spmv_set_compensation_threshold(h: Handle, tau: int):
     _check(_lib.spmv_set_compensation_threshold(h.ptr, int(tau)), "spmv_set_compensation_threshold")
 
 
-def spmv_tune(h: Handle, vec_dtype="f64", accum=SPMV_ACC_DEFAULT, hb=False, stream=None) -> dict:
+def spmv_tune(h: Handle, vec_dtype="f64", accum=SPMV_ACC_DEFAULT, hb=False, mergeb=False, stream=None) -> dict:
     """Time one product per storage format and make the fastest the handle's active format."""
     r = spmv_tune_result()
     vdt = SPMV_F64 if vec_dtype in ("f64", SPMV_F64) else SPMV_F32
-    _check(_lib.spmv_tune(h.ptr, vdt, accum, SPMV_TUNE_HB if hb else 0, ctypes.byref(r), _stream(stream)), "spmv_tune")
-    names = {SPMV_FMT_CSR_ROWSPLIT: "rowsplit", SPMV_FMT_CSR_MERGE: "merge", SPMV_FMT_HB: "hb"}
+    flags = (SPMV_TUNE_HB if hb else 0) | (SPMV_TUNE_MERGEB if mergeb else 0)
+    _check(_lib.spmv_tune(h.ptr, vdt, accum, flags, ctypes.byref(r), _stream(stream)), "spmv_tune")
+    names = {SPMV_FMT_CSR_ROWSPLIT: "rowsplit", SPMV_FMT_CSR_MERGE: "merge", SPMV_FMT_HB: "hb",
+             SPMV_FMT_MERGEB: "mergeb"}
     chosen = names[r.chosen]
     if r.chosen == SPMV_FMT_HB and r.hb_product == SPMV_HB_CHUNKED:
         chosen = "hb_chunked"
-    ms = dict(zip(["rowsplit", "merge", "hb", "hb_chunked"], [float(v) for v in r.ms]))
+    ms = dict(zip(["rowsplit", "merge", "hb", "hb_chunked", "mergeb"], [float(v) for v in r.ms]))
     return {"chosen": chosen, "ms": {k: v for k, v in ms.items() if v >= 0}}
 
 

@@ -477,7 +477,8 @@ spmv_status spmv_tune(spmv_handle h, spmv_dtype vec_dt, uint32_t accum, uint32_t
                       void *stream) {
     g_err.clear();
     SPMV_TRY(check_handle(h));
-    if ((vec_dt != SPMV_F64 && vec_dt != SPMV_F32) || accum > SPMV_ACC_SEGMENT || (flags & ~SPMV_TUNE_HB)) {
+    if ((vec_dt != SPMV_F64 && vec_dt != SPMV_F32) || accum > SPMV_ACC_SEGMENT ||
+        (flags & ~(uint32_t)(SPMV_TUNE_HB | SPMV_TUNE_MERGEB))) {
         set_error("spmv_tune: bad vector dtype, accumulation or flags");
         return SPMV_ERR_INVALID_ARG;
     }
@@ -487,6 +488,13 @@ spmv_status spmv_tune(spmv_handle h, spmv_dtype vec_dt, uint32_t accum, uint32_t
     if (!h->has_bins) SPMV_TRY(build_bins(h, s));
     if (!h->has_merge) SPMV_TRY(build_merge(h, MERGE_WARP_ITEMS, s));
     if (h->dt == SPMV_F64) SPMV_TRY(build_df(h, s));
+    if ((flags & SPMV_TUNE_MERGEB) && !h->has_mergeb) {
+        const int K = bits_for(std::max<int64_t>(std::max(h->m, h->n), 2));
+        const int lb = std::min(default_log2_beta(h->n, h->dt == SPMV_F64 ? 8 : 4), K);
+        if (!h->has_hb || h->block_order != SPMV_BLOCK_ROWMAJOR || h->log2beta != lb)
+            SPMV_TRY(build_hb(h, lb, SPMV_INNER_ROWMAJOR, s, SPMV_BLOCK_ROWMAJOR));
+        SPMV_TRY(build_mergeb(h, s));
+    }
     if ((flags & SPMV_TUNE_HB) && !h->has_hb)
         SPMV_TRY(build_hb(h, default_log2_beta(h->n, h->dt == SPMV_F64 ? 8 : 4), SPMV_INNER_HILBERT, s));
     if ((flags & SPMV_TUNE_HB) && h->has_hb && !h->has_stage) SPMV_TRY(build_stage(h, h->log2beta, s));
@@ -500,8 +508,8 @@ spmv_status spmv_tune(spmv_handle h, spmv_dtype vec_dt, uint32_t accum, uint32_t
     SPMV_TRY(x.alloc((size_t)std::max<int64_t>(h->n, 1) * es, "tune x"));
     SPMV_TRY(y.alloc((size_t)std::max<int64_t>(h->m, 1) * es, "tune y"));
     SPMV_CUDA_TRY(cudaMemsetAsync(x.p, 0, (size_t)std::max<int64_t>(h->n, 1) * es, s));
-    const int32_t fmts[4] = {SPMV_FMT_CSR_ROWSPLIT, SPMV_FMT_CSR_MERGE, SPMV_FMT_HB, SPMV_FMT_HB};
-    const bool chunked[4] = {false, false, false, true};
+    const int32_t fmts[5] = {SPMV_FMT_CSR_ROWSPLIT, SPMV_FMT_CSR_MERGE, SPMV_FMT_HB, SPMV_FMT_HB, SPMV_FMT_MERGEB};
+    const bool chunked[5] = {false, false, false, true, false};
     cudaEvent_t e0, e1;
     SPMV_CUDA_TRY(cudaEventCreate(&e0));
     SPMV_CUDA_TRY(cudaEventCreate(&e1));
@@ -509,8 +517,9 @@ spmv_status spmv_tune(spmv_handle h, spmv_dtype vec_dt, uint32_t accum, uint32_t
     const bool keep_chunked = h->hb_chunked;
     spmv_status st = SPMV_OK;
     int best = -1;
-    for (int f = 0; f < 4 && st == SPMV_OK; ++f) {
+    for (int f = 0; f < 5 && st == SPMV_OK; ++f) {
         if (fmts[f] == SPMV_FMT_HB && (!h->has_hb || (!chunked[f] && !h->has_stage))) continue;
+        if (fmts[f] == SPMV_FMT_MERGEB && !h->has_mergeb) continue;
         h->format = fmts[f];
         h->hb_chunked = chunked[f];
         std::vector<float> t;

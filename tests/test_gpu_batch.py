@@ -227,6 +227,15 @@ def test_tune_picks_a_measured_format(sp):
     sp.spmv_mul(h, torch.from_numpy(x).to(DEV), y)
     torch.cuda.synchronize()
     assert (np.abs(y.cpu().numpy() - oracle.csr_spmv(rp, co, vo, x)) <= TOL * oracle.csr_absmul(rp, co, vo, x)).all()
+    # with Merge Blocking among the candidates: five timings, the choice the fastest, the product right
+    res = sp.spmv_tune(h, "f64", hb=True, mergeb=True)
+    ms = res["ms"]
+    assert set(ms) == {"rowsplit", "merge", "hb", "hb_chunked", "mergeb"} and all(t > 0 for t in ms.values()), ms
+    assert res["chosen"] == min(ms, key=ms.get)
+    y.fill_(float("nan"))
+    sp.spmv_mul(h, torch.from_numpy(x).to(DEV), y)
+    torch.cuda.synchronize()
+    assert (np.abs(y.cpu().numpy() - oracle.csr_spmv(rp, co, vo, x)) <= TOL * oracle.csr_absmul(rp, co, vo, x)).all()
     sp.spmv_destroy(h)
 
 
