@@ -47,10 +47,10 @@ namespace {
 constexpr int ST_TILE = 256;                  // entries per warp tile
 constexpr int ST_IPT = ST_TILE / 32;          // entries per lane
 #ifndef ST_NW_CFG
-#define ST_NW_CFG 20
+#define ST_NW_CFG 22
 #endif
 #ifndef ST_PF_CFG
-#define ST_PF_CFG 3
+#define ST_PF_CFG 0
 #endif
 #ifndef ST_STAGE_MIN_CFG
 #define ST_STAGE_MIN_CFG 16
@@ -58,7 +58,7 @@ constexpr int ST_IPT = ST_TILE / 32;          // entries per lane
 constexpr int ST_NW = ST_NW_CFG;              // warps per CTA
 constexpr int ST_STAGE_MIN = ST_STAGE_MIN_CFG;   // tiles of a slice in a CTA's range from which x is staged
 constexpr int ST_X_MAX = 128 * 1024;          // largest x slice staged in shared memory (bytes)
-constexpr int ST_PF = ST_PF_CFG;              // a warp prefetches its tiles this many turns ahead into L2
+constexpr int ST_PF = ST_PF_CFG;              // a warp prefetches into L2 the tile this many turns after its next
 
 inline unsigned cdivu(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
@@ -257,14 +257,14 @@ __global__ void k_st_meta(const uint32_t *__restrict__ words, int4 *__restrict__
 // Cost of every tile for the split between CTAs: ST_TILE_COST for the tile's 256 entries,
 // ST_RUN_COST per run sum (a shared-memory round trip and a reduction in L2), plus
 // ST_STAGE_COST at the first tile of a slice whose x slice gets staged.  The weights come from
-// per-CTA device times of R-MAT scales 20-22: a staging costs about 70 tiles, a run about 1/500
+// per-CTA device times of R-MAT scales 20-22: a staging costs about 70 tiles, a run about 1/350
 // of a tile (a sweep around them gave the shortest kernel).  All weights are shifted right by
 // `sh` (chosen by the host) so that the prefix sum of the costs fits in 32 bits; cost[ntiles] = 0.
 #ifndef ST_TILE_COST_CFG
 #define ST_TILE_COST_CFG 1024
 #endif
 #ifndef ST_RUN_COST_CFG
-#define ST_RUN_COST_CFG 2
+#define ST_RUN_COST_CFG 3
 #endif
 #ifndef ST_STAGE_COST_CFG
 #define ST_STAGE_COST_CFG 70000
@@ -589,9 +589,11 @@ struct StWalk {
 };
 
 // The CTA's tile range, slice by slice.  Acc/XS: accumulator and x type of the slices.  Each
-// warp takes the tiles t0 + warp, t0 + warp + ST_NW, ... in one register set; the tiles a few
-// turns ahead are prefetched into L2.  (Two register sets, with the next tile's loads in flight
-// while one is computed, cap the CTA at 16 warps by registers; one set and 20 warps is faster.)
+// warp takes the tiles t0 + warp, t0 + warp + ST_NW, ... in one register set, and while it
+// computes one tile its next is prefetched into L2 (measured: no prefetch 0.272 ms, the next
+// tile 0.251 ms, three or five tiles ahead 0.269 / 0.286 ms at R-MAT scale 22).  Two register
+// sets, with the next tile's loads in flight in registers, cap the CTA at 16 warps by registers;
+// one set and 22 warps is faster.
 template <typename Acc, typename SV, typename XS, typename YT>
 __device__ __forceinline__ void st_run(const StArgs<SV, YT> &a, const XS *__restrict__ xg, unsigned char *smem) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -636,7 +638,7 @@ __device__ __forceinline__ void st_run(const StArgs<SV, YT> &a, const XS *__rest
             if (cp + k * ST_NW < t1) StRegs<SV>::prefetch(a, cp + k * ST_NW);
     while (cp < t1) {
         A.load(a, cp, lane);
-        const int64_t tp = cp + (int64_t)(1 + ST_PF) * ST_NW;   // keep ST_PF tiles on their way into L2
+        const int64_t tp = cp + (int64_t)(1 + ST_PF) * ST_NW;   // the next tile (ST_PF = 0) on its way into L2
         if (lane == 0 && tp < t1) StRegs<SV>::prefetch(a, tp);
         tile(A, cp);
         cp += ST_NW;
