@@ -72,6 +72,8 @@ void free_mergeb(spmv_matrix *h, cudaStream_t s);
 spmv_status mul_mergeb(const spmv_matrix *h, const void *x, void *y, spmv_dtype vdt, uint32_t acc, cudaStream_t s);
 // x -> float pairs in h->xsplit, with the window flag h->xsplit_flag reset and set (spmv.cu).
 spmv_status split_x(const spmv_matrix *h, const double *x, cudaStream_t s);
+// The same, and y := 0 (m doubles) in the same launch.
+spmv_status split_x_zero_y(const spmv_matrix *h, const double *x, double *y, cudaStream_t s);
 // Bounded-wait check: one warp waits `polls` polls on an mbarrier nothing arrives at and sets
 // ST_TIMEOUT in *status (device word) when it gives up.
 spmv_status test_wait(long long polls, uint32_t *status, cudaStream_t s);

@@ -830,6 +830,32 @@ __global__ void k_df_split_x(const double *__restrict__ x, int64_t n, float2 *__
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
 }
 
+// The same split, and y := 0 over m entries, in one launch (for products that zero y first).
+__global__ void k_df_split_x_zero(const double *__restrict__ x, int64_t n, float2 *__restrict__ x2, uint32_t *flag,
+                                  double *__restrict__ y, int64_t m) {
+    const int64_t i = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    bool bad = false;
+    if (i + 1 < n && ((reinterpret_cast<uintptr_t>(x) & 15u) == 0u)) {
+        const double2 v = *reinterpret_cast<const double2 *>(x + i);
+        float4 r;
+        bad = !df_split(v.x, &r.x, &r.y);
+        bad |= !df_split(v.y, &r.z, &r.w);
+        *reinterpret_cast<float4 *>(x2 + i) = r;
+    } else {
+        for (int64_t j = i; j < i + 2 && j < n; ++j) {
+            float2 r;
+            bad |= !df_split(x[j], &r.x, &r.y);
+            x2[j] = r;
+        }
+    }
+    if (i + 1 < m && ((reinterpret_cast<uintptr_t>(y) & 15u) == 0u)) {
+        *reinterpret_cast<double2 *>(y + i) = make_double2(0.0, 0.0);
+    } else {
+        for (int64_t j = i; j < i + 2 && j < m; ++j) y[j] = 0.0;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
 // Tile carries, added in tile order: the first tile of each run of equal carry rows sums
 // the run and adds it to y[row] (which the finishing tile has already written).
 template <typename XT>
@@ -1478,6 +1504,17 @@ spmv_status split_x(const spmv_matrix *h, const double *x, cudaStream_t s) {
         SPMV_LAUNCH("k_df_split_x", s,
                     (k_df_split_x<<<cdivu((h->n + 1) / 2, 256), 256, 0, s>>>(x, h->n, h->xsplit, h->xsplit_flag)));
         SPMV_LAUNCH_CHECK("x split");
+    }
+    return SPMV_OK;
+}
+
+spmv_status split_x_zero_y(const spmv_matrix *h, const double *x, double *y, cudaStream_t s) {
+    SPMV_CUDA_TRY(cudaMemsetAsync(h->xsplit_flag, 0, 4, s));
+    const int64_t e = std::max(h->n, h->m);
+    if (e > 0) {
+        SPMV_LAUNCH("k_df_split_x", s, (k_df_split_x_zero<<<cdivu((e + 1) / 2, 256), 256, 0, s>>>(
+                                           x, h->n, h->xsplit, h->xsplit_flag, y, h->m)));
+        SPMV_LAUNCH_CHECK("x split and y zero");
     }
     return SPMV_OK;
 }

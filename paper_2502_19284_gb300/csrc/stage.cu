@@ -762,7 +762,8 @@ template <typename SV>
 spmv_status st_mul_f64(const spmv_matrix *h, const double *x, double *y, bool force_native, cudaStream_t s) {
     constexpr bool CAN_DF = std::is_same<SV, float2>::value || std::is_same<SV, Pattern>::value;
     bool use_df = CAN_DF && !force_native && h->xsplit;
-    if (use_df) SPMV_TRY(split_x(h, x, s));
+    if (use_df) SPMV_TRY(split_x_zero_y(h, x, y, s));   // y zeroed in the same launch
+    else SPMV_CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)h->m * 8, s));
     bool stage_ok = false;
     StArgs<SV, double> a = st_args<SV, double>(h, 8, x, y, &stage_ok);
     static_assert(StOut<DfAcc>::BYTES == StOut<NativeAcc<double>>::BYTES, "one buffer size for both forms");
@@ -979,8 +980,10 @@ spmv_status mul_stage(const spmv_matrix *h, const void *x, void *y, spmv_dtype v
                       (acc == SPMV_ACC_DEFAULT || acc == SPMV_ACC_F32 || acc == SPMV_ACC_SEGMENT ||
                        acc == SPMV_ACC_COMPENSATED);
     if (!ok64 && !ok32) goto unsupported;
-    SPMV_CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)h->m * (vdt == SPMV_F64 ? 8 : 4), s));
-    if (h->stage_tiles == 0) return SPMV_OK;
+    if (h->stage_tiles == 0 || vdt == SPMV_F32) {   // FP64 products zero y themselves
+        SPMV_CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)h->m * (vdt == SPMV_F64 ? 8 : 4), s));
+        if (h->stage_tiles == 0) return SPMV_OK;
+    }
     if (vdt == SPMV_F64) {
         const bool force = acc == SPMV_ACC_F64;
         switch (h->stage_kind) {
