@@ -112,6 +112,33 @@ def test_x_outside_double_float_window(sp):
     within(mul(sp, h, x2, m), rp, co, vo, x2)        # back on the double-float path
 
 
+def test_double_float_window_edge_subnormal_parts(sp):
+    """Values and x near the bottom of the double-float window (2^-50, exactly representable in
+    FP32): products near 2^-100 whose rounding errors, the compensation parts of the run sums,
+    are often subnormal floats.  Those take the exact widening (a short one covers normal numbers
+    and zeros only); flushing them would leave errors near 2^-126, far above the tolerance of
+    about 2^-140 at this scale."""
+    rows, cols = synth.rmat(14, 16, seed=31)
+    m = n = 1 << 14
+    rng = np.random.default_rng(32)
+    def near(k):
+        v = np.ldexp(1.0 + rng.random(k), -50).astype(np.float32).astype(np.float64)
+        return np.where(rng.random(k) < 0.5, -v, v)
+    vals = near(rows.size)
+    x = near(n)
+    rp, co, vo = oracle.coo_to_csr(m, n, rows, cols, vals)
+    h = sp.spmv_create_coo(m, n, dev(rows), dev(cols), dev(vals))
+    sp.spmv_convert(h, "hb")
+    y = mul(sp, h, x, m)
+    within(y, rp, co, vo, x)
+    # the compensation parts really are subnormal here: products of two such floats have
+    # rounding errors below 2^-126 for a sizeable share of the pairs
+    a = np.float32(vals[:1000])
+    b = np.float32(x[cols[:1000]])
+    err = a.astype(np.float64) * b.astype(np.float64) - (a * b).astype(np.float64)
+    assert np.mean((err != 0) & (np.abs(err) < 2.0 ** -126)) > 0.1
+
+
 @pytest.mark.parametrize("inner", [0, 1])
 def test_staged_equals_chunked_product(sp, inner):
     """Both HB products on one handle agree bit for bit on integer data, at several block
