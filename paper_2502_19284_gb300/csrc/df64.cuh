@@ -76,7 +76,27 @@ __device__ __forceinline__ double df_widen(float f) {
     return __longlong_as_double((long long)d);
 }
 
-// (s, c) as one double: one FP64 addition.
-__device__ __forceinline__ double df_to_double(float s, float c) { return df_widen(s) + df_widen(c); }
+// The same for normal numbers and zeros only, in 32-bit operations: the double's high word holds
+// the sign, the exponent rebiased by 1023 - 127 = 896 and the top 20 mantissa bits, the low word
+// the last 3 mantissa bits.
+__device__ __forceinline__ double df_widen_normal(float f) {
+    const uint32_t u = __float_as_uint(f), mag = u & 0x7FFFFFFFu;
+    const uint32_t hi = mag == 0u ? 0u : (mag >> 3) + (896u << 20);
+    return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)(u << 29));
+}
+
+// A subnormal, infinite or NaN float (the classes df_widen_normal does not cover).
+__device__ __forceinline__ bool df_special(float f) {
+    const uint32_t mag = __float_as_uint(f) & 0x7FFFFFFFu;
+    return mag != 0u && mag - 0x00800000u >= 0x7F000000u;
+}
+
+// (s, c) as one double: one FP64 addition of the exactly widened parts.  The short widening
+// serves every lane unless a lane of the warp holds a special part (the result is the same
+// either way: both widenings are exact).
+__device__ __forceinline__ double df_to_double(float s, float c) {
+    if (__any_sync(__activemask(), df_special(s) || df_special(c))) return df_widen(s) + df_widen(c);
+    return df_widen_normal(s) + df_widen_normal(c);
+}
 
 }  // namespace spmv

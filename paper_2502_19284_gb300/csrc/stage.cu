@@ -433,20 +433,6 @@ __device__ __forceinline__ double st_widen(float f) {
     return __longlong_as_double((long long)d);
 }
 
-// The same widening for normal numbers and zeros only, in 32-bit operations: the double's high
-// word holds the sign, the exponent rebiased by 1023 - 127 = 896 and the top 20 mantissa bits, the
-// low word the last 3 mantissa bits.
-__device__ __forceinline__ double st_widen_normal(float f) {
-    const uint32_t u = __float_as_uint(f), mag = u & 0x7FFFFFFFu;
-    const uint32_t hi = mag == 0u ? 0u : (mag >> 3) + (896u << 20);
-    return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)(u << 29));
-}
-// A subnormal, infinite or NaN float (the classes st_widen_normal does not cover).
-__device__ __forceinline__ bool st_special(float f) {
-    const uint32_t mag = __float_as_uint(f) & 0x7FFFFFFFu;
-    return mag != 0u && mag - 0x00800000u >= 0x7F000000u;
-}
-
 // Add a run sum to y with one reduction in L2.  A double-float sum (s, c) is widened part by
 // part (exact, integer operations: the short form unless a lane of the warp holds a special
 // part) and joined by one FP64 addition: measured on R-MAT scale 22, one reduction per run is
@@ -455,10 +441,10 @@ __device__ __forceinline__ bool st_special(float f) {
 template <typename YT, typename Acc>
 __device__ __forceinline__ void st_red(YT *p, const Acc &a) {
     if constexpr (std::is_same<Acc, DfAcc>::value) {
-        const bool sp = st_special(a.s) || st_special(a.c);
+        const bool sp = df_special(a.s) || df_special(a.c);
         double d;
         if (__any_sync(__activemask(), sp)) d = st_widen(a.s) + st_widen(a.c);   // every class, exactly
-        else d = st_widen_normal(a.s) + st_widen_normal(a.c);
+        else d = df_widen_normal(a.s) + df_widen_normal(a.c);
         atomicAdd(p, d);
     } else {
         atomicAdd(p, a.template out<YT>());
