@@ -211,8 +211,11 @@ __global__ void k_st_counts(const int32_t *__restrict__ slice_start, const uint3
 // Lane headers of every tile (one warp per tile), computed from the words exactly as the
 // product decodes them: the row of the lane's first item, the offset of the lane's run sums
 // in the tile's output buffer (exclusive scan of the lanes' counts), the number of rows that
-// end inside the lane, whether the lane's last run ends with it and whether its first run
-// continues the previous lane's; the tile's total run count goes to bits 8.. of header.w.
+// end inside the lane, whether the lane's last run ends with it, whether its first run
+// continues the previous lane's, and the first lane of the lane's scan segment (the last lane
+// at or before it whose items start a row: a row end inside it or a first item that does not
+// continue); the tile's total run count goes to bits 8..16 of header.w and the number of scan
+// levels its longest segment needs (ceil log2 of its length) to bits 17..19.
 __global__ void k_st_meta(const uint32_t *__restrict__ words, int4 *__restrict__ hdr, int64_t ntiles, int lb,
                           uint2 *__restrict__ lmeta) {
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -249,9 +252,13 @@ __global__ void k_st_meta(const uint32_t *__restrict__ words, int4 *__restrict__
     const int total = __shfl_sync(0xffffffffu, base, 31);
     base -= cnt;
     const uint32_t row0 = (uint32_t)hd.x + (incl - lsum) + dr[0];
+    const uint32_t heads = __ballot_sync(0xffffffffu, nch > 0 || !cont);   // lane 0 is always a head
+    const int h = 31 - __clz(heads & (0xFFFFFFFFu >> (31 - lane)));
+    const int longest = __reduce_max_sync(0xffffffffu, (unsigned)(lane - h + 1));
+    const int levels = longest <= 1 ? 0 : 32 - __clz(longest - 1);
     lmeta[t * 32 + lane] = make_uint2(row0, (uint32_t)base | ((uint32_t)nch << 9) | ((seg_end ? 1u : 0u) << 13) |
-                                                ((cont ? 1u : 0u) << 14));
-    if (lane == 0) hdr[t].w = (hd.w & 0xFF) | (total << 8);
+                                                ((cont ? 1u : 0u) << 14) | ((uint32_t)h << 15));
+    if (lane == 0) hdr[t].w = (hd.w & 0xFF) | (total << 8) | (levels << 17);
 }
 
 // Cost of every tile for the split between CTAs: ST_TILE_COST for the tile's 256 entries,
@@ -277,7 +284,7 @@ __global__ void k_st_cost(const int4 *__restrict__ hdr, int64_t ntiles, int sh, 
         return;
     }
     const uint32_t w = (uint32_t)hdr[t].w;
-    const uint32_t c = (uint32_t)ST_TILE_COST_CFG + (w >> 8) * (uint32_t)ST_RUN_COST_CFG +
+    const uint32_t c = (uint32_t)ST_TILE_COST_CFG + ((w >> 8) & 511u) * (uint32_t)ST_RUN_COST_CFG +
                        ((w & 2u) ? (uint32_t)ST_STAGE_COST_CFG : 0u);
     cost[t] = max(c >> sh, 1u);
 }
@@ -468,7 +475,7 @@ __device__ __forceinline__ void st_tile(const StRegs<SV> &T, const XS *xs, const
     const uint32_t meta = T.lm.y;
     const int base = (int)(meta & 511u), nch = (int)((meta >> 9) & 15u);
     const bool seg_end = (meta >> 13) & 1u, cont = (meta >> 14) & 1u;
-    const int total = (int)((uint32_t)T.hd.w >> 8);
+    const int total = (int)(((uint32_t)T.hd.w >> 8) & 511u);
     uint32_t dr[ST_IPT], co[ST_IPT];
     uint32_t valid = 0xFFu;
 #pragma unroll
@@ -513,24 +520,18 @@ __device__ __forceinline__ void st_tile(const StRegs<SV> &T, const XS *xs, const
         }
         if (CLEAN || ((valid >> j) & 1u)) acc.mad(st_a<Acc, SV>(T.val(j)), xv[j]);
     }
-    // segmented inclusive scan of the lanes' trailing partial sums; a segment starts at a
-    // lane that begins a new row within itself or at its first item
-    const bool head = nch > 0 || !cont;
+    // segmented inclusive scan of the lanes' trailing partial sums over the levels the tile's
+    // longest segment needs; a segment starts at a lane that begins a new row within itself or
+    // at its first item (the segment's first lane comes with the lane header)
+    const int h = (int)((meta >> 15) & 31u);
+    const int levels = (int)(((uint32_t)T.hd.w >> 17) & 7u);
     Acc run = acc;
-    if (!__all_sync(0xffffffffu, head)) {
-        bool f = head;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            if (__all_sync(0xffffffffu, f)) break;   // every lane has reached its segment head
-            Acc ov = run.shfl_up(o);
-            const bool of = __shfl_up_sync(0xffffffffu, f, o);
-            if (lane >= o) {
-                if (!f) {
-                    ov.add(run);
-                    run = ov;
-                }
-                f = f || of;
-            }
+    for (int k = 0; k < levels; ++k) {
+        const int o = 1 << k;
+        Acc ov = run.shfl_up(o);
+        if (lane - o >= h) {
+            ov.add(run);
+            run = ov;
         }
     }
     const Acc prev = run.shfl_up(1);

@@ -25,7 +25,7 @@ namespace spmv {
 namespace {
 
 constexpr char MAGIC[8] = {'S', 'P', 'M', 'V', 'G', 'B', '0', '1'};
-constexpr uint32_t VERSION = 1;
+constexpr uint32_t VERSION = 2;   // 2: lane headers carry the scan segment start, tile headers the scan levels
 constexpr size_t CHUNK = 64u << 20;   // host staging per copy
 constexpr size_t TMA_PAD = 64;        // the padding the conversion gives the CRS arrays
 
