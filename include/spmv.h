@@ -307,7 +307,8 @@ spmv_status spmv_cg(spmv_handle h, const double *b, double *x, double tol, int m
  * device's SMs) and makes the saved format active again (its other tables, e.g. the merge-path
  * partition, come from the CRS arrays as a conversion would build them).  The file format is
  * this library's own (host byte order; see csrc/store.cu).  Errors: SPMV_ERR_INVALID_ARG (NULL
- * argument, not a file of this library), SPMV_ERR_NOT_CONVERTED (save before any conversion),
+ * argument, not a file of this library or one written by a build with another file format
+ * version), SPMV_ERR_NOT_CONVERTED (save before any conversion),
  * SPMV_ERR_IO (open, write or read failed, truncated or damaged file), SPMV_ERR_OOM.
  */
 spmv_status spmv_save(spmv_handle h, const char *path, void *stream);

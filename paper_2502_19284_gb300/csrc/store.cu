@@ -182,7 +182,8 @@ spmv_status spmv_load(const char *path, void *stream, spmv_handle *out) {
     if (!ok || memcmp(magic, MAGIC, 8) != 0 || version != VERSION || !(sections & 1u) || m < 0 || n < 0 || nnz < 0 ||
         m >= ((int64_t)1 << 31) || n >= ((int64_t)1 << 31) || nnz >= ((int64_t)1 << 31) || dt < 0 || dt > 3 ||
         fmt < -1 || (fmt > 2 && fmt != SPMV_FMT_MERGEB)) {
-        set_error(std::string("spmv_load: not a matrix file of this library (or a damaged header): ") + path);
+        set_error(std::string("spmv_load: not a matrix file of this library, of another file format version, or a "
+                              "damaged header: ") + path);
         return SPMV_ERR_INVALID_ARG;
     }
     // a handle with no triplets, then the stored arrays
